@@ -1,0 +1,285 @@
+/*
+ * libmlp — energy and forces of an ANI-2x-shaped machine-learning potential
+ * on one B300 GPU (sm_103a).
+ *
+ * The library evaluates the operation the paper builds its NNPOps/TorchForce
+ * stack around (paper, section "PyTorch Model Support": a model takes atomic
+ * positions and returns the potential energy, forces follow from the energy
+ * by backpropagation or are returned explicitly; section "Optimization
+ * Through NNPOps": the accelerated steps are the neighbor list and the ANI
+ * atom-centered symmetry functions; section "OpenMM-ML": ANI-2x over the seven
+ * elements H, C, N, O, S, F, Cl). One evaluation runs, in this library's own
+ * CUDA kernels:
+ *   1. staging: coordinates (FP64) -> split FP32 hi/lo, periodic wrap,
+ *      species counting for the element-grouped network tiles;
+ *   2. neighbor list: cell list (periodic or open systems) or all pairs
+ *      within each molecule (batches of small molecules);
+ *   3. atomic environment vectors (AEV): 112 radial + 896 angular terms;
+ *   4. per-element networks 1008-256-192-160-1 (CELU, alpha 0.1) and their
+ *      backward to dE/dG: FP32 SIMT GEMMs, or BF16 tcgen05 tensor-core GEMMs
+ *      with FP32 accumulation;
+ *   5. AEV backward to forces, accumulated per atom in FP64;
+ *   6. per-molecule FP64 energy sums and the force output.
+ *
+ * Conventions
+ *   Units: positions and box lengths in Angstrom, energy in the network's
+ *   units (eV with trained weights), forces in energy / Angstrom.
+ *   Species codes: H=0, C=1, N=2, O=3, S=4, F=5, Cl=6.
+ *   Coordinates are FP64 arrays [n][3]; forces are FP32 [n][3] = -dE/dr.
+ *   Boxes are orthorhombic: cell = {Lx, Ly, Lz}, or NULL for open boundary.
+ *   "Host" pointers are ordinary CPU memory owned by the caller; the library
+ *   copies what it needs before returning (or, for mlp_submit, before the
+ *   call returns). "Device" pointers are CUDA global memory on the current
+ *   device, owned by the caller, valid until the stream work completes.
+ *   Streams are cudaStream_t passed as void* (NULL = the legacy stream).
+ *   Handles are owned by the library and released by the matching destroy.
+ *
+ * Errors: every int-returning call returns MLP_OK (0) or a negative code and
+ * records a message retrievable with mlp_last_error() (thread-local).
+ * Invalid arguments never reach a kernel. There is no CPU fallback: without
+ * a usable CUDA device every call that computes returns MLP_ECUDA.
+ */
+#ifndef MLP_H
+#define MLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MLP_API __attribute__((visibility("default")))
+#else
+#define MLP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MLP_OK = 0,
+    MLP_PENDING = 1,     /* mlp_poll: the request is not finished yet            */
+    MLP_EINVAL = -1,     /* bad argument (NULL, n <= 0, NaN, unknown species ...) */
+    MLP_ENOMEM = -2,     /* device or host allocation failed                      */
+    MLP_EAGAIN = -3,     /* server queue full or request larger than the budget   */
+    MLP_ETIMEDOUT = -4,  /* mlp_wait deadline passed                              */
+    MLP_ECUDA = -5,      /* CUDA runtime error (message has the CUDA error text)  */
+    MLP_ENOTFOUND = -6,  /* unknown ticket                                        */
+    MLP_EOVERFLOW = -7   /* neighbor capacity exceeded and could not be grown     */
+};
+
+enum { MLP_FP32 = 0, MLP_BF16 = 1 };
+
+#define MLP_NSPECIES 7
+#define MLP_AEV_LEN 1008
+
+typedef struct mlp_weights mlp_weights;
+typedef struct mlp_system mlp_system;
+typedef struct mlp_batch mlp_batch;
+typedef struct mlp_server mlp_server;
+typedef uint64_t mlp_ticket;
+
+/* Host FP32 weights of the seven per-element networks, element-major:
+ * W1[7][256][1008] b1[7][256] W2[7][192][256] b2[7][192] W3[7][160][192]
+ * b3[7][160] W4[7][160] b4[7]; row index = output unit (y = W x + b).
+ * With n_nets > 1 (ensemble, paper section "Performance of MLPs": ANI-2x is
+ * an average of eight independently trained nets) every array gains a
+ * leading [n_nets] axis. */
+typedef struct {
+    const float *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;
+} mlp_weights_host;
+
+/* Cutoffs in Angstrom. rc_rad = 5.1 and rc_ang = 3.5 are the AEV's own
+ * hyper-parameters and must be given as such; skin >= 0 widens the stored
+ * neighbor list (list radius rc_rad + skin) so that it can be reused across
+ * calls while no atom has moved more than skin / 2. */
+typedef struct {
+    double rc_rad;
+    double rc_ang;
+    double skin;
+} mlp_cutoffs;
+
+/* ------------------------------------------------------------------ weights */
+
+/* Uploads the weights to the current device in FP32 and BF16 with the
+ * transposed copies the backward needs. n_nets in [1, 8]. Returns
+ * MLP_EINVAL on NULL arrays or n_nets out of range, MLP_ENOMEM, MLP_ECUDA. */
+MLP_API int mlp_weights_create(const mlp_weights_host *w, int n_nets, mlp_weights **out);
+MLP_API void mlp_weights_destroy(mlp_weights *w);
+
+/* ------------------------------------------------------------------ one system */
+
+/* Creates a persistent system (one molecule or one periodic box) of n atoms
+ * with fixed species[n]; coords[n][3] (host, may be NULL) are stored as the
+ * current positions. cell = NULL gives an open boundary; otherwise every box
+ * length must be >= 2 (rc_rad + skin). precision = MLP_FP32 (FP32 network)
+ * or MLP_BF16 (BF16 tensor-core network, FP32 accumulation). Device buffers
+ * are sized for n atoms at creation. The weights must outlive the system. */
+MLP_API int mlp_create(const int8_t *species, const double *coords, int32_t n, const double *cell,
+               const mlp_cutoffs *cut, const mlp_weights *w, int precision, mlp_system **out);
+MLP_API void mlp_destroy(mlp_system *s);
+
+/* One evaluation from host memory: copies coords (host [n][3]; NULL = the
+ * stored positions) to the device, evaluates, and copies the energy (host
+ * scalar) and forces (host [n][3], may be NULL) back. Synchronous. */
+MLP_API int mlp_energy_forces(mlp_system *s, const double *coords, double *energy, float *forces);
+
+/* One evaluation from device memory, asynchronous on `stream`:
+ * d_coords [n][3] FP64, d_energy FP64 scalar, d_forces FP32 [n][3] (may be
+ * NULL). Returns after enqueueing; the neighbor capacity check is read back
+ * on the next call (or by mlp_sync), which then reports MLP_EOVERFLOW if a
+ * list was truncated. */
+MLP_API int mlp_energy_forces_device(mlp_system *s, const double *d_coords, double *d_energy, float *d_forces,
+                             void *stream);
+
+/* Forward only (autograd forward): d_energy = E(d_coords). keep_aev != 0
+ * keeps the AEVs on the device for a following mlp_backward_device on the
+ * same coordinates; otherwise the backward recomputes them. */
+MLP_API int mlp_forward_device(mlp_system *s, const double *d_coords, double *d_energy, int keep_aev, void *stream);
+
+/* Backward (autograd backward): d_grad_coords[n][3] (FP32) =
+ * (*d_grad_energy) * dE/dr at d_coords, with d_grad_energy an FP64 device
+ * scalar (NULL = 1). Uses kept AEVs when the last forward kept them for
+ * these coordinates, else recomputes them. */
+MLP_API int mlp_backward_device(mlp_system *s, const double *d_coords, const double *d_grad_energy,
+                        float *d_grad_coords, void *stream);
+
+/* Waits for the system's stream work and reports a deferred error. */
+MLP_API int mlp_sync(mlp_system *s);
+
+/* ------------------------------------------------------------------ batches */
+
+/* A batch engine for many independent open-boundary molecules of at most
+ * max_atoms_per_mol atoms each (all-pairs neighbor search inside each
+ * molecule), sized for max_atoms atoms and max_mols molecules in total. */
+MLP_API int mlp_batch_create(const mlp_weights *w, int precision, int32_t max_atoms, int32_t max_mols,
+                     int32_t max_atoms_per_mol, mlp_batch **out);
+MLP_API void mlp_batch_destroy(mlp_batch *b);
+
+/* Evaluates n_mols molecules packed back to back, all pointers device:
+ * d_mol_start[n_mols + 1] (int32, d_mol_start[0] = 0, ascending), the
+ * host copy of the total atom count n_atoms, d_species[n_atoms] (int8),
+ * d_coords[n_atoms][3] (FP64); writes d_energy[n_mols] (FP64) and
+ * d_forces[n_atoms][3] (FP32). Asynchronous on `stream`. */
+MLP_API int mlp_batch_run_device(mlp_batch *b, int32_t n_mols, int32_t n_atoms, const int32_t *d_mol_start,
+                         const int8_t *d_species, const double *d_coords, double *d_energy, float *d_forces,
+                         void *stream);
+
+/* Same from host memory, synchronous (pinned staging inside the batch). */
+MLP_API int mlp_batch_run(mlp_batch *b, int32_t n_mols, const int32_t *mol_start, const int8_t *species,
+                  const double *coords, double *energy, float *forces);
+
+/* Returns the batch's deferred status (neighbor overflow) after its stream
+ * work completed; 0 if fine. */
+MLP_API int mlp_batch_sync(mlp_batch *b);
+
+/* ------------------------------------------------------------------ serving */
+
+typedef struct {
+    int precision;              /* MLP_BF16 (default) or MLP_FP32                        */
+    int32_t max_batch_atoms;    /* atoms packed into one device batch (default 131072)   */
+    int32_t max_batch_mols;     /* molecules per batch (default 4096)                    */
+    int32_t max_atoms_per_mol;  /* largest admissible molecule (default 256)             */
+    int32_t streams;            /* batches in flight on the device (default 2)           */
+    int32_t queue_capacity;     /* pending requests before MLP_EAGAIN (default 65536)    */
+    int64_t budget_bytes;       /* device bytes the in-flight batches may hold (40e9)    */
+} mlp_server_opts;
+
+/* Fills opts with the defaults above. */
+MLP_API void mlp_server_opts_default(mlp_server_opts *opts);
+
+/* Starts a serving loop (one host thread) that packs queued molecules into
+ * batches, runs up to `streams` batches concurrently on the device, and
+ * completes tickets. Device memory for all slots is reserved here, within
+ * budget_bytes (MLP_ENOMEM if the slots do not fit). */
+MLP_API int mlp_server_create(const mlp_weights *w, const mlp_server_opts *opts, mlp_server **out);
+MLP_API void mlp_server_destroy(mlp_server *s);
+
+/* Queues one open-boundary molecule (host species[n], coords[n][3], copied
+ * before returning). Never blocks: MLP_EAGAIN when the queue is full,
+ * MLP_EINVAL for n outside [1, max_atoms_per_mol] or bad input. */
+MLP_API int mlp_submit(mlp_server *s, int32_t n, const int8_t *species, const double *coords, mlp_ticket *out);
+
+/* Non-blocking: MLP_PENDING while in flight; MLP_OK once done, writing the
+ * energy and forces (host [n][3], may be NULL) and releasing the ticket. */
+MLP_API int mlp_poll(mlp_server *s, mlp_ticket t, double *energy, float *forces);
+
+/* Blocking with a deadline: MLP_ETIMEDOUT if not done within timeout_ns
+ * (the ticket stays valid). */
+MLP_API int mlp_wait(mlp_server *s, mlp_ticket t, int64_t timeout_ns, double *energy, float *forces);
+
+typedef struct {
+    int64_t submitted, completed, batches, atoms;
+    int64_t inflight_bytes, peak_inflight_bytes;
+    double mean_batch_atoms;
+} mlp_server_stats;
+
+MLP_API int mlp_server_get_stats(mlp_server *s, mlp_server_stats *out);
+
+/* Latencies (ns, submit to completion) of requests completed since the last
+ * call, oldest first; copies up to cap of them into out and returns how many
+ * were copied (the rest are dropped). */
+MLP_API int mlp_server_latencies(mlp_server *s, int64_t *out, int cap);
+
+/* Open-loop load generator: a native thread submits request r (molecule
+ * r of the packed host arrays mol_start[n_req + 1], species, coords) at
+ * arrival_ns[r] nanoseconds after the call, waits for all of them, and
+ * writes energies[n_req] and forces (host [mol_start[n_req]][3], may be
+ * NULL). Requests refused with MLP_EAGAIN are retried after 20 us. Returns
+ * the wall time from the call to the last completion in *wall_ns. */
+MLP_API int mlp_server_replay(mlp_server *s, int32_t n_req, const int64_t *arrival_ns, const int32_t *mol_start,
+                      const int8_t *species, const double *coords, double *energies, float *forces,
+                      int64_t *wall_ns);
+
+/* ------------------------------------------------------------------ memory */
+
+/* Routes the library's device allocations through alloc_fn / free_fn (for
+ * example a framework's caching allocator); NULL restores cudaMalloc. Must
+ * be set before any handle is created. alloc_fn returns NULL on failure. */
+MLP_API void mlp_set_allocator(void *(*alloc_fn)(size_t bytes, void *ctx), void (*free_fn)(void *ptr, void *ctx),
+                       void *ctx);
+
+/* Failure injection for tests: the after-th device allocation from now
+ * (0 = the next one) fails as if the device were out of memory. */
+MLP_API void mlp_debug_fail_alloc(long long after);
+
+/* ------------------------------------------------------------------ introspection */
+
+/* Message of the last error on this thread ("" if none). */
+MLP_API const char *mlp_last_error(void);
+
+/* Kernel launches issued by this library since load (all threads). */
+MLP_API int64_t mlp_launch_count(void);
+
+/* Per-kernel timing with CUDA events on the launching stream: enable with
+ * on != 0; mlp_profile_read fills up to cap entries of name / total ms /
+ * launches (names are static strings) and returns the entry count;
+ * mlp_profile_reset clears the totals. Timing synchronizes each event pair,
+ * so it is meant for measurement runs. */
+MLP_API int mlp_profile_enable(int on);
+MLP_API int mlp_profile_read(const char **names, double *total_ms, int64_t *launches, int cap);
+MLP_API void mlp_profile_reset(void);
+
+/* ------------------------------------------------------------------ kernel-level access (tests) */
+
+/* The stored neighbor list of a system after its last evaluation: counts[n]
+ * (host) and up to cap indices per atom in list[n][cap] (host); returns the
+ * capacity used by the device list (call with list = NULL to query it). */
+MLP_API int mlp_debug_neighbors(mlp_system *s, int32_t *counts, int32_t *list, int32_t cap);
+
+/* AEVs of the last evaluation in atom order, host FP32 G[n][1008]. */
+MLP_API int mlp_debug_aev(mlp_system *s, float *G);
+
+/* Per-atom energies e[n] (host FP32) and dE/dG[n][1008] (host FP32, may be
+ * NULL) of the last evaluation that ran the network backward. */
+MLP_API int mlp_debug_atom_energies(mlp_system *s, float *e, float *dEdG);
+
+/* Runs only the network (forward and backward) on caller-provided AEV rows:
+ * host G[n][1008] FP32 and species[n]; writes e[n] and dEdG[n][1008] (host).
+ * precision selects the FP32 SIMT or the BF16 tensor-core network. */
+MLP_API int mlp_debug_network(const mlp_weights *w, int precision, int32_t n, const int8_t *species, const float *G,
+                      float *e, float *dEdG);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLP_H */

@@ -85,6 +85,11 @@ def lib():
         L.oracle_local_energy.restype = ctypes.c_double
         L.oracle_local_energy.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), ctypes.c_int,
                                           _dp, ctypes.c_double]
+        L.oracle_atom_energies.restype = None
+        L.oracle_atom_energies.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), ctypes.c_int, _ip,
+                                           _dp, ctypes.c_int]
+        L.oracle_aev_subset.restype = None
+        L.oracle_aev_subset.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.c_int, _ip, _dp]
         L.oracle_energy_forces_batch.restype = None
         L.oracle_energy_forces_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_long), _ip, _dp, _dp,
                                                  ctypes.POINTER(_Weights), _dp, _dp, ctypes.c_int]
@@ -238,6 +243,31 @@ def local_energy(species, coords, cell, w, m, center, margin=0.2):
     c = _cell(cell)
     return lib().oracle_local_energy(x.shape[0], _i(s), _d(x), None if c is None else _d(c), w.ref(), int(m),
                                      _d(ctr), float(margin))
+
+
+def atom_energies(species, coords, cell, w, idx=None, nthreads=None):
+    """e_i for the listed atoms (all atoms if idx is None), threads over atoms."""
+    w = _as_weights(w)
+    x = _f64(coords)
+    s = _i32(species)
+    n = x.shape[0]
+    idx = np.arange(n, dtype=np.int32) if idx is None else _i32(idx)
+    e = np.zeros(idx.shape[0])
+    c = _cell(cell)
+    nt = int(nthreads or os.cpu_count() or 1)
+    lib().oracle_atom_energies(n, _i(s), _d(x), None if c is None else _d(c), w.ref(), idx.shape[0], _i(idx), _d(e),
+                               nt)
+    return e
+
+
+def aev_subset(species, coords, cell, idx):
+    x = _f64(coords)
+    s = _i32(species)
+    idx = _i32(idx)
+    G = np.zeros((idx.shape[0], AEV_LEN))
+    c = _cell(cell)
+    lib().oracle_aev_subset(x.shape[0], _i(s), _d(x), None if c is None else _d(c), idx.shape[0], _i(idx), _d(G))
+    return G
 
 
 def energy_forces_batch(mol_start, species, coords, w, nthreads=None):

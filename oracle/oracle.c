@@ -481,4 +481,39 @@ void oracle_energy_forces_batch(int nmol, const long *mol_start, const int *spec
     (void)nthreads;
 }
 
+/* Per-atom energies e_out[q] = e_{idx[q]} for the listed atoms (each one an
+ * independent evaluation of its AEV and network), spread over nthreads
+ * OpenMP threads when built with OpenMP. */
+void oracle_atom_energies(int n, const int *species, const double *xyz, const double *cell,
+                          const oracle_weights *w, int nidx, const int *idx, double *e_out, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    {
+        double *G = (double *)malloc(sizeof(double) * AEV_LEN);
+        int *nb = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int q = 0; q < nidx; ++q) {
+            int i = idx[q];
+            aev_atom(i, n, species, xyz, cell, nb, G);
+            e_out[q] = oracle_atom_energy(species[i], G, w, NULL);
+        }
+        free(G);
+        free(nb);
+    }
+    (void)nthreads;
+}
+
+/* AEV rows of the listed atoms only: G_out[nidx][1008]. */
+void oracle_aev_subset(int n, const int *species, const double *xyz, const double *cell, int nidx, const int *idx,
+                       double *G_out)
+{
+    int *nb = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    for (int q = 0; q < nidx; ++q) aev_atom(idx[q], n, species, xyz, cell, nb, G_out + (size_t)AEV_LEN * q);
+    free(nb);
+}
+
 int oracle_aev_length(void) { return AEV_LEN; }

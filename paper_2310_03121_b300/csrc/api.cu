@@ -1,0 +1,795 @@
+// C-ABI of libmlp (declared in include/mlp.h): weights, systems, batches,
+// introspection and kernel-level test access. The serving loop is in
+// server.cu. Every entry point validates its arguments on the host before
+// anything reaches a kernel, and converts failures into MLP_* codes.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mlp.h"
+#include "engine.cuh"
+
+using namespace mlp;
+
+struct mlp_weights {
+    DevWeights dw;
+};
+
+struct mlp_system {
+    int n = 0;
+    int periodic = 0;
+    double L[3] = {0, 0, 0};
+    mlp_cutoffs cut{};
+    const mlp_weights* w = nullptr;
+    int precision = 0;
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    int8_t* d_species = nullptr;
+    double* d_xyz = nullptr;
+    double* d_E = nullptr;
+    float* d_F = nullptr;
+    double* h_xyz = nullptr;   // pinned staging
+    double* h_E = nullptr;
+    float* h_F = nullptr;
+    void* dev_block = nullptr;
+    long long calls = 0;
+    int rebuild_interval = 10;
+    bool kept = false;
+    const double* kept_coords = nullptr;
+    bool nbr_valid = false;
+    cudaEvent_t done = nullptr;
+    bool pending = false;   // counters of an asynchronous call not yet checked
+};
+
+struct mlp_batch {
+    int precision = 0;
+    int max_atoms_per_mol = 256;
+    const mlp_weights* w = nullptr;
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    void* dev_block = nullptr;
+    int* d_mol_start = nullptr;
+    int8_t* d_species = nullptr;
+    double* d_xyz = nullptr;
+    double* d_E = nullptr;
+    float* d_F = nullptr;
+    void* h_block = nullptr;   // pinned staging
+    int* h_mol_start = nullptr;
+    int8_t* h_species = nullptr;
+    double* h_xyz = nullptr;
+    double* h_E = nullptr;
+    float* h_F = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+namespace mlp {
+const DevWeights& weights_of(const mlp_weights* w) { return w->dw; }
+}  // namespace mlp
+
+namespace {
+
+int check_cuda_device() {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return set_error(MLP_ECUDA, "no usable CUDA device (%s)", e == cudaSuccess ? "none" : cudaGetErrorString(e));
+    }
+    init_constants_for_current_device();
+    return MLP_OK;
+}
+
+inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// float -> bf16 (round to nearest even) on the host
+inline __nv_bfloat16 to_bf16(float f) { return __float2bfloat16_rn(f); }
+
+int sys_finish_pending(mlp_system* s) {
+    if (!s->pending) return MLP_OK;
+    cudaError_t e = cudaEventSynchronize(s->done);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize");
+    s->pending = false;
+    return check_counters(s->ws);
+}
+
+int sys_make_workspace(mlp_system* s, int nbr_cap) {
+    // open systems: at most ~2 cells per atom plus slack
+    int max_cells = s->periodic ? make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin)).ncell
+                                : (s->n * 2 + 64);
+    int rc = workspace_create(s->ws, s->n, 1, s->precision, true, nbr_cap, max_cells);
+    if (rc) return rc;
+    if (s->periodic) {
+        Grid g = make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin));
+        cudaError_t e = cudaMemcpy(s->ws.grid, &g, sizeof(Grid), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(grid)");
+    }
+    s->nbr_valid = false;
+    return MLP_OK;
+}
+
+EvalSpec sys_spec(mlp_system* s, const double* d_xyz) {
+    EvalSpec sp;
+    sp.n_atoms = s->n;
+    sp.n_mols = 1;
+    sp.d_species = s->d_species;
+    sp.d_xyz = d_xyz;
+    sp.periodic = s->periodic;
+    for (int a = 0; a < 3; ++a) sp.L[a] = s->L[a];
+    sp.r_list = (float)(s->cut.rc_rad + s->cut.skin);
+    double hs = 0.5 * s->cut.skin;
+    sp.half_skin2 = (float)(hs * hs);
+    sp.force_rebuild = !s->nbr_valid || s->cut.skin <= 0.0 || (s->calls % s->rebuild_interval) == 0;
+    return sp;
+}
+
+int sys_enqueue(mlp_system* s, EvalSpec& sp, cudaStream_t st) {
+    int rc = enqueue_eval(s->ws, s->w->dw, sp, st);
+    if (rc) return rc;
+    cudaError_t e = cudaEventRecord(s->done, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    s->pending = true;
+    s->nbr_valid = true;
+    s->calls++;
+    return MLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlp_last_error(void) { return last_error(); }
+
+int64_t mlp_launch_count(void) { return (int64_t)launch_count(); }
+
+int mlp_profile_enable(int on) { return profile_enable(on); }
+
+int mlp_profile_read(const char** names, double* total_ms, int64_t* launches, int cap) {
+    std::vector<long long> tmp(cap > 0 ? cap : 1);
+    int k = profile_read(names, total_ms, tmp.data(), cap);
+    if (launches)
+        for (int q = 0; q < cap && q < k; ++q) launches[q] = tmp[q];
+    return k;
+}
+
+void mlp_profile_reset(void) { profile_reset(); }
+
+void mlp_set_allocator(void* (*alloc_fn)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
+    set_allocator(alloc_fn, free_fn, ctx);
+}
+
+void mlp_debug_fail_alloc(long long after) { set_alloc_failure(after); }
+
+// ------------------------------------------------------------------ weights
+int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out) {
+    clear_error();
+    if (!w || !out) return set_error(MLP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_nets < 1 || n_nets > kMaxNets) return set_error(MLP_EINVAL, "n_nets %d outside [1, %d]", n_nets, kMaxNets);
+    if (!w->W1 || !w->b1 || !w->W2 || !w->b2 || !w->W3 || !w->b3 || !w->W4 || !w->b4)
+        return set_error(MLP_EINVAL, "NULL weight array");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    const int S = kNSpecies;
+    // per-net sizes (floats)
+    const size_t nW1 = (size_t)S * kH1 * kAevLen, nb1 = S * kH1, nW2 = (size_t)S * kH2 * kH1, nb2 = S * kH2,
+                 nW3 = (size_t)S * kH3 * kH2, nb3 = S * kH3, nW4 = S * kH3, nb4 = S;
+    // FP32 block: W1 b1 W2 b2 W3 b3 W4 b4 W1t W2t W3t per net
+    size_t f32_per_net = al256(nW1 * 4) + al256(nb1 * 4) + al256(nW2 * 4) + al256(nb2 * 4) + al256(nW3 * 4) +
+                         al256(nb3 * 4) + al256(nW4 * 4) + al256(nb4 * 4) + al256(nW1 * 4) + al256(nW2 * 4) +
+                         al256(nW3 * 4);
+    const size_t nW1p = (size_t)S * kH1 * kAevLd;   // padded K for the BF16 operands
+    size_t bf_per_net = al256(nW1p * 2) + al256(nW2 * 2) + al256(nW3 * 2) + al256(nW1p * 2) + al256(nW2 * 2) +
+                        al256(nW3 * 2);
+    mlp_weights* mw = new (std::nothrow) mlp_weights();
+    if (!mw) return set_error(MLP_ENOMEM, "host allocation failed");
+    mw->dw.n_nets = n_nets;
+    cudaGetDevice(&mw->dw.device);
+    mw->dw.blk_f32 = dev_alloc(f32_per_net * n_nets);
+    mw->dw.blk_bf16 = dev_alloc(bf_per_net * n_nets);
+    if (!mw->dw.blk_f32 || !mw->dw.blk_bf16) {
+        mlp_weights_destroy(mw);
+        return set_error(MLP_ENOMEM, "device allocation of the weights failed");
+    }
+    std::vector<char> hf(f32_per_net), hb(bf_per_net);
+    for (int net = 0; net < n_nets; ++net) {
+        const float* W1 = w->W1 + net * nW1;
+        const float* b1 = w->b1 + net * nb1;
+        const float* W2 = w->W2 + net * nW2;
+        const float* b2 = w->b2 + net * nb2;
+        const float* W3 = w->W3 + net * nW3;
+        const float* b3 = w->b3 + net * nb3;
+        const float* W4 = w->W4 + net * nW4;
+        const float* b4 = w->b4 + net * nb4;
+        for (size_t q = 0; q < nW1; ++q)
+            if (!std::isfinite(W1[q])) {
+                mlp_weights_destroy(mw);
+                return set_error(MLP_EINVAL, "non-finite weight in W1");
+            }
+        // FP32 layout
+        std::memset(hf.data(), 0, hf.size());
+        size_t off = 0;
+        auto put = [&](const float* src, size_t cnt) {
+            float* dst = reinterpret_cast<float*>(hf.data() + off);
+            if (src) std::memcpy(dst, src, cnt * 4);
+            size_t o = off;
+            off += al256(cnt * 4);
+            return o;
+        };
+        size_t oW1 = put(W1, nW1), ob1 = put(b1, nb1), oW2 = put(W2, nW2), ob2 = put(b2, nb2), oW3 = put(W3, nW3),
+               ob3 = put(b3, nb3), oW4 = put(W4, nW4), ob4 = put(b4, nb4);
+        size_t oW1t = put(nullptr, nW1), oW2t = put(nullptr, nW2), oW3t = put(nullptr, nW3);
+        float* W1t = reinterpret_cast<float*>(hf.data() + oW1t);
+        float* W2t = reinterpret_cast<float*>(hf.data() + oW2t);
+        float* W3t = reinterpret_cast<float*>(hf.data() + oW3t);
+        for (int s = 0; s < S; ++s) {
+            for (int o = 0; o < kH1; ++o)
+                for (int c = 0; c < kAevLen; ++c)
+                    W1t[(size_t)s * kAevLen * kH1 + (size_t)c * kH1 + o] = W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c];
+            for (int o = 0; o < kH2; ++o)
+                for (int c = 0; c < kH1; ++c) W2t[(size_t)s * kH1 * kH2 + c * kH2 + o] = W2[(size_t)s * kH2 * kH1 + o * kH1 + c];
+            for (int o = 0; o < kH3; ++o)
+                for (int c = 0; c < kH2; ++c) W3t[(size_t)s * kH2 * kH3 + c * kH3 + o] = W3[(size_t)s * kH3 * kH2 + o * kH2 + c];
+        }
+        char* dbase = static_cast<char*>(mw->dw.blk_f32) + net * f32_per_net;
+        cudaError_t e = cudaMemcpy(dbase, hf.data(), f32_per_net, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            mlp_weights_destroy(mw);
+            return cuda_error(e, "cudaMemcpy(weights)");
+        }
+        NetF32& nf = mw->dw.f32[net];
+        nf.W1 = reinterpret_cast<const float*>(dbase + oW1);
+        nf.b1 = reinterpret_cast<const float*>(dbase + ob1);
+        nf.W2 = reinterpret_cast<const float*>(dbase + oW2);
+        nf.b2 = reinterpret_cast<const float*>(dbase + ob2);
+        nf.W3 = reinterpret_cast<const float*>(dbase + oW3);
+        nf.b3 = reinterpret_cast<const float*>(dbase + ob3);
+        nf.W4 = reinterpret_cast<const float*>(dbase + oW4);
+        nf.b4 = reinterpret_cast<const float*>(dbase + ob4);
+        nf.W1t = reinterpret_cast<const float*>(dbase + oW1t);
+        nf.W2t = reinterpret_cast<const float*>(dbase + oW2t);
+        nf.W3t = reinterpret_cast<const float*>(dbase + oW3t);
+        // BF16 layout: W1 [7][256][1024] (K padded with zeros), W2, W3, and the
+        // transposes W1t [7][1024][256] (rows >= 1008 zero), W2t, W3t
+        std::memset(hb.data(), 0, hb.size());
+        size_t boff = 0;
+        auto bput = [&](size_t cnt) {
+            size_t o = boff;
+            boff += al256(cnt * 2);
+            return o;
+        };
+        size_t bW1 = bput(nW1p), bW2 = bput(nW2), bW3 = bput(nW3), bW1t = bput(nW1p), bW2t = bput(nW2),
+               bW3t = bput(nW3);
+        auto B = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(hb.data() + o); };
+        for (int s = 0; s < S; ++s) {
+            for (int o = 0; o < kH1; ++o)
+                for (int c = 0; c < kAevLen; ++c) {
+                    __nv_bfloat16 v = to_bf16(W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c]);
+                    B(bW1)[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = v;
+                    B(bW1t)[(size_t)s * kAevLd * kH1 + (size_t)c * kH1 + o] = v;
+                }
+            for (int o = 0; o < kH2; ++o)
+                for (int c = 0; c < kH1; ++c) {
+                    __nv_bfloat16 v = to_bf16(W2[(size_t)s * kH2 * kH1 + o * kH1 + c]);
+                    B(bW2)[(size_t)s * kH2 * kH1 + o * kH1 + c] = v;
+                    B(bW2t)[(size_t)s * kH1 * kH2 + c * kH2 + o] = v;
+                }
+            for (int o = 0; o < kH3; ++o)
+                for (int c = 0; c < kH2; ++c) {
+                    __nv_bfloat16 v = to_bf16(W3[(size_t)s * kH3 * kH2 + o * kH2 + c]);
+                    B(bW3)[(size_t)s * kH3 * kH2 + o * kH2 + c] = v;
+                    B(bW3t)[(size_t)s * kH2 * kH3 + c * kH3 + o] = v;
+                }
+        }
+        char* bbase = static_cast<char*>(mw->dw.blk_bf16) + net * bf_per_net;
+        e = cudaMemcpy(bbase, hb.data(), bf_per_net, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            mlp_weights_destroy(mw);
+            return cuda_error(e, "cudaMemcpy(weights bf16)");
+        }
+        NetBF16& nb = mw->dw.bf16[net];
+        nb.W1 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1);
+        nb.W2 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2);
+        nb.W3 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3);
+        nb.W1t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1t);
+        nb.W2t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2t);
+        nb.W3t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3t);
+        nb.b1 = nf.b1;
+        nb.b2 = nf.b2;
+        nb.b3 = nf.b3;
+        nb.W4 = nf.W4;
+        nb.b4 = nf.b4;
+    }
+    *out = mw;
+    return MLP_OK;
+}
+
+void mlp_weights_destroy(mlp_weights* w) {
+    if (!w) return;
+    dev_free(w->dw.blk_f32);
+    dev_free(w->dw.blk_bf16);
+    delete w;
+}
+
+// ------------------------------------------------------------------ systems
+int mlp_create(const int8_t* species, const double* coords, int32_t n, const double* cell, const mlp_cutoffs* cut,
+               const mlp_weights* w, int precision, mlp_system** out) {
+    clear_error();
+    if (!out) return set_error(MLP_EINVAL, "NULL out");
+    *out = nullptr;
+    if (!species || !cut || !w) return set_error(MLP_EINVAL, "NULL argument");
+    if (n <= 0) return set_error(MLP_EINVAL, "n = %d must be positive", n);
+    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision %d", precision);
+    if (precision == MLP_BF16 && !mlp_tc_available())
+        return set_error(MLP_EINVAL, "BF16 tensor-core network is not available in this build");
+    if (std::fabs(cut->rc_rad - 5.1) > 1e-12 || std::fabs(cut->rc_ang - 3.5) > 1e-12)
+        return set_error(MLP_EINVAL, "cutoffs must be rc_rad = 5.1 and rc_ang = 3.5 (the AEV's own)");
+    if (!(cut->skin >= 0.0) || cut->skin > 2.0) return set_error(MLP_EINVAL, "skin must be in [0, 2]");
+    for (int i = 0; i < n; ++i)
+        if (species[i] < 0 || species[i] >= kNSpecies) return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
+    if (cell) {
+        for (int a = 0; a < 3; ++a)
+            if (!(cell[a] >= 2.0 * (cut->rc_rad + cut->skin)) || !std::isfinite(cell[a]))
+                return set_error(MLP_EINVAL, "box length %g below 2 (rc_rad + skin)", cell[a]);
+    }
+    if (coords)
+        for (long q = 0; q < 3L * n; ++q)
+            if (!std::isfinite(coords[q])) return set_error(MLP_EINVAL, "non-finite coordinate");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    mlp_system* s = new (std::nothrow) mlp_system();
+    if (!s) return set_error(MLP_ENOMEM, "host allocation failed");
+    s->n = n;
+    s->periodic = cell ? 1 : 0;
+    if (cell)
+        for (int a = 0; a < 3; ++a) s->L[a] = cell[a];
+    s->cut = *cut;
+    s->w = w;
+    s->precision = precision;
+    rc = sys_make_workspace(s, kDefaultNbrCap);
+    if (rc) {
+        mlp_destroy(s);
+        return rc;
+    }
+    size_t db = al256((size_t)n) + al256(24 * (size_t)n) + al256(8) + al256(12 * (size_t)n);
+    s->dev_block = dev_alloc(db);
+    if (!s->dev_block) {
+        mlp_destroy(s);
+        return set_error(MLP_ENOMEM, "device allocation failed");
+    }
+    char* p = static_cast<char*>(s->dev_block);
+    s->d_species = reinterpret_cast<int8_t*>(p);
+    p += al256(n);
+    s->d_xyz = reinterpret_cast<double*>(p);
+    p += al256(24 * (size_t)n);
+    s->d_E = reinterpret_cast<double*>(p);
+    p += al256(8);
+    s->d_F = reinterpret_cast<float*>(p);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void**>(&s->h_xyz), 24 * (size_t)n)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void**>(&s->h_E), 8)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void**>(&s->h_F), 12 * (size_t)n)) != cudaSuccess) {
+        mlp_destroy(s);
+        return cuda_error(e, "mlp_create");
+    }
+    e = cudaMemcpy(s->d_species, species, n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && coords) e = cudaMemcpy(s->d_xyz, coords, 24 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mlp_destroy(s);
+        return cuda_error(e, "mlp_create copy");
+    }
+    *out = s;
+    return MLP_OK;
+}
+
+void mlp_destroy(mlp_system* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    workspace_destroy(s->ws);
+    dev_free(s->dev_block);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->done) cudaEventDestroy(s->done);
+    if (s->h_xyz) cudaFreeHost(s->h_xyz);
+    if (s->h_E) cudaFreeHost(s->h_E);
+    if (s->h_F) cudaFreeHost(s->h_F);
+    delete s;
+}
+
+int mlp_sync(mlp_system* s) {
+    clear_error();
+    if (!s) return set_error(MLP_EINVAL, "NULL system");
+    return sys_finish_pending(s);
+}
+
+int mlp_energy_forces(mlp_system* s, const double* coords, double* energy, float* forces) {
+    clear_error();
+    if (!s || !energy) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    const size_t nb = 24 * (size_t)s->n;
+    if (coords) {
+        for (long q = 0; q < 3L * s->n; ++q)
+            if (!std::isfinite(coords[q])) return set_error(MLP_EINVAL, "non-finite coordinate");
+        std::memcpy(s->h_xyz, coords, nb);
+        cudaError_t e = cudaMemcpyAsync(s->d_xyz, s->h_xyz, nb, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(coords)");
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        s->kept = false;
+        EvalSpec sp = sys_spec(s, s->d_xyz);
+        sp.d_E = s->d_E;
+        sp.d_F = forces ? s->d_F : nullptr;
+        rc = sys_enqueue(s, sp, s->stream);
+        if (rc) return rc;
+        cudaMemcpyAsync(s->h_E, s->d_E, 8, cudaMemcpyDeviceToHost, s->stream);
+        if (forces) cudaMemcpyAsync(s->h_F, s->d_F, 12 * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream);
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+        s->pending = false;
+        rc = check_counters(s->ws);
+        if (rc == MLP_EOVERFLOW && s->ws.h_ctr->nbr_overflow && s->ws.nbr_cap < 256 && attempt == 0) {
+            // grow the neighbor rows once and redo the evaluation
+            workspace_destroy(s->ws);
+            rc = sys_make_workspace(s, 256);
+            if (rc) return rc;
+            continue;
+        }
+        if (rc) return rc;
+        break;
+    }
+    *energy = *s->h_E;
+    if (forces) std::memcpy(forces, s->h_F, 12 * (size_t)s->n);
+    return MLP_OK;
+}
+
+int mlp_energy_forces_device(mlp_system* s, const double* d_coords, double* d_energy, float* d_forces, void* stream) {
+    clear_error();
+    if (!s || !d_coords || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    s->kept = false;
+    EvalSpec sp = sys_spec(s, d_coords);
+    sp.d_E = d_energy;
+    sp.d_F = d_forces;
+    return sys_enqueue(s, sp, static_cast<cudaStream_t>(stream));
+}
+
+int mlp_forward_device(mlp_system* s, const double* d_coords, double* d_energy, int keep_aev, void* stream) {
+    clear_error();
+    if (!s || !d_coords || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    EvalSpec sp = sys_spec(s, d_coords);
+    sp.network_backward = false;
+    sp.d_E = d_energy;
+    rc = sys_enqueue(s, sp, static_cast<cudaStream_t>(stream));
+    s->kept = rc == MLP_OK && keep_aev;
+    s->kept_coords = d_coords;
+    return rc;
+}
+
+int mlp_backward_device(mlp_system* s, const double* d_coords, const double* d_grad_energy, float* d_grad_coords,
+                        void* stream) {
+    clear_error();
+    if (!s || !d_coords || !d_grad_coords) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    EvalSpec sp = sys_spec(s, d_coords);
+    sp.reuse_aev = s->kept && s->kept_coords == d_coords;
+    sp.network_backward = true;
+    sp.energy = false;
+    sp.d_F = d_grad_coords;
+    sp.d_grad_scale = d_grad_energy;
+    sp.sign = 1.f;
+    if (sp.reuse_aev) sp.force_rebuild = false;
+    rc = sys_enqueue(s, sp, static_cast<cudaStream_t>(stream));
+    return rc;
+}
+
+// ------------------------------------------------------------------ batches
+int mlp_batch_create(const mlp_weights* w, int precision, int32_t max_atoms, int32_t max_mols,
+                     int32_t max_atoms_per_mol, mlp_batch** out) {
+    clear_error();
+    if (!out) return set_error(MLP_EINVAL, "NULL out");
+    *out = nullptr;
+    if (!w) return set_error(MLP_EINVAL, "NULL weights");
+    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision %d", precision);
+    if (precision == MLP_BF16 && !mlp_tc_available())
+        return set_error(MLP_EINVAL, "BF16 tensor-core network is not available in this build");
+    if (max_atoms <= 0 || max_mols <= 0 || max_atoms_per_mol <= 0 || max_atoms_per_mol > max_atoms)
+        return set_error(MLP_EINVAL, "bad batch dimensions");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    mlp_batch* b = new (std::nothrow) mlp_batch();
+    if (!b) return set_error(MLP_ENOMEM, "host allocation failed");
+    b->precision = precision;
+    b->max_atoms_per_mol = max_atoms_per_mol;
+    b->w = w;
+    rc = workspace_create(b->ws, max_atoms, max_mols, precision, false, kDefaultNbrCap, 0);
+    if (rc) {
+        mlp_batch_destroy(b);
+        return rc;
+    }
+    const size_t A = max_atoms, Mo = max_mols;
+    size_t db = al256(4 * (Mo + 1)) + al256(A) + al256(24 * A) + al256(8 * Mo) + al256(12 * A);
+    b->dev_block = dev_alloc(db);
+    if (!b->dev_block) {
+        mlp_batch_destroy(b);
+        return set_error(MLP_ENOMEM, "device allocation failed");
+    }
+    char* p = static_cast<char*>(b->dev_block);
+    b->d_mol_start = reinterpret_cast<int*>(p);
+    p += al256(4 * (Mo + 1));
+    b->d_species = reinterpret_cast<int8_t*>(p);
+    p += al256(A);
+    b->d_xyz = reinterpret_cast<double*>(p);
+    p += al256(24 * A);
+    b->d_E = reinterpret_cast<double*>(p);
+    p += al256(8 * Mo);
+    b->d_F = reinterpret_cast<float*>(p);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaMallocHost(&b->h_block, db)) != cudaSuccess) {
+        mlp_batch_destroy(b);
+        return cuda_error(e, "mlp_batch_create");
+    }
+    char* h = static_cast<char*>(b->h_block);
+    b->h_mol_start = reinterpret_cast<int*>(h);
+    h += al256(4 * (Mo + 1));
+    b->h_species = reinterpret_cast<int8_t*>(h);
+    h += al256(A);
+    b->h_xyz = reinterpret_cast<double*>(h);
+    h += al256(24 * A);
+    b->h_E = reinterpret_cast<double*>(h);
+    h += al256(8 * Mo);
+    b->h_F = reinterpret_cast<float*>(h);
+    *out = b;
+    return MLP_OK;
+}
+
+void mlp_batch_destroy(mlp_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    workspace_destroy(b->ws);
+    dev_free(b->dev_block);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->h_block) cudaFreeHost(b->h_block);
+    delete b;
+}
+
+int mlp_batch_sync(mlp_batch* b) {
+    clear_error();
+    if (!b) return set_error(MLP_EINVAL, "NULL batch");
+    if (!b->pending) return MLP_OK;
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize");
+    b->pending = false;
+    return check_counters(b->ws);
+}
+
+int mlp_batch_run_device(mlp_batch* b, int32_t n_mols, int32_t n_atoms, const int32_t* d_mol_start,
+                         const int8_t* d_species, const double* d_coords, double* d_energy, float* d_forces,
+                         void* stream) {
+    clear_error();
+    if (!b || !d_mol_start || !d_species || !d_coords || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
+    if (n_mols <= 0 || n_mols > b->ws.cap_mols) return set_error(MLP_EINVAL, "n_mols %d outside [1, %d]", n_mols, b->ws.cap_mols);
+    if (n_atoms <= 0 || n_atoms > b->ws.cap_atoms)
+        return set_error(MLP_EINVAL, "n_atoms %d outside [1, %d]", n_atoms, b->ws.cap_atoms);
+    int rc = mlp_batch_sync(b);
+    if (rc) return rc;
+    EvalSpec sp;
+    sp.n_atoms = n_atoms;
+    sp.n_mols = n_mols;
+    sp.d_mol_start = d_mol_start;
+    sp.d_species = d_species;
+    sp.d_xyz = d_coords;
+    sp.r_list = kRcRad;
+    sp.d_E = d_energy;
+    sp.d_F = d_forces;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = enqueue_eval(b->ws, b->w->dw, sp, st);
+    if (rc) return rc;
+    cudaError_t e = cudaEventRecord(b->done, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    b->pending = true;
+    return MLP_OK;
+}
+
+int mlp_batch_run(mlp_batch* b, int32_t n_mols, const int32_t* mol_start, const int8_t* species, const double* coords,
+                  double* energy, float* forces) {
+    clear_error();
+    if (!b || !mol_start || !species || !coords || !energy) return set_error(MLP_EINVAL, "NULL argument");
+    if (n_mols <= 0 || n_mols > b->ws.cap_mols) return set_error(MLP_EINVAL, "n_mols %d outside [1, %d]", n_mols, b->ws.cap_mols);
+    if (mol_start[0] != 0) return set_error(MLP_EINVAL, "mol_start[0] must be 0");
+    for (int m = 0; m < n_mols; ++m) {
+        int sz = mol_start[m + 1] - mol_start[m];
+        if (sz <= 0 || sz > b->max_atoms_per_mol)
+            return set_error(MLP_EINVAL, "molecule %d has %d atoms (allowed 1..%d)", m, sz, b->max_atoms_per_mol);
+    }
+    const int n = mol_start[n_mols];
+    if (n > b->ws.cap_atoms) return set_error(MLP_EINVAL, "%d atoms above capacity %d", n, b->ws.cap_atoms);
+    for (int i = 0; i < n; ++i)
+        if (species[i] < 0 || species[i] >= kNSpecies) return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
+    for (long q = 0; q < 3L * n; ++q)
+        if (!std::isfinite(coords[q])) return set_error(MLP_EINVAL, "non-finite coordinate");
+    int rc = mlp_batch_sync(b);
+    if (rc) return rc;
+    std::memcpy(b->h_mol_start, mol_start, 4 * (size_t)(n_mols + 1));
+    std::memcpy(b->h_species, species, n);
+    std::memcpy(b->h_xyz, coords, 24 * (size_t)n);
+    cudaStream_t st = b->stream;
+    cudaMemcpyAsync(b->d_mol_start, b->h_mol_start, 4 * (size_t)(n_mols + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(b->d_species, b->h_species, n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(b->d_xyz, b->h_xyz, 24 * (size_t)n, cudaMemcpyHostToDevice, st);
+    rc = mlp_batch_run_device(b, n_mols, n, b->d_mol_start, b->d_species, b->d_xyz, b->d_E, forces ? b->d_F : nullptr,
+                              st);
+    if (rc) return rc;
+    cudaMemcpyAsync(b->h_E, b->d_E, 8 * (size_t)n_mols, cudaMemcpyDeviceToHost, st);
+    if (forces) cudaMemcpyAsync(b->h_F, b->d_F, 12 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    // the completion event must follow the result copies
+    cudaError_t e = cudaEventRecord(b->done, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    rc = mlp_batch_sync(b);
+    if (rc) return rc;
+    std::memcpy(energy, b->h_E, 8 * (size_t)n_mols);
+    if (forces) std::memcpy(forces, b->h_F, 12 * (size_t)n);
+    return MLP_OK;
+}
+
+// ------------------------------------------------------------------ kernel-level access
+int mlp_debug_neighbors(mlp_system* s, int32_t* counts, int32_t* list, int32_t cap) {
+    clear_error();
+    if (!s) return set_error(MLP_EINVAL, "NULL system");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    cudaStreamSynchronize(s->stream);
+    const int n = s->n, C = s->ws.nbr_cap;
+    if (counts) cudaMemcpy(counts, s->ws.nbr_cnt, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    if (list) {
+        std::vector<int> tmp((size_t)n * C);
+        cudaMemcpy(tmp.data(), s->ws.nbr, 4 * tmp.size(), cudaMemcpyDeviceToHost);
+        for (int i = 0; i < n; ++i)
+            for (int q = 0; q < cap; ++q) list[(size_t)i * cap + q] = q < C ? tmp[(size_t)i * C + q] : -1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "mlp_debug_neighbors");
+    return C;
+}
+
+// Row of every atom in the element-grouped matrices (host copy of the counters).
+static int atom_rows(mlp_system* s, std::vector<int>& rows) {
+    const int n = s->n;
+    std::vector<int> rank(n);
+    cudaMemcpy(rank.data(), s->ws.rank, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    Counters c;
+    cudaMemcpy(&c, s->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost);
+    std::vector<int8_t> sp(n);
+    cudaMemcpy(sp.data(), s->d_species, n, cudaMemcpyDeviceToHost);
+    int base[kNSpecies];
+    int b = 0;
+    for (int q = 0; q < kNSpecies; ++q) {
+        base[q] = b;
+        b += (c.species[q] + kTileRows - 1) / kTileRows * kTileRows;
+    }
+    rows.resize(n);
+    for (int i = 0; i < n; ++i) rows[i] = base[sp[i]] + rank[i];
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : cuda_error(e, "atom_rows");
+}
+
+int mlp_debug_aev(mlp_system* s, float* G) {
+    clear_error();
+    if (!s || !G) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    cudaStreamSynchronize(s->stream);
+    std::vector<int> rows;
+    rc = atom_rows(s, rows);
+    if (rc) return rc;
+    const size_t R = s->ws.rows_cap;
+    if (s->precision == MLP_FP32) {
+        std::vector<float> all(R * kAevLd);
+        cudaMemcpy(all.data(), s->ws.G32, 4 * all.size(), cudaMemcpyDeviceToHost);
+        for (int i = 0; i < s->n; ++i) std::memcpy(G + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
+    } else {
+        std::vector<__nv_bfloat16> all(R * kAevLd);
+        cudaMemcpy(all.data(), s->ws.G16, 2 * all.size(), cudaMemcpyDeviceToHost);
+        for (int i = 0; i < s->n; ++i)
+            for (int c = 0; c < kAevLen; ++c) G[(size_t)i * kAevLen + c] = __bfloat162float(all[(size_t)rows[i] * kAevLd + c]);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MLP_OK : cuda_error(e, "mlp_debug_aev");
+}
+
+int mlp_debug_atom_energies(mlp_system* s, float* e_out, float* dEdG) {
+    clear_error();
+    if (!s || !e_out) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    cudaStreamSynchronize(s->stream);
+    cudaMemcpy(e_out, s->ws.e, 4 * (size_t)s->n, cudaMemcpyDeviceToHost);
+    if (dEdG) {
+        std::vector<int> rows;
+        rc = atom_rows(s, rows);
+        if (rc) return rc;
+        std::vector<float> all((size_t)s->ws.rows_cap * kAevLd);
+        cudaMemcpy(all.data(), s->ws.dG, 4 * all.size(), cudaMemcpyDeviceToHost);
+        for (int i = 0; i < s->n; ++i)
+            std::memcpy(dEdG + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MLP_OK : cuda_error(e, "mlp_debug_atom_energies");
+}
+
+int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8_t* species, const float* G,
+                      float* e_out, float* dEdG) {
+    clear_error();
+    if (!w || !species || !G || !e_out) return set_error(MLP_EINVAL, "NULL argument");
+    if (n <= 0) return set_error(MLP_EINVAL, "n must be positive");
+    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision");
+    if (precision == MLP_BF16 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    Workspace ws;
+    rc = workspace_create(ws, n, 1, precision, false, 1, 0);
+    if (rc) return rc;
+    // element-grouped rows: stable order inside each element
+    Counters c;
+    std::memset(&c, 0, sizeof(c));
+    std::vector<int> rank(n);
+    for (int i = 0; i < n; ++i) {
+        if (species[i] < 0 || species[i] >= kNSpecies) {
+            workspace_destroy(ws);
+            return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
+        }
+        rank[i] = c.species[species[i]]++;
+    }
+    int base[kNSpecies], b = 0;
+    for (int q = 0; q < kNSpecies; ++q) {
+        base[q] = b;
+        b += (c.species[q] + kTileRows - 1) / kTileRows * kTileRows;
+    }
+    const size_t R = ws.rows_cap;
+    std::vector<int> row_atom(R, 0);
+    std::vector<int> rows(n);
+    for (int i = 0; i < n; ++i) {
+        rows[i] = base[species[i]] + rank[i];
+        row_atom[rows[i]] = i;
+    }
+    cudaMemcpy(ws.ctr, &c, sizeof(c), cudaMemcpyHostToDevice);
+    cudaMemcpy(ws.row_atom, row_atom.data(), 4 * R, cudaMemcpyHostToDevice);
+    if (precision == MLP_FP32) {
+        std::vector<float> all(R * kAevLd, 0.f);
+        for (int i = 0; i < n; ++i) std::memcpy(&all[(size_t)rows[i] * kAevLd], G + (size_t)i * kAevLen, 4 * kAevLen);
+        cudaMemcpy(ws.G32, all.data(), 4 * all.size(), cudaMemcpyHostToDevice);
+        launch_mlp_f32(nullptr, ws.rows_cap, ws.ctr, w->dw.f32[0], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG, true);
+    } else {
+        std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f));
+        for (int i = 0; i < n; ++i)
+            for (int q = 0; q < kAevLen; ++q) all[(size_t)rows[i] * kAevLd + q] = to_bf16(G[(size_t)i * kAevLen + q]);
+        cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
+        launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG, true, ws.tc_err);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(e_out, ws.e, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && dEdG) {
+        std::vector<float> all(R * kAevLd);
+        e = cudaMemcpy(all.data(), ws.dG, 4 * all.size(), cudaMemcpyDeviceToHost);
+        for (int i = 0; i < n; ++i) std::memcpy(dEdG + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
+    }
+    int tc = 0;
+    if (e == cudaSuccess && precision == MLP_BF16) e = cudaMemcpy(&tc, ws.tc_err, 4, cudaMemcpyDeviceToHost);
+    workspace_destroy(ws);
+    if (e != cudaSuccess) return cuda_error(e, "mlp_debug_network");
+    if (tc) return set_error(MLP_ECUDA, "tensor-core kernel reported error %d", tc);
+    return MLP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Kernel launchers of the CUDA path (one evaluation = the launches below on
+// one stream). Every launcher goes through MLP_LAUNCH, which counts launches
+// and, when profiling is on, brackets them with CUDA events on that stream.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mlp {
+
+// ---- launch accounting / per-kernel event timing (runtime.cu)
+void launch_begin(const char* name, cudaStream_t st);
+void launch_end(const char* name, cudaStream_t st);
+void init_constants_for_current_device();
+
+#define MLP_LAUNCH(name, st, ...)            \
+    do {                                     \
+        ::mlp::launch_begin(name, st);       \
+        __VA_ARGS__;                         \
+        ::mlp::launch_end(name, st);         \
+    } while (0)
+
+// ---- staging and neighbor search (kernels_nbr.cu)
+struct NbrArgs {
+    const float4* hi;
+    const float4* lo;
+    int* nbr;        // [n][cap]
+    int* nbr_cnt;    // [n]
+    int cap;
+    float rl2;       // list radius squared
+};
+
+void launch_stage_system(cudaStream_t st, int n, const double* xyz, const int8_t* species, const double* Ld,
+                         int periodic, int want_bbox, float4* hi, float4* lo, int* rank, Counters* ctr,
+                         double* grad, const float4* ref, float half_skin2, int force_rebuild);
+void launch_stage_batch(cudaStream_t st, int n_mols, int n_atoms, const int* mol_start, const double* xyz,
+                        const int8_t* species, float4* hi, float4* lo, int* rank, Counters* ctr, double* grad);
+void launch_nbr_allpairs(cudaStream_t st, int n, int n_mols, const int* mol_start, const NbrArgs& a, Counters* ctr);
+void launch_grid_setup(cudaStream_t st, Counters* ctr, Grid* g, float r_list, int max_cells);
+void launch_cell_build(cudaStream_t st, int n, const float4* hi, const Grid* g, int max_cells, int* cell_of_atom,
+                       int* cell_rank, int* cell_count, int* cell_start, int* cell_atoms, const Counters* ctr);
+void launch_nbr_cell(cudaStream_t st, int n, const NbrArgs& a, const Box& box, const Grid* g,
+                     const int* cell_of_atom, const int* cell_start, const int* cell_atoms, Counters* ctr,
+                     float4* ref);
+
+// ---- AEV forward and AEV backward -> forces (kernels_aev.cu)
+struct AevArgs {
+    int n;
+    const float4* hi;
+    const float4* lo;
+    const int* nbr;
+    const int* nbr_cnt;
+    int cap;
+    Box box;
+    Counters* ctr;
+    const int* rank;
+};
+void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast);
+void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, int* row_atom, bool fast);
+void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, double* grad, bool fast);
+
+// ---- network, FP32 SIMT path (kernels_mlp_f32.cu)
+struct NetF32 {   // device pointers, element-major, one net
+    const float *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;
+    const float *W1t, *W2t, *W3t;   // transposes: [7][1008][256], [7][256][192], [7][192][160]
+};
+struct MlpF32Bufs {
+    float *Z1, *H1, *Z2, *H2, *H3, *G3, *G2, *G1;   // [rows][256|192|160]
+};
+void launch_mlp_f32(cudaStream_t st, int rows_cap, const Counters* ctr, const NetF32& w, const float* G,
+                    const int* row_atom, MlpF32Bufs& b, float* e, float* dG, bool backward);
+
+// ---- network, BF16 tcgen05 path (kernels_mlp_tc.cu)
+struct NetBF16 {
+    const __nv_bfloat16 *W1, *W2, *W3;       // [7][256][1024], [7][192][256], [7][160][192]
+    const __nv_bfloat16 *W1t, *W2t, *W3t;    // [7][1024][256], [7][256][192], [7][192][160]
+    const float *b1, *b2, *b3, *W4, *b4;
+};
+bool mlp_tc_available();
+void launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
+                     const __nv_bfloat16* G, const int* row_atom, float* e, float* dG, bool backward,
+                     int* err_flag);
+
+// ---- finalize (kernels_misc.cu)
+void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
+                     const double* grad, double* E, float* F, const double* grad_scale, float sign);
+
+}  // namespace mlp

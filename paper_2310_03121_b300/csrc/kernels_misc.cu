@@ -1,0 +1,54 @@
+// Final reductions: per-molecule energy E_m = sum_i e_i in FP64 (one block
+// per molecule, fixed reduction tree -> identical result for a molecule
+// evaluated alone or inside any batch), and the FP32 force output
+// F = sign * scale * dE/dr from the FP64 per-atom accumulators.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mlp {
+namespace {
+
+constexpr int kEBlock = 128;
+
+// Blocks [0, n_mols) reduce energies; the remaining blocks convert forces.
+// mol_start == nullptr means one molecule made of all n_atoms atoms.
+__global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_atoms, const float* __restrict__ e,
+                           const double* __restrict__ grad, double* __restrict__ E, float* __restrict__ F,
+                           const double* __restrict__ grad_scale, float sign) {
+    if ((int)blockIdx.x < n_mols) {
+        const int m = blockIdx.x;
+        const int a = mol_start ? mol_start[m] : 0;
+        const int b = mol_start ? mol_start[m + 1] : n_atoms;
+        double acc = 0.0;
+        for (int i = a + threadIdx.x; i < b; i += kEBlock) acc += (double)e[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __shared__ double ws[kEBlock / 32];
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kEBlock / 32; ++q) t += ws[q];
+            if (E) E[m] = t;
+        }
+        return;
+    }
+    const double scale = (grad_scale ? *grad_scale : 1.0) * (double)sign;
+    const int fb = blockIdx.x - n_mols;
+    const int nfb = gridDim.x - n_mols;
+    for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) F[q] = (float)(scale * grad[q]);
+}
+
+}  // namespace
+
+void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
+                     const double* grad, double* E, float* F, const double* grad_scale, float sign) {
+    const int fblocks = F ? (3 * n_atoms + kEBlock * 4 - 1) / (kEBlock * 4) : 0;
+    const int eblocks = E ? n_mols : 0;
+    if (eblocks + fblocks == 0) return;
+    MLP_LAUNCH("finalize", st,
+               k_finalize<<<eblocks + fblocks, kEBlock, 0, st>>>(eblocks, mol_start, n_atoms, e, grad, E, F,
+                                                                 grad_scale, sign));
+}
+
+}  // namespace mlp

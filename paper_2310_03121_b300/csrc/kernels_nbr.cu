@@ -1,0 +1,444 @@
+// Staging and neighbor search.
+//
+// Staging turns FP64 coordinates into split FP32 positions (hi = rounded
+// value, lo = remainder), wraps periodic positions into [0, L), counts atoms
+// per element (the rank of each atom inside its element fixes its row in the
+// element-grouped AEV matrix) and clears the FP64 force accumulators.
+//
+// Neighbor search ("building neighbor lists", paper section "Optimization
+// Through NNPOps") produces a full list: every ordered pair (i, j), j != i,
+// with |d_ij| < r_list, stored per atom in a fixed-capacity row nbr[i][cap]
+// with the true count in nbr_cnt[i] (overflow is reported, never written
+// past the row). Two builders:
+//   * cell list: cells of side >= r_list over the periodic box (minimum
+//     image) or over the bounding box of an open system; one warp per atom
+//     scans the 27 surrounding cells, candidates in cell order and, inside a
+//     cell, in atom order, so the list order is deterministic;
+//   * all pairs inside each molecule, for batches of small open molecules
+//     (the one-cell case of the same search).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mlp {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Order-preserving float -> unsigned key (0 below every float), for atomicMax.
+__device__ __forceinline__ unsigned float_key(float f) {
+    int i = __float_as_int(f);
+    i = i >= 0 ? i : i ^ 0x7fffffff;
+    return (unsigned)i ^ 0x80000000u;
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+    int i = (int)(k ^ 0x80000000u);
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// Warp-aggregated per-element counter: returns the atom's rank in its element.
+__device__ __forceinline__ int element_rank(bool valid, int s, Counters* ctr) {
+    int key = valid ? s : -1;
+    unsigned grp = __match_any_sync(0xffffffffu, key);
+    int leader = __ffs(grp) - 1;
+    int lane = threadIdx.x & 31;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&ctr->species[s], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(grp & lanemask_lt());
+}
+
+__device__ __forceinline__ void split(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// Persistent lists: ref holds the positions of the last rebuild; an atom that
+// moved more than half the skin since then (or force_rebuild) sets
+// ctr->rebuild, and the cell/neighbor kernels of this evaluation run in full.
+__global__ void k_stage_system(int n, const double* __restrict__ xyz, const int8_t* __restrict__ species,
+                               double L0, double L1, double L2, int periodic, int want_bbox,
+                               float4* __restrict__ hi, float4* __restrict__ lo, int* __restrict__ rank,
+                               Counters* ctr, double* __restrict__ grad, const float4* __restrict__ ref,
+                               float half_skin2, int force_rebuild) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = i < n;
+    if (force_rebuild && i == 0) ctr->rebuild = 1;
+    int s = 0;
+    float hx = 0.f, hy = 0.f, hz = 0.f;
+    if (valid) {
+        double x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+        if (periodic) {
+            x -= L0 * floor(x / L0);
+            y -= L1 * floor(y / L1);
+            z -= L2 * floor(z / L2);
+        }
+        float lx, ly, lz;
+        split(x, hx, lx);
+        split(y, hy, ly);
+        split(z, hz, lz);
+        s = species[i];
+        if (s < 0 || s >= kNSpecies) {
+            atomicOr(&ctr->bad_species, 1);   // invalid element code: reported by the host
+            s = 0;
+        }
+        hi[i] = make_float4(hx, hy, hz, __int_as_float(s));
+        lo[i] = make_float4(lx, ly, lz, __int_as_float(0));
+        grad[3 * (size_t)i] = 0.0;
+        grad[3 * (size_t)i + 1] = 0.0;
+        grad[3 * (size_t)i + 2] = 0.0;
+        if (!force_rebuild && half_skin2 > 0.f) {
+            float4 p = ref[i];
+            float dx = hx - p.x, dy = hy - p.y, dz = hz - p.z;
+            if (periodic) {
+                dx -= (float)L0 * rintf(dx / (float)L0);
+                dy -= (float)L1 * rintf(dy / (float)L1);
+                dz -= (float)L2 * rintf(dz / (float)L2);
+            }
+            if (dx * dx + dy * dy + dz * dz > half_skin2) atomicOr(&ctr->rebuild, 1);
+        }
+    }
+    int r = element_rank(valid, s, ctr);
+    if (valid) rank[i] = r;
+    if (want_bbox) {
+        float mn[3] = {valid ? hx : 3.0e38f, valid ? hy : 3.0e38f, valid ? hz : 3.0e38f};
+        float mx[3] = {valid ? hx : -3.0e38f, valid ? hy : -3.0e38f, valid ? hz : -3.0e38f};
+        for (int a = 0; a < 3; ++a) {
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+                mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            for (int a = 0; a < 3; ++a) {
+                atomicMax(&ctr->bbox_negmin_key[a], float_key(-mn[a]));
+                atomicMax(&ctr->bbox_max_key[a], float_key(mx[a]));
+            }
+        }
+    }
+}
+
+// One block per molecule: atoms mol_start[m] .. mol_start[m+1]; lo.w = m.
+// Molecule bounds outside [0, n_atoms] (device input) are flagged as bad
+// input and skipped; the host then reports the evaluation invalid.
+__global__ void k_stage_batch(int n_mols, int n_atoms, const int* __restrict__ mol_start,
+                              const double* __restrict__ xyz, const int8_t* __restrict__ species,
+                              float4* __restrict__ hi, float4* __restrict__ lo, int* __restrict__ rank,
+                              Counters* ctr, double* __restrict__ grad) {
+    int m = blockIdx.x;
+    int a = mol_start[m], b = mol_start[m + 1];
+    if (m == 0 && threadIdx.x == 0 && (a != 0 || mol_start[n_mols] != n_atoms)) atomicOr(&ctr->bad_species, 2);
+    if (a < 0 || b < a || b > n_atoms) {
+        if (threadIdx.x == 0) atomicOr(&ctr->bad_species, 2);
+        return;
+    }
+    for (int base = a; base < b; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        bool valid = i < b;
+        int s = 0;
+        if (valid) {
+            float hx, hy, hz, lx, ly, lz;
+            split(xyz[3 * (size_t)i], hx, lx);
+            split(xyz[3 * (size_t)i + 1], hy, ly);
+            split(xyz[3 * (size_t)i + 2], hz, lz);
+            s = species[i];
+            if (s < 0 || s >= kNSpecies) {
+                atomicOr(&ctr->bad_species, 1);
+                s = 0;
+            }
+            hi[i] = make_float4(hx, hy, hz, __int_as_float(s));
+            lo[i] = make_float4(lx, ly, lz, __int_as_float(m));
+            grad[3 * (size_t)i] = 0.0;
+            grad[3 * (size_t)i + 1] = 0.0;
+            grad[3 * (size_t)i + 2] = 0.0;
+        }
+        int r = element_rank(valid, s, ctr);
+        if (valid) rank[i] = r;
+    }
+}
+
+// Warp per atom: every j of the atom's molecule.
+__global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_start, NbrArgs a, Counters* ctr) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    int i = warp;
+    float4 hi_i = a.hi[i], lo_i = a.lo[i];
+    int m = __float_as_int(lo_i.w);
+    int beg = 0, end = 0;
+    if (m >= 0 && m < n_mols) {
+        beg = mol_start[m];
+        end = mol_start[m + 1];
+    }
+    if (beg < 0 || end > n || beg > end || i < beg || i >= end) {
+        // atom not covered by a valid molecule (bad device input, already flagged)
+        beg = end = 0;
+    }
+    Box box{};
+    int count = 0;
+    int* row = a.nbr + (size_t)i * a.cap;
+    for (int base = beg; base < end; base += 32) {
+        int j = base + lane;
+        bool ok = false;
+        if (j < end && j != i) {
+            float3 d = displacement(hi_i, lo_i, a.hi[j], a.lo[j], box);
+            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        int pos = count + __popc(mask & lanemask_lt());
+        if (ok && pos < a.cap) row[pos] = j;
+        count += __popc(mask);
+    }
+    if (lane == 0) {
+        a.nbr_cnt[i] = count;
+        if (count > a.cap) atomicMax(&ctr->nbr_overflow, count);
+    }
+}
+
+// Grid over the bounding box of an open system (single thread).
+__global__ void k_grid_setup(Counters* ctr, Grid* g, float r_list, int max_cells) {
+    if (!ctr->rebuild) return;
+    float mn[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = -key_float(ctr->bbox_negmin_key[a]);
+        float mx = key_float(ctr->bbox_max_key[a]);
+        ext[a] = fmaxf(mx - mn[a], 0.f) + 2e-3f;
+        mn[a] -= 1e-3f;
+    }
+    float cs = r_list;
+    int nc[3] = {1, 1, 1};
+    bool fits = false;
+    for (int it = 0; it < 96 && !fits; ++it) {
+        long long tot = 1;
+        for (int a = 0; a < 3; ++a) {
+            float f = floorf(ext[a] / cs);
+            nc[a] = (f >= 1.f && f < 1.0e6f) ? (int)f : (f >= 1.0e6f ? 1000000 : 1);
+            tot *= nc[a];
+        }
+        fits = tot <= max_cells;
+        if (!fits) cs *= 1.25f;
+    }
+    if (!fits) nc[0] = nc[1] = nc[2] = 1;   // degenerate input: one cell, still exact
+    for (int a = 0; a < 3; ++a) {
+        g->nc[a] = nc[a];
+        g->origin[a] = mn[a];
+        // cells are at least r_list wide: ext / nc >= cs >= r_list
+        g->inv_cs[a] = (float)nc[a] / ext[a];
+    }
+    g->ncell = nc[0] * nc[1] * nc[2];
+}
+
+__device__ __forceinline__ int cell_coord(float x, float origin, float inv_cs, int nc) {
+    int c = (int)floorf((x - origin) * inv_cs);
+    return min(max(c, 0), nc - 1);
+}
+
+__global__ void k_cell_count(int n, const float4* __restrict__ hi, const Grid* __restrict__ g,
+                             int* __restrict__ cell_of_atom, int* __restrict__ cell_rank,
+                             int* __restrict__ cell_count, const Counters* __restrict__ ctr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !ctr->rebuild) return;
+    float4 p = hi[i];
+    int cx = cell_coord(p.x, g->origin[0], g->inv_cs[0], g->nc[0]);
+    int cy = cell_coord(p.y, g->origin[1], g->inv_cs[1], g->nc[1]);
+    int cz = cell_coord(p.z, g->origin[2], g->inv_cs[2], g->nc[2]);
+    int c = (cz * g->nc[1] + cy) * g->nc[0] + cx;
+    cell_of_atom[i] = c;
+    cell_rank[i] = atomicAdd(&cell_count[c], 1);
+}
+
+// Exclusive scan of the cell counts (one block of 1024 threads).
+__global__ void k_cell_scan(const Grid* __restrict__ g, const int* __restrict__ cell_count,
+                            int* __restrict__ cell_start, const Counters* __restrict__ ctr) {
+    if (!ctr->rebuild) return;
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    int ncell = g->ncell;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < ncell; base += 1024) {
+        int c = base + threadIdx.x;
+        int v = c < ncell ? cell_count[c] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        int incl = x + (w > 0 ? warp_sums[w - 1] : 0) + carry;
+        if (c < ncell) cell_start[c] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cell_start[ncell] = carry;
+}
+
+__global__ void k_cell_scatter(int n, const int* __restrict__ cell_of_atom, const int* __restrict__ cell_rank,
+                               const int* __restrict__ cell_start, int* __restrict__ cell_atoms,
+                               const Counters* __restrict__ ctr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !ctr->rebuild) return;
+    cell_atoms[cell_start[cell_of_atom[i]] + cell_rank[i]] = i;
+}
+
+// Insertion sort of each cell's atoms by index, so that the neighbor order
+// does not depend on the order of the counting atomics.
+__global__ void k_cell_sort(const Grid* __restrict__ g, const int* __restrict__ cell_start,
+                            int* __restrict__ cell_atoms, const Counters* __restrict__ ctr) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!ctr->rebuild || c >= g->ncell) return;
+    int a = cell_start[c], b = cell_start[c + 1];
+    for (int p = a + 1; p < b; ++p) {
+        int v = cell_atoms[p];
+        int q = p - 1;
+        while (q >= a && cell_atoms[q] > v) {
+            cell_atoms[q + 1] = cell_atoms[q];
+            --q;
+        }
+        cell_atoms[q + 1] = v;
+    }
+}
+
+__global__ void k_nbr_cell(int n, NbrArgs a, Box box, const Grid* __restrict__ g,
+                           const int* __restrict__ cell_of_atom, const int* __restrict__ cell_start,
+                           const int* __restrict__ cell_atoms, Counters* ctr, float4* __restrict__ ref) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n || !ctr->rebuild) return;
+    int i = warp;
+    float4 hi_i = a.hi[i], lo_i = a.lo[i];
+    if (lane == 0) ref[i] = hi_i;
+    int nc0 = g->nc[0], nc1 = g->nc[1], nc2 = g->nc[2];
+    int c = cell_of_atom[i];
+    int cx = c % nc0, cy = (c / nc0) % nc1, cz = c / (nc0 * nc1);
+    int count = 0;
+    int* row = a.nbr + (size_t)i * a.cap;
+    // per axis: three relative cells, or (periodic box with fewer than three
+    // cells along the axis) every cell once
+    int lo3[3], hi3[3], rel[3];
+    const int ncs[3] = {nc0, nc1, nc2};
+    for (int ax = 0; ax < 3; ++ax) {
+        if (box.periodic && ncs[ax] < 3) {
+            lo3[ax] = 0;
+            hi3[ax] = ncs[ax] - 1;
+            rel[ax] = 0;
+        } else {
+            lo3[ax] = -1;
+            hi3[ax] = 1;
+            rel[ax] = 1;
+        }
+    }
+    const int cc[3] = {cx, cy, cz};
+    for (int oz = lo3[2]; oz <= hi3[2]; ++oz) {
+        int z = rel[2] ? cc[2] + oz : oz;
+        if (rel[2]) {
+            if (box.periodic) z = (z + nc2) % nc2;
+            else if (z < 0 || z >= nc2) continue;
+        }
+        for (int oy = lo3[1]; oy <= hi3[1]; ++oy) {
+            int y = rel[1] ? cc[1] + oy : oy;
+            if (rel[1]) {
+                if (box.periodic) y = (y + nc1) % nc1;
+                else if (y < 0 || y >= nc1) continue;
+            }
+            for (int ox = lo3[0]; ox <= hi3[0]; ++ox) {
+                int x = rel[0] ? cc[0] + ox : ox;
+                if (rel[0]) {
+                    if (box.periodic) x = (x + nc0) % nc0;
+                    else if (x < 0 || x >= nc0) continue;
+                }
+                int cell = (z * nc1 + y) * nc0 + x;
+                int beg = cell_start[cell], end = cell_start[cell + 1];
+                for (int base = beg; base < end; base += 32) {
+                    int q = base + lane;
+                    bool ok = false;
+                    int j = -1;
+                    if (q < end) {
+                        j = cell_atoms[q];
+                        if (j != i) {
+                            float3 d = displacement(hi_i, lo_i, a.hi[j], a.lo[j], box);
+                            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+                        }
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, ok);
+                    int pos = count + __popc(mask & lanemask_lt());
+                    if (ok && pos < a.cap) row[pos] = j;
+                    count += __popc(mask);
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        a.nbr_cnt[i] = count;
+        if (count > a.cap) atomicMax(&ctr->nbr_overflow, count);
+    }
+}
+
+}  // namespace
+
+void launch_stage_system(cudaStream_t st, int n, const double* xyz, const int8_t* species, const double* Ld,
+                         int periodic, int want_bbox, float4* hi, float4* lo, int* rank, Counters* ctr,
+                         double* grad, const float4* ref, float half_skin2, int force_rebuild) {
+    int bs = 256, gs = (n + bs - 1) / bs;
+    MLP_LAUNCH("stage", st,
+               k_stage_system<<<gs, bs, 0, st>>>(n, xyz, species, Ld[0], Ld[1], Ld[2], periodic, want_bbox, hi,
+                                                 lo, rank, ctr, grad, ref, half_skin2, force_rebuild));
+}
+
+void launch_stage_batch(cudaStream_t st, int n_mols, int n_atoms, const int* mol_start, const double* xyz,
+                        const int8_t* species, float4* hi, float4* lo, int* rank, Counters* ctr, double* grad) {
+    MLP_LAUNCH("stage", st,
+               k_stage_batch<<<n_mols, 128, 0, st>>>(n_mols, n_atoms, mol_start, xyz, species, hi, lo, rank, ctr,
+                                                     grad));
+}
+
+void launch_nbr_allpairs(cudaStream_t st, int n, int n_mols, const int* mol_start, const NbrArgs& a, Counters* ctr) {
+    int warps_per_block = 8;
+    int gs = (n + warps_per_block - 1) / warps_per_block;
+    MLP_LAUNCH("neighbors_allpairs", st,
+               k_nbr_allpairs<<<gs, 32 * warps_per_block, 0, st>>>(n, n_mols, mol_start, a, ctr));
+}
+
+void launch_grid_setup(cudaStream_t st, Counters* ctr, Grid* g, float r_list, int max_cells) {
+    MLP_LAUNCH("grid_setup", st, k_grid_setup<<<1, 1, 0, st>>>(ctr, g, r_list, max_cells));
+}
+
+void launch_cell_build(cudaStream_t st, int n, const float4* hi, const Grid* g, int max_cells, int* cell_of_atom,
+                       int* cell_rank, int* cell_count, int* cell_start, int* cell_atoms, const Counters* ctr) {
+    int bs = 256, gs = (n + bs - 1) / bs;
+    MLP_LAUNCH("cell_count", st,
+               k_cell_count<<<gs, bs, 0, st>>>(n, hi, g, cell_of_atom, cell_rank, cell_count, ctr));
+    MLP_LAUNCH("cell_scan", st, k_cell_scan<<<1, 1024, 0, st>>>(g, cell_count, cell_start, ctr));
+    MLP_LAUNCH("cell_scatter", st,
+               k_cell_scatter<<<gs, bs, 0, st>>>(n, cell_of_atom, cell_rank, cell_start, cell_atoms, ctr));
+    MLP_LAUNCH("cell_sort", st,
+               k_cell_sort<<<(max_cells + 255) / 256, 256, 0, st>>>(g, cell_start, cell_atoms, ctr));
+}
+
+void launch_nbr_cell(cudaStream_t st, int n, const NbrArgs& a, const Box& box, const Grid* g,
+                     const int* cell_of_atom, const int* cell_start, const int* cell_atoms, Counters* ctr,
+                     float4* ref) {
+    int warps_per_block = 8;
+    int gs = (n + warps_per_block - 1) / warps_per_block;
+    MLP_LAUNCH("neighbors_cell", st,
+               k_nbr_cell<<<gs, 32 * warps_per_block, 0, st>>>(n, a, box, g, cell_of_atom, cell_start, cell_atoms,
+                                                               ctr, ref));
+}
+
+}  // namespace mlp

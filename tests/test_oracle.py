@@ -365,3 +365,13 @@ def test_golden_config0(W):
     assert E == pytest.approx(g["energy"], rel=1e-13)
     np.testing.assert_allclose(e, g["atom_energies"], rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(F, g["forces"], rtol=1e-11, atol=1e-15)
+
+
+def test_parallel_atom_energies_equal_serial(W):
+    c = gen.make_config(1)
+    E, e = oracle.energy(c.species, c.coords, None, W, per_atom=True)
+    e2 = oracle.atom_energies(c.species, c.coords, None, W, nthreads=4)
+    np.testing.assert_array_equal(e2, e)
+    G = oracle.aev(c.species, c.coords)
+    idx = [3, 100, 671]
+    np.testing.assert_array_equal(oracle.aev_subset(c.species, c.coords, None, idx), G[idx])
