@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: atom energy+force evaluations per second of the served path.
+
+Workload: the served stream of 20,000 independent open-boundary molecules,
+N log-uniform in [8, 256] atoms (1,426,039 atoms in total, seeded synthetic
+geometries at 0.111 atoms/A^3, drug-like element mix, random-init
+ANI-2x-shaped weights). One step evaluates every molecule once: the stream is
+packed, oldest first, into device batches of at most 131,072 atoms / 4,096
+molecules (the serving loop's packing) and the batches run on two CUDA
+streams, two in flight, as the server's two slots do.
+
+value  device-resident inputs (all coordinates in HBM before the timed
+       region), CUDA-event time per step, L2 flushed between steps.
+e2e    the same stream through the C-ABI server (mlp_server_replay: host
+       coordinates in, host energies and forces out, every request queued at
+       t = 0), wall time; p50/p99 request latency of that run.
+Also reported: Poisson-arrival latency sweep, the one-molecule-per-launch
+FP32 path, the roofline of the dominant kernel and the FP64 oracle on the
+host cores (cpu_baseline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom energy+force evals/s (served BF16 vs plain FP32, same GPU); p50/p99 latency"
+UNIT = "atom-evals/s"
+WORKLOAD = ("served stream: 20,000 open-boundary molecules, N log-uniform in [8, 256] (1,426,039 atoms), "
+            "ANI-2x-shaped network 1008-256-192-160-1 x 7 elements")
+
+# Algorithmic work per atom of each kernel (measurement section).
+MLP_FLOP_FWD = 2 * (1008 * 256 + 256 * 192 + 192 * 160 + 160)          # 676,160
+MLP_FLOP_BWD = 2 * (160 * 192 + 192 * 256 + 256 * 1008)                 # 675,840
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.05)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+        "fallback"
+
+
+def pack_chunks(mol_start, max_atoms, max_mols):
+    """Oldest-first packing of consecutive molecules into batches."""
+    chunks = []
+    m0 = 0
+    M = len(mol_start) - 1
+    while m0 < M:
+        m1 = m0
+        while m1 < M and (mol_start[m1 + 1] - mol_start[m0]) <= max_atoms and (m1 - m0) < max_mols:
+            m1 += 1
+        chunks.append((m0, m1))
+        m0 = m1
+    return chunks
+
+
+def cpu_baseline(stream, wts, seconds, nthreads=None):
+    """FP64 oracle on the host cores: a bounded sample of the served stream."""
+    import oracle
+
+    OW = oracle.Weights(wts)
+    nthreads = nthreads or os.cpu_count() or 1
+    # calibrate on a small prefix, then size the sample to ~`seconds`
+    m_cal = min(nthreads * 2, stream.count)
+    t0 = time.perf_counter()
+    oracle.energy_forces_batch(stream.mol_start[: m_cal + 1], stream.species[: stream.mol_start[m_cal]],
+                               stream.coords[: stream.mol_start[m_cal]], OW, nthreads=nthreads)
+    t_cal = time.perf_counter() - t0
+    atoms_cal = int(stream.mol_start[m_cal])
+    rate = atoms_cal / max(t_cal, 1e-9)
+    target_atoms = rate * seconds
+    m = int(np.searchsorted(stream.mol_start, target_atoms))
+    m = max(m_cal, min(m, stream.count))
+    t0 = time.perf_counter()
+    oracle.energy_forces_batch(stream.mol_start[: m + 1], stream.species[: stream.mol_start[m]],
+                               stream.coords[: stream.mol_start[m]], OW, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    atoms = int(stream.mol_start[m])
+    return {"value": atoms / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"first {m} molecules ({atoms} atoms) of the served stream, FP64 oracle "
+                      f"(brute-force neighbors, loop AEV, naive network, analytic forces), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import gen
+
+    stream = gen.served_stream(args.count)
+    wts = gen.make_weights()
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    vals = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(stream, wts, budget if i >= args.warmup else min(budget, 2.0))
+        if i >= args.warmup:
+            vals.append(cb["value"])
+            base = cb
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded per-step sample, see cpu_baseline"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import gen
+    import paper_2310_03121_b300 as P
+
+    prec = args.precision
+    stream = gen.served_stream(args.count)
+    wts = gen.make_weights()
+    W = P.Weights(wts)
+    n_atoms = stream.n_atoms
+    max_atoms, max_mols = args.max_batch_atoms, args.max_batch_mols
+    chunks = pack_chunks(stream.mol_start, max_atoms, max_mols)
+
+    # device-resident inputs and outputs
+    d_xyz = torch.from_numpy(stream.coords).to(dev)
+    d_sp = torch.from_numpy(stream.species).to(dev)
+    d_E = torch.zeros(stream.count, dtype=torch.float64, device=dev)
+    d_F = torch.zeros((n_atoms, 3), dtype=torch.float32, device=dev)
+    chunk_ms = []
+    for (m0, m1) in chunks:
+        a0 = int(stream.mol_start[m0])
+        ms = (stream.mol_start[m0:m1 + 1] - a0).astype(np.int32)
+        chunk_ms.append(torch.from_numpy(ms).to(dev))
+    batches = [P.Batch(W, precision=prec, max_atoms=max_atoms, max_mols=max_mols) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(one_stream=False):
+        start = torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        start.record(cur)
+        for s in streams:
+            s.wait_event(start)
+        for k, (m0, m1) in enumerate(chunks):
+            a0, a1 = int(stream.mol_start[m0]), int(stream.mol_start[m1])
+            b = batches[k & 1]
+            st = streams[0 if one_stream else (k & 1)]
+            b.run_device(m1 - m0, a1 - a0, chunk_ms[k], d_sp[a0:a1], d_xyz[a0:a1], d_E[m0:m1], d_F[a0:a1],
+                         stream=st)
+        ends = []
+        for s in streams:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(s)
+            ends.append(e)
+        for e in ends:
+            cur.wait_event(e)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record(cur)
+        return start, end
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+        for b in batches:
+            b.sync()
+    barrier()
+    launches0 = P.launch_count()
+    clk = Clocks(local)
+    clk.start()
+    times = []
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the events)
+        torch.cuda.synchronize()
+        s_ev, e_ev = step()
+        torch.cuda.synchronize()
+        for b in batches:
+            b.sync()
+        times.append(s_ev.elapsed_time(e_ev))
+    barrier()
+    clocks = clk.stop()
+    launches = P.launch_count() - launches0
+    # per-kernel durations: the same step on one stream (so that an event pair
+    # brackets exactly one kernel), CUDA events around every launch
+    P.profile_reset()
+    P.profile_enable(True)
+    for _ in range(args.profile_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step(one_stream=True)
+        torch.cuda.synchronize()
+        for b in batches:
+            b.sync()
+    P.profile_enable(False)
+    prof = P.profile_read()
+    ms_step = float(np.mean(times))
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * n_atoms / (ms_step * 1e-3)
+
+    # sanity: outputs finite
+    assert torch.isfinite(d_E).all() and torch.isfinite(d_F).all()
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "precision": prec, "molecules": stream.count, "atoms": n_atoms,
+                         "batch_atoms": max_atoms, "batches_per_step": len(chunks), "streams": 2,
+                         "l2": "flushed between timed steps (256 MB write)",
+                         "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+              "clocks": clocks, "gpu_launches": int(round(launches / max(1, args.steps)))}
+    result["gpu_launches_timed_total"] = int(launches)
+    result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec)
+    result["kernels_ms_per_step"] = {k: v[0] / max(1, args.profile_steps) for k, v in sorted(prof.items())}
+    result["kernels_timing"] = ("CUDA events around every launch, on the launching stream, in "
+                                f"{args.profile_steps} extra steps run on one stream after the timed steps")
+
+    # ---------------- e2e through the server (host buffers), saturating arrivals
+    if not args.no_e2e:
+        srv = P.Server(W, precision=prec, max_batch_atoms=max_atoms, max_batch_mols=max_mols, streams=2)
+        arr = np.zeros(stream.count, dtype=np.int64)
+        walls = []
+        lat = None
+        for i in range(1 + max(1, min(3, args.steps))):
+            E, F, wall = srv.replay(arr, stream.mol_start, stream.species, stream.coords)
+            lt = srv.latencies()
+            if i > 0:                       # the first run warms the server up
+                walls.append(wall)
+                lat = lt
+        wall = statistics.median(walls)
+        h2d = 24 * n_atoms + n_atoms + 4 * (stream.count + len(chunks))
+        d2h = 12 * n_atoms + 8 * stream.count
+        result["e2e"] = {"value": ws * n_atoms / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h, "wall_s": wall,
+                         "latency_ms": {"p50": float(np.percentile(lat, 50)) * 1e-6,
+                                        "p99": float(np.percentile(lat, 99)) * 1e-6},
+                         "path": "mlp_server_replay, all 20,000 requests queued at t=0"}
+        if not args.no_sweep and rank == 0:
+            result["latency_sweep"] = sweep(srv, stream, args)
+        srv.close()
+
+    # ---------------- plain FP32, one molecule per launch
+    if not args.no_plain and rank == 0:
+        result["plain_fp32"] = plain_fp32(P, W, stream, args)
+
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(stream, wts, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(prof, n_atoms, steps, prec):
+    peaks, src = measured_peaks()
+    if not prof:
+        return None
+    name, (tot_ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = tot_ms / max(1, cnt)
+    launches_per_step = cnt / max(1, steps)
+    atoms_per_launch = n_atoms / max(1e-9, launches_per_step)
+    sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    if name.startswith("mlp_tc"):
+        flop = (MLP_FLOP_FWD + MLP_FLOP_BWD) * atoms_per_launch
+        ach = flop / (avg_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside a long step",
+                "work": "1,351,680 FLOP per atom (network forward + backward)"}
+    if name.startswith("mlp_f32"):
+        # each FP32 GEMM launch: its own share of the 1.35 MFLOP per atom
+        layer_flop = {"mlp_f32_l1": 2 * 1008 * 256, "mlp_f32_l2": 2 * 256 * 192, "mlp_f32_l3": 2 * 192 * 160,
+                      "mlp_f32_b3": 2 * 160 * 192, "mlp_f32_b2": 2 * 192 * 256, "mlp_f32_b1": 2 * 256 * 1008}
+        flop = layer_flop.get(name, 0) * atoms_per_launch
+        ach = flop / (avg_ms * 1e-3) / 1e12
+        peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock"}
+    # AEV / forces: plain FP32 ALU + MUFU; report issue-limited FP32 rate
+    per_atom = {"aev": 36000.0, "forces": 72000.0}.get(name, 0.0)
+    ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
+    peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": "FP32 FMA peak from unit counts and max SM clock",
+            "work": f"{per_atom:.0f} FP32 FLOP per atom (estimate at water density)"}
+
+
+def sweep(srv, stream, args):
+    out = []
+    rng = np.random.default_rng(7)
+    for lam in (1000, 2000, 5000, 10000, 20000, 50000):
+        n = int(min(stream.count, max(200, lam * args.sweep_seconds)))
+        gaps = rng.exponential(1.0 / lam, size=n)
+        arr = (np.cumsum(gaps) * 1e9).astype(np.int64)
+        ms = stream.mol_start[: n + 1]
+        E, F, wall = srv.replay(arr, ms, stream.species[: ms[-1]], stream.coords[: ms[-1]], forces=True)
+        lt = srv.latencies()
+        out.append({"rate_req_s": lam, "requests": n, "atoms_per_s": float(ms[-1] / wall),
+                    "p50_ms": float(np.percentile(lt, 50)) * 1e-6, "p99_ms": float(np.percentile(lt, 99)) * 1e-6})
+    return out
+
+
+def plain_fp32(P, W, stream, args):
+    """One molecule per launch sequence, FP32 network, synchronous host calls."""
+    b = P.Batch(W, precision="fp32", max_atoms=256, max_mols=1, max_atoms_per_mol=256)
+    lat = []
+    atoms = 0
+    t_end = time.perf_counter() + args.plain_seconds
+    m = 0
+    t0 = time.perf_counter()
+    while m < stream.count and (time.perf_counter() < t_end or m < 50):
+        a, z = int(stream.mol_start[m]), int(stream.mol_start[m + 1])
+        t1 = time.perf_counter()
+        b.run(np.array([0, z - a], dtype=np.int32), stream.species[a:z], stream.coords[a:z])
+        lat.append(time.perf_counter() - t1)
+        atoms += z - a
+        m += 1
+    dt = time.perf_counter() - t0
+    b.close()
+    return {"value": atoms / dt, "unit": UNIT, "molecules": m, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+            "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+            "path": "mlp_batch_run with one molecule per call (host buffers, synchronous)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--count", type=int, default=20000)
+    ap.add_argument("--max-batch-atoms", type=int, default=131072)
+    ap.add_argument("--max-batch-mols", type=int, default=4096)
+    ap.add_argument("--sweep-seconds", type=float, default=1.0)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--plain-seconds", type=float, default=3.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -302,6 +302,10 @@ int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out)
         nb.b3 = nf.b3;
         nb.W4 = nf.W4;
         nb.b4 = nf.b4;
+        if (!make_weight_maps(nb)) {
+            mlp_weights_destroy(mw);
+            return set_error(MLP_ECUDA, "TMA tensor map creation for the weights failed");
+        }
     }
     *out = mw;
     return MLP_OK;
@@ -775,7 +779,11 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         for (int i = 0; i < n; ++i)
             for (int q = 0; q < kAevLen; ++q) all[(size_t)rows[i] * kAevLd + q] = to_bf16(G[(size_t)i * kAevLen + q]);
         cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
-        launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG, true, ws.tc_err);
+        if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG, true,
+                             ws.tc_err)) {
+            workspace_destroy(ws);
+            return MLP_ECUDA;
+        }
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(e_out, ws.e, 4 * (size_t)n, cudaMemcpyDeviceToHost);

@@ -208,8 +208,9 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
                        sp.network_backward);
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
-        launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG, sp.network_backward,
-                        ws.tc_err);
+        if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG,
+                             sp.network_backward, ws.tc_err))
+            return -5;
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.grad, fast);
     launch_finalize(st, sp.n_mols, sp.d_mol_start, n, ws.e, ws.grad, sp.energy ? sp.d_E : nullptr,

@@ -3,6 +3,7 @@
 // and, when profiling is on, brackets them with CUDA events on that stream.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -77,9 +78,13 @@ struct NetBF16 {
     const __nv_bfloat16 *W1, *W2, *W3;       // [7][256][1024], [7][192][256], [7][160][192]
     const __nv_bfloat16 *W1t, *W2t, *W3t;    // [7][1024][256], [7][256][192], [7][192][160]
     const float *b1, *b2, *b3, *W4, *b4;
+    // TMA descriptors of the six weight matrices (built once per weight set)
+    CUtensorMap tmW1, tmW2, tmW3, tmW1t, tmW2t, tmW3t;
+    bool maps_ok;
 };
 bool mlp_tc_available();
-void launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
+bool make_weight_maps(NetBF16& w);
+bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
                      const __nv_bfloat16* G, const int* row_atom, float* e, float* dG, bool backward,
                      int* err_flag);
 

@@ -232,3 +232,93 @@ def test_allocation_failure_is_reported(P, W):
     assert ei.value.code == _lib.MLP_ENOMEM
     s = P.System(W, c.species, c.coords, None)   # the next one works
     s.energy_forces()
+
+
+# ------------------------------------------------------------------ BF16 tensor-core network
+E_REL_BF16 = 1e-3
+F_RMS_BF16 = 2e-2
+
+
+def _bf16(x):
+    return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def _emulate_bf16_network(wts, sp, G):
+    """The tensor-core kernel's arithmetic in float64: BF16 operands (G, W,
+    stored activations), exact products, FP32-level accumulation, celu'(z)
+    recovered from the stored BF16 activation."""
+    e = np.zeros(len(sp))
+    g = np.zeros((len(sp), 1008))
+    for s in range(7):
+        idx = np.nonzero(sp == s)[0]
+        if idx.size == 0:
+            continue
+        W1, W2, W3 = (_bf16(wts[k][s]) for k in ("W1", "W2", "W3"))
+        b1, b2, b3, w4 = (torch.as_tensor(wts[k][s], dtype=torch.float32).double() for k in ("b1", "b2", "b3", "W4"))
+        b4 = float(np.float32(wts["b4"][s]))
+        A = _bf16(G[idx])
+        cel = lambda z: torch.where(z > 0, z, 0.1 * (torch.exp(z / 0.1) - 1))
+        dcel = lambda h: torch.where(h > 0, torch.ones_like(h), h / 0.1 + 1)
+        h1 = _bf16(cel(A @ W1.T + b1))
+        h2 = _bf16(cel(h1 @ W2.T + b2))
+        z3 = h2 @ W3.T + b3
+        e[idx] = (cel(z3) @ w4 + b4).numpy()
+        g3 = _bf16(w4 * torch.where(z3 > 0, torch.ones_like(z3), torch.exp(z3 / 0.1)))
+        g2 = _bf16((g3 @ W3) * dcel(h2))
+        g1 = _bf16((g2 @ W2) * dcel(h1))
+        g[idx] = (g1 @ W1).numpy()
+    return e, g
+
+
+@pytest.mark.parametrize("n", [1, 129, 400])
+def test_network_bf16_matches_emulation(P, W, wts, n):
+    rng = np.random.default_rng(100 + n)
+    c = gen.make_config(1)
+    G_all = oracle.aev(c.species, c.coords)
+    pick = rng.choice(c.n, size=n, replace=n > c.n)
+    sp = c.species[pick].copy()
+    sp[: min(n, 7)] = np.arange(min(n, 7))
+    G = G_all[pick].astype(np.float32)
+    e, g = P.debug_network(W, "bf16", sp, G)
+    e_ref, g_ref = _emulate_bf16_network(wts, sp, G)
+    # remaining differences: FP32 accumulation order and BF16 re-rounding of
+    # activations that sit on a rounding boundary
+    assert np.abs(e - e_ref).max() <= 2e-3 * max(1.0, np.abs(e_ref).max()), np.abs(e - e_ref).max()
+    assert np.abs(g - g_ref).max() <= 2e-2 * np.abs(g_ref).max(), (np.abs(g - g_ref).max(), np.abs(g_ref).max())
+    assert np.sqrt(np.mean((g - g_ref) ** 2)) <= 2e-3 * np.sqrt(np.mean(g_ref ** 2))
+
+
+def _check_bf16(E, F, E_ref, F_ref):
+    assert abs(E - E_ref) <= E_REL_BF16 * abs(E_ref), (E, E_ref, abs(E - E_ref) / abs(E_ref))
+    rms = float(np.sqrt(np.mean((F - F_ref) ** 2)))
+    assert rms <= F_RMS_BF16, rms
+
+
+@pytest.mark.parametrize("case", ["config0", "config1", "box300"])
+def test_energy_forces_bf16(P, W, OW, case):
+    c = CASES[case]()
+    E_ref, F_ref = oracle.energy_forces(c.species, c.coords, c.cell, OW)
+    s = P.System(W, c.species, c.coords, c.cell, precision="bf16")
+    E, F = s.energy_forces()
+    _check_bf16(E, F, E_ref, F_ref)
+
+
+@pytest.mark.parametrize("case", ["config2", "config4"])
+def test_energy_forces_bf16_full_size(P, W, OW, case):
+    c = CASES[case]()
+    s = P.System(W, c.species, c.coords, c.cell, precision="bf16")
+    E, F = s.energy_forces()
+    E_ref = float(np.sum(oracle.atom_energies(c.species, c.coords, c.cell, OW)))
+    idx = np.random.default_rng(3).choice(c.n, 48, replace=False)
+    F_ref = oracle.forces_subset(c.species, c.coords, c.cell, OW, idx)
+    _check_bf16(E, F[idx], E_ref, F_ref)
+
+
+def test_batch_bf16_matches_oracle(P, W, OW):
+    st = gen.served_stream(count=300)
+    b = P.Batch(W, precision="bf16", max_atoms=st.n_atoms, max_mols=300)
+    E, F = b.run(st.mol_start, st.species, st.coords)
+    E_ref, F_ref = oracle.energy_forces_batch(st.mol_start, st.species, st.coords, OW)
+    rel = np.abs(E - E_ref) / np.abs(E_ref)
+    assert rel.max() <= E_REL_BF16, rel.max()
+    assert np.sqrt(np.mean((F - F_ref) ** 2)) <= F_RMS_BF16
