@@ -230,6 +230,31 @@ MLP_API int mlp_server_replay(mlp_server *s, int32_t n_req, const int64_t *arriv
                       const int8_t *species, const double *coords, double *energies, float *forces,
                       int64_t *wall_ns);
 
+/* ------------------------------------------------------------------ allocation-free neighbor list */
+
+/* Cell-list neighbor search for one system that allocates nothing. The paper
+ * has no counterpart: this entry point exists for callers that may not call
+ * cudaMalloc once they run (an engine or plugin living inside a fixed memory
+ * plan or a host framework's own pool, or a time-critical loop that cannot
+ * take an allocation's latency or failure). All working memory sits in a
+ * file-scope __device__ array of about 2.2 MB that every GPU loading the
+ * library holds until the process exits.
+ *
+ * d_coords [n][3] FP64 (device); cell = {Lx, Ly, Lz} (host) or NULL for an
+ * open system; cutoff = list radius in A, (0, 20]; outputs (device, caller
+ * owned): d_counts[n] = true neighbor count of each atom (may exceed cap),
+ * d_list[n][cap] = the first min(count, cap) neighbors of each atom (all j
+ * != i with |d_ij| < cutoff, minimum image when periodic). Limits: n <= 32768
+ * atoms and at most 32768 cells (periodic: floor(L / cutoff) per axis);
+ * larger inputs return MLP_EINVAL before any work is enqueued. Asynchronous
+ * on `stream`. The first call on each device resolves the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Every call reuses the same array (and
+ * clears its counters on `stream`), so calls that overlap on the GPU race:
+ * order them on one stream or synchronize between them. */
+MLP_API int mlp_neighbors_static(const double *d_coords, int32_t n, const double *cell, double cutoff,
+                                 int32_t *d_counts, int32_t *d_list, int32_t cap, void *stream);
+
 /* ------------------------------------------------------------------ memory */
 
 /* Routes the library's device allocations through alloc_fn / free_fn (for
