@@ -67,7 +67,14 @@ enum {
     MLP_EOVERFLOW = -7   /* neighbor capacity exceeded and could not be grown     */
 };
 
-enum { MLP_FP32 = 0, MLP_BF16 = 1 };
+/* Network precision. MLP_FP32: FP32 GEMMs on the CUDA cores. MLP_BF16: BF16
+ * tensor-core GEMMs with FP32 accumulation; the forward (energy) GEMMs take
+ * both operands as BF16 hi/lo pairs (X = X_hi + X_lo) and accumulate
+ * A_hi B_hi + A_lo B_hi + A_hi B_lo, the backward (forces) single BF16
+ * operands. MLP_BF16_1PASS: single BF16 operands everywhere (faster, energy
+ * error ~1e-3 relative from operand rounding). AEV and forces are FP32 in
+ * every mode; energy and force sums FP64. */
+enum { MLP_FP32 = 0, MLP_BF16 = 1, MLP_BF16_1PASS = 2 };
 
 #define MLP_NSPECIES 7
 #define MLP_AEV_LEN 1008
@@ -111,8 +118,8 @@ MLP_API void mlp_weights_destroy(mlp_weights *w);
 /* Creates a persistent system (one molecule or one periodic box) of n atoms
  * with fixed species[n]; coords[n][3] (host, may be NULL) are stored as the
  * current positions. cell = NULL gives an open boundary; otherwise every box
- * length must be >= 2 (rc_rad + skin). precision = MLP_FP32 (FP32 network)
- * or MLP_BF16 (BF16 tensor-core network, FP32 accumulation). Device buffers
+ * length must be >= 2 (rc_rad + skin). precision = MLP_FP32, MLP_BF16 or
+ * MLP_BF16_1PASS (see the precision enum). Device buffers
  * are sized for n atoms at creation. The weights must outlive the system. */
 MLP_API int mlp_create(const int8_t *species, const double *coords, int32_t n, const double *cell,
                const mlp_cutoffs *cut, const mlp_weights *w, int precision, mlp_system **out);
@@ -175,7 +182,7 @@ MLP_API int mlp_batch_sync(mlp_batch *b);
 /* ------------------------------------------------------------------ serving */
 
 typedef struct {
-    int precision;              /* MLP_BF16 (default) or MLP_FP32                        */
+    int precision;              /* MLP_BF16 (default), MLP_BF16_1PASS or MLP_FP32         */
     int32_t max_batch_atoms;    /* atoms packed into one device batch (default 131072)   */
     int32_t max_batch_mols;     /* molecules per batch (default 4096)                    */
     int32_t max_atoms_per_mol;  /* largest admissible molecule (default 256)             */

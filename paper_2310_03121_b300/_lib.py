@@ -23,6 +23,7 @@ MLP_ENOTFOUND = -6
 MLP_EOVERFLOW = -7
 MLP_FP32 = 0
 MLP_BF16 = 1
+MLP_BF16_1PASS = 2
 
 _NAMES = {0: "MLP_OK", 1: "MLP_PENDING", -1: "MLP_EINVAL", -2: "MLP_ENOMEM", -3: "MLP_EAGAIN",
           -4: "MLP_ETIMEDOUT", -5: "MLP_ECUDA", -6: "MLP_ENOTFOUND", -7: "MLP_EOVERFLOW"}

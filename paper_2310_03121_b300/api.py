@@ -10,16 +10,17 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import MLP_BF16, MLP_FP32, MLPError, check, load
+from ._lib import MLP_BF16, MLP_BF16_1PASS, MLP_FP32, MLPError, check, load
 
-PRECISIONS = {"fp32": MLP_FP32, "bf16": MLP_BF16, MLP_FP32: MLP_FP32, MLP_BF16: MLP_BF16}
+PRECISIONS = {"fp32": MLP_FP32, "bf16": MLP_BF16, "bf16_1pass": MLP_BF16_1PASS, MLP_FP32: MLP_FP32,
+              MLP_BF16: MLP_BF16, MLP_BF16_1PASS: MLP_BF16_1PASS}
 
 
 def _prec(p):
     try:
         return PRECISIONS[p]
     except KeyError:
-        raise ValueError(f"precision must be 'fp32' or 'bf16', got {p!r}") from None
+        raise ValueError(f"precision must be 'fp32', 'bf16' or 'bf16_1pass', got {p!r}") from None
 
 
 def _f64(a, shape=None):

@@ -182,8 +182,8 @@ int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out)
                          al256(nb3 * 4) + al256(nW4 * 4) + al256(nb4 * 4) + al256(nW1 * 4) + al256(nW2 * 4) +
                          al256(nW3 * 4);
     const size_t nW1p = (size_t)S * kH1 * kAevLd;   // padded K for the BF16 operands
-    size_t bf_per_net = al256(nW1p * 2) + al256(nW2 * 2) + al256(nW3 * 2) + al256(nW1p * 2) + al256(nW2 * 2) +
-                        al256(nW3 * 2);
+    size_t bf_per_net = 2 * (al256(nW1p * 2) + al256(nW2 * 2) + al256(nW3 * 2)) + al256(nW1p * 2) +
+                        al256(nW2 * 2) + al256(nW3 * 2);
     mlp_weights* mw = new (std::nothrow) mlp_weights();
     if (!mw) return set_error(MLP_ENOMEM, "host allocation failed");
     mw->dw.n_nets = n_nets;
@@ -263,24 +263,33 @@ int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out)
         };
         size_t bW1 = bput(nW1p), bW2 = bput(nW2), bW3 = bput(nW3), bW1t = bput(nW1p), bW2t = bput(nW2),
                bW3t = bput(nW3);
+        size_t bW1lo = bput(nW1p), bW2lo = bput(nW2), bW3lo = bput(nW3);
+        // remainder after BF16 rounding, itself rounded to BF16
+        auto lo_of = [](float x) { return to_bf16(x - __bfloat162float(to_bf16(x))); };
         auto B = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(hb.data() + o); };
         for (int s = 0; s < S; ++s) {
             for (int o = 0; o < kH1; ++o)
                 for (int c = 0; c < kAevLen; ++c) {
-                    __nv_bfloat16 v = to_bf16(W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c]);
+                    const float x = W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c];
+                    __nv_bfloat16 v = to_bf16(x);
                     B(bW1)[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = v;
+                    B(bW1lo)[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = lo_of(x);
                     B(bW1t)[(size_t)s * kAevLd * kH1 + (size_t)c * kH1 + o] = v;
                 }
             for (int o = 0; o < kH2; ++o)
                 for (int c = 0; c < kH1; ++c) {
-                    __nv_bfloat16 v = to_bf16(W2[(size_t)s * kH2 * kH1 + o * kH1 + c]);
+                    const float x = W2[(size_t)s * kH2 * kH1 + o * kH1 + c];
+                    __nv_bfloat16 v = to_bf16(x);
                     B(bW2)[(size_t)s * kH2 * kH1 + o * kH1 + c] = v;
+                    B(bW2lo)[(size_t)s * kH2 * kH1 + o * kH1 + c] = lo_of(x);
                     B(bW2t)[(size_t)s * kH1 * kH2 + c * kH2 + o] = v;
                 }
             for (int o = 0; o < kH3; ++o)
                 for (int c = 0; c < kH2; ++c) {
-                    __nv_bfloat16 v = to_bf16(W3[(size_t)s * kH3 * kH2 + o * kH2 + c]);
+                    const float x = W3[(size_t)s * kH3 * kH2 + o * kH2 + c];
+                    __nv_bfloat16 v = to_bf16(x);
                     B(bW3)[(size_t)s * kH3 * kH2 + o * kH2 + c] = v;
+                    B(bW3lo)[(size_t)s * kH3 * kH2 + o * kH2 + c] = lo_of(x);
                     B(bW3t)[(size_t)s * kH2 * kH3 + c * kH3 + o] = v;
                 }
         }
@@ -297,6 +306,9 @@ int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out)
         nb.W1t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1t);
         nb.W2t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2t);
         nb.W3t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3t);
+        nb.W1lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1lo);
+        nb.W2lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2lo);
+        nb.W3lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3lo);
         nb.b1 = nf.b1;
         nb.b2 = nf.b2;
         nb.b3 = nf.b3;
@@ -326,8 +338,8 @@ int mlp_create(const int8_t* species, const double* coords, int32_t n, const dou
     *out = nullptr;
     if (!species || !cut || !w) return set_error(MLP_EINVAL, "NULL argument");
     if (n <= 0) return set_error(MLP_EINVAL, "n = %d must be positive", n);
-    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision %d", precision);
-    if (precision == MLP_BF16 && !mlp_tc_available())
+    if (precision < MLP_FP32 || precision > MLP_BF16_1PASS) return set_error(MLP_EINVAL, "unknown precision %d", precision);
+    if (precision != MLP_FP32 && !mlp_tc_available())
         return set_error(MLP_EINVAL, "BF16 tensor-core network is not available in this build");
     if (std::fabs(cut->rc_rad - 5.1) > 1e-12 || std::fabs(cut->rc_ang - 3.5) > 1e-12)
         return set_error(MLP_EINVAL, "cutoffs must be rc_rad = 5.1 and rc_ang = 3.5 (the AEV's own)");
@@ -502,8 +514,8 @@ int mlp_batch_create(const mlp_weights* w, int precision, int32_t max_atoms, int
     if (!out) return set_error(MLP_EINVAL, "NULL out");
     *out = nullptr;
     if (!w) return set_error(MLP_EINVAL, "NULL weights");
-    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision %d", precision);
-    if (precision == MLP_BF16 && !mlp_tc_available())
+    if (precision < MLP_FP32 || precision > MLP_BF16_1PASS) return set_error(MLP_EINVAL, "unknown precision %d", precision);
+    if (precision != MLP_FP32 && !mlp_tc_available())
         return set_error(MLP_EINVAL, "BF16 tensor-core network is not available in this build");
     if (max_atoms <= 0 || max_mols <= 0 || max_atoms_per_mol <= 0 || max_atoms_per_mol > max_atoms)
         return set_error(MLP_EINVAL, "bad batch dimensions");
@@ -737,8 +749,8 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
     clear_error();
     if (!w || !species || !G || !e_out) return set_error(MLP_EINVAL, "NULL argument");
     if (n <= 0) return set_error(MLP_EINVAL, "n must be positive");
-    if (precision != MLP_FP32 && precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision");
-    if (precision == MLP_BF16 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
+    if (precision < MLP_FP32 || precision > MLP_BF16_1PASS) return set_error(MLP_EINVAL, "unknown precision");
+    if (precision != MLP_FP32 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
     int rc = check_cuda_device();
     if (rc) return rc;
     Workspace ws;
@@ -775,12 +787,17 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         cudaMemcpy(ws.G32, all.data(), 4 * all.size(), cudaMemcpyHostToDevice);
         launch_mlp_f32(nullptr, ws.rows_cap, ws.ctr, w->dw.f32[0], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG, true);
     } else {
-        std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f));
+        std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f)), all_lo(R * kAevLd, to_bf16(0.f));
         for (int i = 0; i < n; ++i)
-            for (int q = 0; q < kAevLen; ++q) all[(size_t)rows[i] * kAevLd + q] = to_bf16(G[(size_t)i * kAevLen + q]);
+            for (int q = 0; q < kAevLen; ++q) {
+                const float x = G[(size_t)i * kAevLen + q];
+                all[(size_t)rows[i] * kAevLd + q] = to_bf16(x);
+                all_lo[(size_t)rows[i] * kAevLd + q] = to_bf16(x - __bfloat162float(to_bf16(x)));
+            }
         cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
-        if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG, true,
-                             ws.tc_err)) {
+        if (ws.G16lo) cudaMemcpy(ws.G16lo, all_lo.data(), 2 * all_lo.size(), cudaMemcpyHostToDevice);
+        if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.G16lo, precision == MLP_BF16,
+                             ws.row_atom, ws.e, ws.dG, true, ws.tc_err)) {
             workspace_destroy(ws);
             return MLP_ECUDA;
         }
@@ -793,7 +810,7 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         for (int i = 0; i < n; ++i) std::memcpy(dEdG + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
     }
     int tc = 0;
-    if (e == cudaSuccess && precision == MLP_BF16) e = cudaMemcpy(&tc, ws.tc_err, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && precision != MLP_FP32) e = cudaMemcpy(&tc, ws.tc_err, 4, cudaMemcpyDeviceToHost);
     workspace_destroy(ws);
     if (e != cudaSuccess) return cuda_error(e, "mlp_debug_network");
     if (tc) return set_error(MLP_ECUDA, "tensor-core kernel reported error %d", tc);

@@ -88,6 +88,7 @@ void plan_workspace(Plan& P, Workspace& ws) {
         P.add(&ws.fb.G1, R * kH1);
     } else {
         P.add(&ws.G16, R * kAevLd);
+        if (ws.precision == 1) P.add(&ws.G16lo, R * kAevLd);
     }
     if (ws.cell_path) {
         P.add(&ws.grid, 1);
@@ -163,7 +164,7 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     if (n <= 0 || n > ws.cap_atoms) return set_error(-1, "atom count %d outside [1, %d]", n, ws.cap_atoms);
     if (sp.n_mols > ws.cap_mols) return set_error(-1, "molecule count %d above %d", sp.n_mols, ws.cap_mols);
     const bool batch = sp.d_mol_start != nullptr;
-    const bool fast = ws.precision == 1;
+    const bool fast = ws.precision != 0;
     cudaError_t ce;
 
     AevArgs aa;
@@ -200,7 +201,7 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
         if (ws.precision == 0)
             launch_aev_f32(st, aa, ws.G32, ws.row_atom, fast);
         else
-            launch_aev_bf16(st, aa, ws.G16, ws.row_atom, fast);
+            launch_aev_bf16(st, aa, ws.G16, ws.G16lo, ws.row_atom, fast);
     }
 
     if (ws.precision == 0) {
@@ -208,8 +209,8 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
                        sp.network_backward);
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
-        if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.row_atom, ws.e, ws.dG,
-                             sp.network_backward, ws.tc_err))
+        if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
+                             ws.e, ws.dG, sp.network_backward, ws.tc_err))
             return -5;
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.grad, fast);

@@ -44,6 +44,8 @@ struct DevWeights {
     NetBF16 bf16[kMaxNets];
 };
 
+// precision: 0 = FP32 network, 1 = BF16 tensor cores with split-precision
+// forward, 2 = BF16 tensor cores, single pass
 struct Workspace {
     int cap_atoms = 0, cap_mols = 0, rows_cap = 0, nbr_cap = 0, max_cells = 0;
     int precision = 0;
@@ -57,6 +59,7 @@ struct Workspace {
     double* grad = nullptr;
     float* G32 = nullptr;
     __nv_bfloat16* G16 = nullptr;
+    __nv_bfloat16* G16lo = nullptr;   // split-precision network only
     float* dG = nullptr;
     MlpF32Bufs fb{};
     float* e = nullptr;

@@ -59,7 +59,8 @@ struct AevArgs {
     const int* rank;
 };
 void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast);
-void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, int* row_atom, bool fast);
+void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,
+                     bool fast);
 void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, double* grad, bool fast);
 
 // ---- network, FP32 SIMT path (kernels_mlp_f32.cu)
@@ -76,17 +77,20 @@ void launch_mlp_f32(cudaStream_t st, int rows_cap, const Counters* ctr, const Ne
 // ---- network, BF16 tcgen05 path (kernels_mlp_tc.cu)
 struct NetBF16 {
     const __nv_bfloat16 *W1, *W2, *W3;       // [7][256][1024], [7][192][256], [7][160][192]
+    const __nv_bfloat16 *W1lo, *W2lo, *W3lo; // BF16 remainders W - W_hi of the forward weights
     const __nv_bfloat16 *W1t, *W2t, *W3t;    // [7][1024][256], [7][256][192], [7][192][160]
     const float *b1, *b2, *b3, *W4, *b4;
-    // TMA descriptors of the six weight matrices (built once per weight set)
-    CUtensorMap tmW1, tmW2, tmW3, tmW1t, tmW2t, tmW3t;
+    // TMA descriptors of the weight matrices (built once per weight set)
+    CUtensorMap tmW1, tmW2, tmW3, tmW1lo, tmW2lo, tmW3lo, tmW1t, tmW2t, tmW3t;
     bool maps_ok;
 };
 bool mlp_tc_available();
 bool make_weight_maps(NetBF16& w);
+// split = true: forward GEMMs from hi/lo BF16 pairs of both operands (G_lo
+// required); false: single BF16 pass everywhere.
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
-                     const __nv_bfloat16* G, const int* row_atom, float* e, float* dG, bool backward,
-                     int* err_flag);
+                     const __nv_bfloat16* G, const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e,
+                     float* dG, bool backward, int* err_flag);
 
 // ---- finalize (kernels_misc.cu)
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,

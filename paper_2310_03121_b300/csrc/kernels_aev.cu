@@ -174,19 +174,28 @@ template <>
 __device__ __forceinline__ void store_row<true, float>(float* out, const float* acc, int lane) {
     store_row<false, float>(out, acc, lane);
 }
+// BF16 row; with out_lo != nullptr also the BF16 rounding of the remainder
+// (G = G_hi + G_lo to ~16 bits), for the split-precision network.
 template <bool FAST>
-__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* out, const float* acc, int lane) {
+__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* out, __nv_bfloat16* out_lo, const float* acc,
+                                               int lane) {
     for (int c = 2 * lane; c < kAevLd; c += 64) {
         float v0, v1;
         v0 = c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
         int c1 = c + 1;
         v1 = c1 < kRadLen ? acc[c1] + acc[kRadLen + c1] : (c1 < kAevLen ? acc[kRadLen + c1] : 0.f);
-        *reinterpret_cast<__nv_bfloat162*>(out + c) = __floats2bfloat162_rn(v0, v1);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        *reinterpret_cast<__nv_bfloat162*>(out + c) = h;
+        if (out_lo) {
+            const float2 f = __bfloat1622float2(h);
+            *reinterpret_cast<__nv_bfloat162*>(out_lo + c) = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
+        }
     }
 }
 
 template <bool FAST, typename OutT>
-__global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, int* __restrict__ row_atom) {
+__global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
+                                                      int* __restrict__ row_atom) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + w;
@@ -251,7 +260,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     if constexpr (sizeof(OutT) == 4) {
         store_row<FAST, float>(reinterpret_cast<float*>(G) + (size_t)row * kAevLd, acc, lane);
     } else {
-        store_row_bf16<FAST>(reinterpret_cast<__nv_bfloat16*>(G) + (size_t)row * kAevLd, acc, lane);
+        store_row_bf16<FAST>(reinterpret_cast<__nv_bfloat16*>(G) + (size_t)row * kAevLd,
+                             G_lo ? reinterpret_cast<__nv_bfloat16*>(G_lo) + (size_t)row * kAevLd : nullptr, acc,
+                             lane);
     }
     if (lane == 0) row_atom[row] = i;
 }
@@ -408,25 +419,26 @@ void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, 
     if (fast) {
         static bool once = (set_smem(k_aev<true, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kWarps * 32, sm, st>>>(a, G, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     } else {
         static bool once = (set_smem(k_aev<false, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kWarps * 32, sm, st>>>(a, G, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     }
 }
 
-void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, int* row_atom, bool fast) {
+void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,
+                     bool fast) {
     const size_t sm = kWarps * kAevSmemPerWarp;
     const int gs = (a.n + kWarps - 1) / kWarps;
     if (fast) {
         static bool once = (set_smem(k_aev<true, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     } else {
         static bool once = (set_smem(k_aev<false, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     }
 }
 

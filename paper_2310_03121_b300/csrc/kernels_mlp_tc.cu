@@ -15,6 +15,11 @@
 //   B2  D[128x256] = g2 W2              W2^T streamed;  g1 = D * celu'(z1) (over h1)
 //   B1  dE/dG[128x1024] = g1 W1         W1^T streamed in four 256-column blocks -> global FP32
 // celu'(z) comes from the stored BF16 activation: 1 if h > 0 else h / alpha + 1.
+// Split mode (the default BF16 precision): every forward GEMM is computed from
+// BF16 hi/lo pairs of both operands, X = X_hi + X_lo with X_lo the BF16
+// rounding of the remainder, as A_hi B_hi + A_lo B_hi + A_hi B_lo (three MMAs
+// per K step, FP32 accumulation), so the energy carries ~16 bits of operand
+// precision; the backward (forces) uses the single BF16 terms.
 // Accumulators live in tensor memory (512 columns: two 256-column halves).
 // Thread 0 issues the TMA loads (cp.async.bulk.tensor) and the tcgen05.mma
 // instructions; all 128 threads run the epilogues (tcgen05.ld -> registers ->
@@ -36,18 +41,26 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr uint32_t kAtom = 128 * 128;          // 128 rows x 64 BF16 (one K atom of a 128-row operand)
-constexpr uint32_t kOffH1 = 0;                 // h1 / g1: 4 atoms
-constexpr uint32_t kOffH2 = 4 * kAtom;         // h2 / g2: 3 atoms
-constexpr uint32_t kOffG3 = 7 * kAtom;         // g3: 3 atoms (160 of 192 columns used)
-constexpr uint32_t kOffRB = 10 * kAtom;        // streamed weights: 2 stages x 32 KB
-constexpr uint32_t kRBStage = 32768;
-constexpr uint32_t kF1Stage = 49152;           // F1: A (16 KB) + B (32 KB) per stage, overlaying [0, 192 KB)
-constexpr int kNF1 = 4;
-constexpr uint32_t kSmemUsed = kOffRB + 2 * kRBStage;   // 229,376 bytes
+// Shared memory map (224 KB, offsets from the 1024-aligned base):
+//   [0, 64K)      h1 / g1                         (4 atoms)
+//   [64K, 112K)   h2 / g2                         (3 atoms)
+//   [112K, 160K)  g3                              (3 atoms, 160 of 192 columns used)
+//   [160K, 224K)  weight ring of the backward GEMMs (2 x 32 KB)
+// Split mode also keeps h1_lo at [64K, 128K) during F2 (ring [128K, 224K),
+// 4 x 24 KB) and h2_lo at [112K, 160K) during F3 (ring [160K, 224K), 3 x 20 KB).
+// F1 streams G and W1 chunks through stages overlaying [0, 192K): 4 x 48 KB,
+// or 2 x 96 KB in split mode (G_hi, G_lo, W1_hi, W1_lo per chunk).
+constexpr uint32_t kOffH1 = 0;
+constexpr uint32_t kOffH2 = 4 * kAtom;
+constexpr uint32_t kOffG3 = 7 * kAtom;
+constexpr uint32_t kOffH1lo = 4 * kAtom;
+constexpr uint32_t kOffH2lo = 7 * kAtom;
+constexpr uint32_t kOffRB = 10 * kAtom;
+constexpr uint32_t kSmemUsed = 14 * kAtom;               // 229,376 bytes
 constexpr uint32_t kSmemAlloc = kSmemUsed + 1024;       // + alignment slack
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
-enum { kBarF1Full = 0, kBarF1Empty = 4, kBarRBFull = 8, kBarRBEmpty = 10, kBarDone = 12, kNBars = 13 };
+enum { kBarF1Full = 0, kBarF1Empty = 4, kBarRBFull = 8, kBarRBEmpty = 12, kBarDone = 16, kNBars = 17 };
 
 struct TcArgs {
     const Counters* ctr;
@@ -168,11 +181,11 @@ __device__ __forceinline__ float dcelu_f(float x) { return x > 0.f ? 1.f : __exp
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : h * (1.f / kCeluAlpha) + 1.f; }
 
 // ------------------------------------------------------------------ issuing thread state
-// Stage slots 0..3: F1 (A + B), 4..5: streamed weights of the other GEMMs.
+// Slots 0..3: F1 stages; slots 4..7: weight-ring slots of the other GEMMs.
 struct Issuer {
     uint32_t bar0;          // shared address of barrier 0 (barriers are 8 bytes apart)
-    uint32_t nfull[6];      // phases consumed per full barrier
-    uint32_t nempty[6];     // phases consumed per empty barrier
+    uint32_t nfull[8];      // phases consumed per full barrier
+    uint32_t nempty[8];     // phases consumed per empty barrier
     uint32_t pend;          // slots with an MMA commit not yet waited for
     uint32_t loaded;        // slots with a TMA load not yet consumed
     uint32_t f1_next, rb_next;
@@ -203,100 +216,163 @@ struct Issuer {
     }
 };
 
+// One GEMM D[128 x N] = A[128 x K] B^T with B streamed by TMA through a ring
+// of slots, one sub-chunk (N rows x 64 K columns) per slot. In split mode
+// every K chunk c brings two sub-chunks, B_hi(c) then B_lo(c), and the MMAs
+// are A_hi(c) B_hi(c) + A_lo(c) B_hi(c) and A_hi(c) B_lo(c).
 struct Job {
-    const CUtensorMap* map;
-    int brow;          // first weight row (element block + column block)
-    int nc;            // K chunks of 64
-    int lastk;         // 16-wide K steps in the last chunk
-    uint32_t a_off;    // A operand region
-    uint32_t d_col;    // TMEM column of the accumulator
+    const CUtensorMap* map;      // B (hi)
+    const CUtensorMap* map_lo;   // B lo (split only)
+    int brow;                    // first B row (element block + column block)
+    int nc;                      // K chunks of 64
+    int lastk;                   // 16-wide K steps in the last chunk
+    uint32_t a_off, a_lo_off;    // A operand regions (lo: split only)
+    uint32_t d_col;              // TMEM column of the accumulator
     int N;
-    uint32_t bytes;    // TMA bytes per chunk (N rows x 128 B)
-    int st[4];
+    uint32_t ring_off, slot_bytes;
+    int slots;
+    int split;
+    int st[8];                   // slot of each sub-chunk
+    __device__ int nq() const { return split ? 2 * nc : nc; }
 };
 
-__device__ __forceinline__ bool load_rb(Issuer& I, uint32_t sbase, Job& J, int c) {
-    const int si = J.st[c];
+__device__ __forceinline__ bool load_sub(Issuer& I, uint32_t sbase, Job& J, int q) {
+    const int si = J.st[q];
     if (!I.acquire(si)) return false;
-    const uint32_t dst = sbase + kOffRB + (uint32_t)(si - 4) * kRBStage;
-    mbar_expect_tx(I.full(si), J.bytes);
-    tma_load_2d(dst, J.map, c * 64, J.brow, I.full(si));
+    const uint32_t dst = sbase + J.ring_off + (uint32_t)(si - 4) * J.slot_bytes;
+    const int c = J.split ? (q >> 1) : q;
+    const CUtensorMap* m = (J.split && (q & 1)) ? J.map_lo : J.map;
+    mbar_expect_tx(I.full(si), (uint32_t)J.N * 128u);
+    tma_load_2d(dst, m, c * 64, J.brow, I.full(si));
     I.loaded |= 1u << si;
     return true;
 }
 
 __device__ bool job_prefetch(Issuer& I, uint32_t sbase, Job& J) {
-    for (int c = 0; c < 2 && c < J.nc; ++c) {
-        J.st[c] = 4 + (int)(I.rb_next & 1u);
+    const int nq = J.nq();
+    for (int q = 0; q < J.slots && q < nq; ++q) {
+        J.st[q] = 4 + (int)(I.rb_next % (uint32_t)J.slots);
         I.rb_next++;
-        if (!load_rb(I, sbase, J, c)) return false;
+        if (!load_sub(I, sbase, J, q)) return false;
     }
     return true;
 }
 
 __device__ bool job_run(Issuer& I, uint32_t sbase, uint32_t tmem, Job& J) {
     const uint32_t idesc = idesc_bf16(128, J.N);
-    for (int c = 0; c < J.nc; ++c) {
-        const int si = J.st[c];
+    const int nq = J.nq();
+    bool first = true;
+    for (int q = 0; q < nq; ++q) {
+        const int si = J.st[q];
         if (!I.consume(si)) return false;
-        const uint32_t b_base = sbase + kOffRB + (uint32_t)(si - 4) * kRBStage;
-        const uint32_t a_base = sbase + J.a_off + (uint32_t)c * kAtom;
+        const int c = J.split ? (q >> 1) : q;
+        const bool lo_b = J.split && (q & 1);
+        const uint32_t b_base = sbase + J.ring_off + (uint32_t)(si - 4) * J.slot_bytes;
+        const uint32_t a_hi = sbase + J.a_off + (uint32_t)c * kAtom;
+        const uint32_t a_lo = sbase + J.a_lo_off + (uint32_t)c * kAtom;
         const int ks = (c == J.nc - 1) ? J.lastk : 4;
-        for (int k = 0; k < ks; ++k)
-            mma_bf16(tmem + J.d_col, sdesc(a_base + 32u * k), sdesc(b_base + 32u * k), idesc,
-                     (c > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < ks; ++k) {
+            const uint64_t b = sdesc(b_base + 32u * k);
+            mma_bf16(tmem + J.d_col, sdesc(a_hi + 32u * k), b, idesc, first ? 0u : 1u);
+            first = false;
+            if (J.split && !lo_b) mma_bf16(tmem + J.d_col, sdesc(a_lo + 32u * k), b, idesc, 1u);
+        }
         I.release(si);
-        if (c >= 1 && c + 1 < J.nc) {
-            J.st[c + 1] = J.st[c - 1];
-            if (!load_rb(I, sbase, J, c + 1)) return false;
+        const int nxt = q - 1 + J.slots;
+        if (q >= 1 && nxt < nq) {
+            J.st[nxt] = J.st[q - 1];
+            if (!load_sub(I, sbase, J, nxt)) return false;
         }
     }
     mma_commit(I.bar(kBarDone));
     return true;
 }
 
-__device__ bool f1_run(Issuer& I, uint32_t sbase, uint32_t tmem, const CUtensorMap* mG, const CUtensorMap* mW1,
-                       int row0, int s) {
-    constexpr int nc = kAevLd / 64;   // 16
+// Layer 1: A (G) and B (W1) both streamed, K = 1024 in 16 chunks.
+template <bool SPLIT>
+__device__ bool f1_run(Issuer& I, uint32_t sbase, uint32_t tmem, const CUtensorMap* mG, const CUtensorMap* mGlo,
+                       const CUtensorMap* mW1, const CUtensorMap* mW1lo, int row0, int s) {
+    constexpr int nc = kAevLd / 64;                       // 16
+    constexpr int nst = SPLIT ? 2 : 4;
+    constexpr uint32_t stage = SPLIT ? 98304u : 49152u;   // A (+A_lo) 16 KB each, B (+B_lo) 32 KB each
     const uint32_t idesc = idesc_bf16(128, kH1);
     int st[nc];
     auto load = [&](int c) -> bool {
         const int si = st[c];
         if (!I.acquire(si)) return false;
-        const uint32_t dst = sbase + (uint32_t)si * kF1Stage;
-        mbar_expect_tx(I.full(si), kF1Stage);
+        const uint32_t dst = sbase + (uint32_t)si * stage;
+        mbar_expect_tx(I.full(si), stage);
         tma_load_2d(dst, mG, c * 64, row0, I.full(si));
-        tma_load_2d(dst + 16384u, mW1, c * 64, s * kH1, I.full(si));
+        if (SPLIT) {
+            tma_load_2d(dst + 16384u, mGlo, c * 64, row0, I.full(si));
+            tma_load_2d(dst + 32768u, mW1, c * 64, s * kH1, I.full(si));
+            tma_load_2d(dst + 65536u, mW1lo, c * 64, s * kH1, I.full(si));
+        } else {
+            tma_load_2d(dst + 16384u, mW1, c * 64, s * kH1, I.full(si));
+        }
         I.loaded |= 1u << si;
         return true;
     };
-    for (int c = 0; c < kNF1; ++c) {
-        st[c] = (int)(I.f1_next & 3u);
+    for (int c = 0; c < nst; ++c) {
+        st[c] = (int)(I.f1_next % (uint32_t)nst);
         I.f1_next++;
         if (!load(c)) return false;
     }
     for (int c = 0; c < nc; ++c) {
         const int si = st[c];
         if (!I.consume(si)) return false;
-        const uint32_t a_base = sbase + (uint32_t)si * kF1Stage;
-        for (int k = 0; k < 4; ++k)
-            mma_bf16(tmem, sdesc(a_base + 32u * k), sdesc(a_base + 16384u + 32u * k), idesc,
-                     (c > 0 || k > 0) ? 1u : 0u);
+        const uint32_t base = sbase + (uint32_t)si * stage;
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+            if (SPLIT) {
+                const uint64_t ah = sdesc(base + 32u * k), al = sdesc(base + 16384u + 32u * k);
+                const uint64_t bh = sdesc(base + 32768u + 32u * k), bl = sdesc(base + 65536u + 32u * k);
+                mma_bf16(tmem, ah, bh, idesc, acc);
+                mma_bf16(tmem, al, bh, idesc, 1u);
+                mma_bf16(tmem, ah, bl, idesc, 1u);
+            } else {
+                mma_bf16(tmem, sdesc(base + 32u * k), sdesc(base + 16384u + 32u * k), idesc, acc);
+            }
+        }
         I.release(si);
-        if (c >= 1 && c + 3 < nc) {
-            st[c + 3] = st[c - 1];
-            if (!load(c + 3)) return false;
+        if (c >= 1 && c - 1 + nst < nc) {
+            st[c - 1 + nst] = st[c - 1];
+            if (!load(c - 1 + nst)) return false;
         }
     }
     mma_commit(I.bar(kBarDone));
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_mlp_tc(const __grid_constant__ CUtensorMap mG, const __grid_constant__ CUtensorMap mW1,
-             const __grid_constant__ CUtensorMap mW2, const __grid_constant__ CUtensorMap mW3,
-             const __grid_constant__ CUtensorMap mW3t, const __grid_constant__ CUtensorMap mW2t,
-             const __grid_constant__ CUtensorMap mW1t, TcArgs p) {
+// Epilogue helper: 16 values of this thread's row -> BF16 hi (and lo) in the
+// operand layout at column c0.
+template <bool SPLIT>
+__device__ __forceinline__ void store_act(uint32_t sbase, uint32_t off_hi, uint32_t off_lo, int r, int c0,
+                                          const float (&h)[16]) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(h[2 * q], h[2 * q + 1]);
+        hi[q] = *reinterpret_cast<uint32_t*>(&v);
+        if (SPLIT) {
+            const float2 f = __bfloat1622float2(v);
+            lo[q] = pack_bf16(h[2 * q] - f.x, h[2 * q + 1] - f.y);
+        }
+    }
+    st_shared_v4(sbase + off_hi + op_off(r, c0), hi[0], hi[1], hi[2], hi[3]);
+    st_shared_v4(sbase + off_hi + op_off(r, c0 + 8), hi[4], hi[5], hi[6], hi[7]);
+    if (SPLIT) {
+        st_shared_v4(sbase + off_lo + op_off(r, c0), lo[0], lo[1], lo[2], lo[3]);
+        st_shared_v4(sbase + off_lo + op_off(r, c0 + 8), lo[4], lo[5], lo[6], lo[7]);
+    }
+}
+
+struct TcMaps {
+    CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t;
+};
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ TcMaps M, TcArgs p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) unsigned long long bars[kNBars];
     __shared__ uint32_t tmem_slot;
@@ -307,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     Issuer I;
     I.bar0 = smem_u32(&bars[0]);
-    for (int q = 0; q < 6; ++q) I.nfull[q] = I.nempty[q] = 0;
+    for (int q = 0; q < 8; ++q) I.nfull[q] = I.nempty[q] = 0;
     I.pend = I.loaded = 0;
     I.f1_next = I.rb_next = 0;
     I.ok = true;
@@ -352,24 +428,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float* b2 = p.b2 + s * kH2;
         const float* b3 = p.b3 + s * kH3;
         const float* w4 = p.W4 + s * kH3;
-        Job jF2{&mW2, s * kH2, 4, 4, kOffH1, 256, kH2, (uint32_t)kH2 * 128u, {0, 0, 0, 0}};
-        Job jF3{&mW3, s * kH3, 3, 4, kOffH2, 0, kH3, (uint32_t)kH3 * 128u, {0, 0, 0, 0}};
-        Job jB3{&mW3t, s * kH2, 3, 2, kOffG3, 256, kH2, (uint32_t)kH2 * 128u, {0, 0, 0, 0}};
-        Job jB2{&mW2t, s * kH1, 3, 4, kOffH2, 0, kH1, (uint32_t)kH1 * 128u, {0, 0, 0, 0}};
+        // forward jobs (ring geometry depends on the mode), backward jobs
+        Job jF2 = SPLIT ? Job{&M.W2, &M.W2lo, s * kH2, 4, 4, kOffH1, kOffH1lo, 256, kH2, 8 * kAtom,
+                              (uint32_t)kH2 * 128u, 4, 1, {0}}
+                        : Job{&M.W2, nullptr, s * kH2, 4, 4, kOffH1, 0, 256, kH2, kOffRB, 32768u, 2, 0, {0}};
+        Job jF3 = SPLIT ? Job{&M.W3, &M.W3lo, s * kH3, 3, 4, kOffH2, kOffH2lo, 0, kH3, kOffRB, (uint32_t)kH3 * 128u,
+                              3, 1, {0}}
+                        : Job{&M.W3, nullptr, s * kH3, 3, 4, kOffH2, 0, 0, kH3, kOffRB, 32768u, 2, 0, {0}};
+        Job jB3{&M.W3t, nullptr, s * kH2, 3, 2, kOffG3, 0, 256, kH2, kOffRB, 32768u, 2, 0, {0}};
+        Job jB2{&M.W2t, nullptr, s * kH1, 3, 4, kOffH2, 0, 0, kH1, kOffRB, 32768u, 2, 0, {0}};
 
         // ---- F1 -> E1
-        if (tid == 0 && !f1_run(I, sbase, tmem, &mG, &mW1, row0, s)) issue_fail();
+        if (tid == 0 && !f1_run<SPLIT>(I, sbase, tmem, &M.G, &M.Glo, &M.W1, &M.W1lo, row0, s)) issue_fail();
         wait_done();
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF2)) issue_fail();
         for (int c0 = 0; c0 < kH1; c0 += 16) {
             float v[16];
             tmem_ld16(tl + (uint32_t)c0, v);
-            uint32_t pk[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                pk[q] = pack_bf16(celu_f(v[2 * q] + __ldg(b1 + c0 + 2 * q)), celu_f(v[2 * q + 1] + __ldg(b1 + c0 + 2 * q + 1)));
-            st_shared_v4(sbase + kOffH1 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
-            st_shared_v4(sbase + kOffH1 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
+            for (int q = 0; q < 16; ++q) v[q] = celu_f(v[q] + __ldg(b1 + c0 + q));
+            store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
         }
         if (!sync_all()) break;
 
@@ -380,12 +458,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c0 = 0; c0 < kH2; c0 += 16) {
             float v[16];
             tmem_ld16(tl + 256u + (uint32_t)c0, v);
-            uint32_t pk[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                pk[q] = pack_bf16(celu_f(v[2 * q] + __ldg(b2 + c0 + 2 * q)), celu_f(v[2 * q + 1] + __ldg(b2 + c0 + 2 * q + 1)));
-            st_shared_v4(sbase + kOffH2 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
-            st_shared_v4(sbase + kOffH2 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
+            for (int q = 0; q < 16; ++q) v[q] = celu_f(v[q] + __ldg(b2 + c0 + q));
+            store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
         }
         if (!sync_all()) break;
 
@@ -443,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- B2 -> g1 (over h1)
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB2)) issue_fail();
         wait_done();
-        Job jB1{&mW1t, s * kAevLd, 4, 4, kOffH1, 0, 256, 256u * 128u, {0, 0, 0, 0}};
+        Job jB1{&M.W1t, nullptr, s * kAevLd, 4, 4, kOffH1, 0, 0, 256, kOffRB, 32768u, 2, 0, {0}};
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
         for (int c0 = 0; c0 < kH1; c0 += 16) {
             float v[16];
@@ -498,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (abort_flag) {
         if (tid == 0) {
             atomicOr(p.err, 1);
-            for (int si = 0; si < 6; ++si)
+            for (int si = 0; si < 8; ++si)
                 if (I.loaded & (1u << si)) (void)mbar_wait(I.full(si), I.nfull[si] & 1u);
             mma_commit(I.bar(kBarDone));
             (void)mbar_wait(I.bar(kBarDone), n_done & 1u);
@@ -552,6 +627,9 @@ bool make_weight_maps(NetBF16& w) {
     ok &= make_map(&w.tmW1, w.W1, kAevLd, (uint64_t)kNSpecies * kH1, kH1);
     ok &= make_map(&w.tmW2, w.W2, kH1, (uint64_t)kNSpecies * kH2, kH2);
     ok &= make_map(&w.tmW3, w.W3, kH2, (uint64_t)kNSpecies * kH3, kH3);
+    ok &= make_map(&w.tmW1lo, w.W1lo, kAevLd, (uint64_t)kNSpecies * kH1, kH1);
+    ok &= make_map(&w.tmW2lo, w.W2lo, kH1, (uint64_t)kNSpecies * kH2, kH2);
+    ok &= make_map(&w.tmW3lo, w.W3lo, kH2, (uint64_t)kNSpecies * kH3, kH3);
     ok &= make_map(&w.tmW3t, w.W3t, kH3, (uint64_t)kNSpecies * kH2, kH2);
     ok &= make_map(&w.tmW2t, w.W2t, kH2, (uint64_t)kNSpecies * kH1, kH1);
     ok &= make_map(&w.tmW1t, w.W1t, kH1, (uint64_t)kNSpecies * kAevLd, 256);
@@ -560,15 +638,28 @@ bool make_weight_maps(NetBF16& w) {
 }
 
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w, const __nv_bfloat16* G,
-                     const int* row_atom, float* e, float* dG, bool backward, int* err_flag) {
-    CUtensorMap mG;
-    if (!w.maps_ok || !make_map(&mG, G, kAevLd, (uint64_t)rows_cap, 128)) {
+                     const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, float* dG, bool backward,
+                     int* err_flag) {
+    TcMaps M;
+    if (!w.maps_ok || !make_map(&M.G, G, kAevLd, (uint64_t)rows_cap, 128) ||
+        (split && (!G_lo || !make_map(&M.Glo, G_lo, kAevLd, (uint64_t)rows_cap, 128)))) {
         set_error(-5, "TMA tensor map creation failed");
         return false;
     }
+    if (!split) M.Glo = M.G;
+    M.W1 = w.tmW1;
+    M.W1lo = w.tmW1lo;
+    M.W2 = w.tmW2;
+    M.W2lo = w.tmW2lo;
+    M.W3 = w.tmW3;
+    M.W3lo = w.tmW3lo;
+    M.W3t = w.tmW3t;
+    M.W2t = w.tmW2t;
+    M.W1t = w.tmW1t;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
         attr = true;
     }
     static int sms = 0;
@@ -581,8 +672,10 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
     const int tiles = rows_cap / kTileRows;
     const int grid = tiles < sms ? tiles : sms;
     TcArgs a{ctr, row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, dG, backward ? 1 : 0, err_flag};
-    MLP_LAUNCH("mlp_tc", st,
-               k_mlp_tc<<<grid, kThreads, kSmemAlloc, st>>>(mG, w.tmW1, w.tmW2, w.tmW3, w.tmW3t, w.tmW2t, w.tmW1t, a));
+    if (split)
+        MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+    else
+        MLP_LAUNCH("mlp_tc", st, k_mlp_tc<false><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
     return true;
 }
 

@@ -293,8 +293,8 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     mlp_server_opts o;
     mlp_server_opts_default(&o);
     if (opts) o = *opts;
-    if (o.precision != MLP_FP32 && o.precision != MLP_BF16) return set_error(MLP_EINVAL, "unknown precision");
-    if (o.precision == MLP_BF16 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
+    if (o.precision < MLP_FP32 || o.precision > MLP_BF16_1PASS) return set_error(MLP_EINVAL, "unknown precision");
+    if (o.precision != MLP_FP32 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
     if (o.max_batch_atoms <= 0 || o.max_batch_mols <= 0 || o.max_atoms_per_mol <= 0 ||
         o.max_atoms_per_mol > o.max_batch_atoms || o.streams <= 0 || o.streams > 16 || o.queue_capacity <= 0 ||
         o.budget_bytes <= 0)

@@ -243,35 +243,52 @@ def _bf16(x):
     return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
 
 
-def _emulate_bf16_network(wts, sp, G):
-    """The tensor-core kernel's arithmetic in float64: BF16 operands (G, W,
-    stored activations), exact products, FP32-level accumulation, celu'(z)
-    recovered from the stored BF16 activation."""
+def _split(x):
+    """FP32 value -> (BF16 hi, BF16 rounding of the remainder), as float64."""
+    x32 = torch.as_tensor(x, dtype=torch.float64).float()
+    hi = x32.to(torch.bfloat16)
+    lo = (x32 - hi.float()).to(torch.bfloat16)
+    return hi.double(), lo.double()
+
+
+def _emulate_bf16_network(wts, sp, G, split=True):
+    """The tensor-core kernel's arithmetic in float64. Forward GEMMs: BF16
+    operands (split = False) or A_hi B_hi + A_lo B_hi + A_hi B_lo from hi/lo
+    BF16 pairs (split = True); backward: BF16 operands; celu'(z) of the
+    hidden layers recovered from the stored BF16 activation."""
     e = np.zeros(len(sp))
     g = np.zeros((len(sp), 1008))
+    cel = lambda z: torch.where(z > 0, z, 0.1 * (torch.exp(z / 0.1) - 1))
+    dcel = lambda h: torch.where(h > 0, torch.ones_like(h), h / 0.1 + 1)
+
+    def fwd(a, W):
+        ah, al = _split(a)
+        wh, wl = _split(W)
+        return ah @ wh.T + al @ wh.T + ah @ wl.T if split else ah @ wh.T
+
     for s in range(7):
         idx = np.nonzero(sp == s)[0]
         if idx.size == 0:
             continue
-        W1, W2, W3 = (_bf16(wts[k][s]) for k in ("W1", "W2", "W3"))
+        W1, W2, W3 = (torch.as_tensor(wts[k][s], dtype=torch.float32).double() for k in ("W1", "W2", "W3"))
         b1, b2, b3, w4 = (torch.as_tensor(wts[k][s], dtype=torch.float32).double() for k in ("b1", "b2", "b3", "W4"))
         b4 = float(np.float32(wts["b4"][s]))
-        A = _bf16(G[idx])
-        cel = lambda z: torch.where(z > 0, z, 0.1 * (torch.exp(z / 0.1) - 1))
-        dcel = lambda h: torch.where(h > 0, torch.ones_like(h), h / 0.1 + 1)
-        h1 = _bf16(cel(A @ W1.T + b1))
-        h2 = _bf16(cel(h1 @ W2.T + b2))
-        z3 = h2 @ W3.T + b3
+        A = torch.as_tensor(G[idx], dtype=torch.float32).double()
+        h1 = cel(fwd(A, W1) + b1).float().double()
+        h2 = cel(fwd(h1, W2) + b2).float().double()
+        z3 = fwd(h2, W3) + b3
         e[idx] = (cel(z3) @ w4 + b4).numpy()
+        h1b, h2b = _bf16(h1), _bf16(h2)
         g3 = _bf16(w4 * torch.where(z3 > 0, torch.ones_like(z3), torch.exp(z3 / 0.1)))
-        g2 = _bf16((g3 @ W3) * dcel(h2))
-        g1 = _bf16((g2 @ W2) * dcel(h1))
-        g[idx] = (g1 @ W1).numpy()
+        g2 = _bf16((g3 @ _bf16(W3)) * dcel(h2b))
+        g1 = _bf16((g2 @ _bf16(W2)) * dcel(h1b))
+        g[idx] = (g1 @ _bf16(W1)).numpy()
     return e, g
 
 
 @pytest.mark.parametrize("n", [1, 129, 400])
-def test_network_bf16_matches_emulation(P, W, wts, n):
+@pytest.mark.parametrize("mode", ["bf16", "bf16_1pass"])
+def test_network_bf16_matches_emulation(P, W, wts, n, mode):
     rng = np.random.default_rng(100 + n)
     c = gen.make_config(1)
     G_all = oracle.aev(c.species, c.coords)
@@ -279,11 +296,12 @@ def test_network_bf16_matches_emulation(P, W, wts, n):
     sp = c.species[pick].copy()
     sp[: min(n, 7)] = np.arange(min(n, 7))
     G = G_all[pick].astype(np.float32)
-    e, g = P.debug_network(W, "bf16", sp, G)
-    e_ref, g_ref = _emulate_bf16_network(wts, sp, G)
-    # remaining differences: FP32 accumulation order and BF16 re-rounding of
+    e, g = P.debug_network(W, mode, sp, G)
+    e_ref, g_ref = _emulate_bf16_network(wts, sp, G, split=(mode == "bf16"))
+    # remaining differences: FP32 accumulation order, and BF16 re-rounding of
     # activations that sit on a rounding boundary
-    assert np.abs(e - e_ref).max() <= 2e-3 * max(1.0, np.abs(e_ref).max()), np.abs(e - e_ref).max()
+    tol_e = 2e-5 if mode == "bf16" else 2e-3
+    assert np.abs(e - e_ref).max() <= tol_e * max(1.0, np.abs(e_ref).max()), np.abs(e - e_ref).max()
     assert np.abs(g - g_ref).max() <= 2e-2 * np.abs(g_ref).max(), (np.abs(g - g_ref).max(), np.abs(g_ref).max())
     assert np.sqrt(np.mean((g - g_ref) ** 2)) <= 2e-3 * np.sqrt(np.mean(g_ref ** 2))
 
