@@ -11,19 +11,26 @@
 // cos theta' cos Z + sin theta' sin Z, so no acos is evaluated.
 //
 // Work decomposition (one warp per atom, 8 warps per block):
-//   * the atom's neighbors within 5.1 A are staged in shared memory as
-//     (dx, dy, dz, r) with their cutoff values; the ones within 3.5 A form
-//     the angular sub-list;
-//   * radial: lane = (half, k): 16 shift lanes x 2 neighbor streams, each
-//     lane owns its own accumulator column per element -> no atomics;
-//   * angular: triples are taken four at a time, lane = (t, z): the lane
+//   * the neighbor list is read 32 entries at a time, one neighbor per lane
+//     (displacement, distance, element, cutoff value in registers); only the
+//     neighbors within 3.5 A are staged in shared memory, as unit vector,
+//     distance, 1/r and cutoff values (the angular sub-list);
+//   * radial (forward): lane = (half, k), 16 shift lanes x 2 neighbors taken
+//     from the lanes that loaded them by shuffles; each lane owns its own
+//     accumulator column per element -> no atomics, fixed order;
+//   * angular: pairs are taken four at a time, lane = (t, z): the lane
 //     evaluates the angle factor of section z and the distance factor of
-//     shift z & 3 for triple t; then, for each of the four triples in turn,
+//     shift z & 3 for pair t; then, for each of the four pairs in turn,
 //     lane (a, z) multiplies the shuffled factors and adds them to its own
 //     column 32 p + 8 a + z (conflict-free, fixed order -> deterministic).
-// The backward recomputes the same terms with their derivatives, contracts
-// them with dE/dG, and accumulates per-neighbor gradients in shared memory
-// before one FP64 atomic per (atom, neighbor, axis) into the global sums.
+// The backward recomputes the terms with their derivatives and contracts
+// them with dE/dG (staged in shared memory): radial per neighbor lane (on
+// the fast path the 16 Gaussians come from a two-sided recurrence started
+// at the nearest shift: 3 exponentials instead of 16), angular per pair
+// group with the four distance factors shared by shuffles and the final
+// vector updates spread over six lanes. Gradients on neighbors go to FP64
+// global sums (radial: per neighbor; angular: accumulated per angular
+// neighbor in shared memory first).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -54,7 +61,6 @@ void init_constants_for_current_device() {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kMaxRad = 160;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <bool FAST>
@@ -67,31 +73,32 @@ struct M<false> {   // accurate FP32 library functions (FP32 path)
     static __device__ __forceinline__ float spi(float x) { return sinpif(x); }
     static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float dv(float a, float b) { return a / b; }
+    static __device__ __forceinline__ float rcp(float x) { return 1.f / x; }
 };
 template <>
 struct M<true> {    // hardware approximations (BF16-network path)
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
-    static __device__ __forceinline__ float pw(float b, float e) { return __powf(b, e); }
+    static __device__ __forceinline__ float pw(float b, float e) { return exp2f(e * __log2f(b)); }
     static __device__ __forceinline__ float cpi(float x) { return __cosf(3.14159265358979f * x); }
     static __device__ __forceinline__ float spi(float x) { return __sinf(3.14159265358979f * x); }
     static __device__ __forceinline__ float sq(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 };
 
-struct NbrStage {
-    float4 d[kMaxRad];    // dx, dy, dz, r of neighbors within 5.1 A
-    float fc[kMaxRad];    // fc(r; 5.1)
-    float dfc[kMaxRad];   // d fc / dr
-    int sp[kMaxRad];      // element
-    int idx[kMaxRad];     // atom index
-    int ang[kMaxAng];     // slot (into the arrays above) of neighbors within 3.5 A
-    float fca[kMaxAng];   // fc(r; 3.5)
-    float dfca[kMaxAng];
+// Angular sub-list of one atom (neighbors within 3.5 A).
+struct AngStage {
+    float4 u[kMaxAng];     // unit vector d / r, and r
+    float invr[kMaxAng];
+    float fc[kMaxAng];     // fc(r; 3.5)
+    float dfc[kMaxAng];    // d fc / dr
+    int sp[kMaxAng];       // element
+    int idx[kMaxAng];      // atom index
 };
 
 constexpr int kAccFloats = 2 * kRadLen + kAngLen;   // two radial halves + angular
-constexpr size_t kAevSmemPerWarp = sizeof(NbrStage) + kAccFloats * sizeof(float);
-constexpr size_t kForceSmemPerWarp = sizeof(NbrStage) + (kAevLen + 3 * kMaxRad) * sizeof(float);
+constexpr size_t kAevSmemPerWarp = sizeof(AngStage) + kAccFloats * sizeof(float);
+constexpr size_t kForceSmemPerWarp = sizeof(AngStage) + (kAevLen + 3 * kMaxAng) * sizeof(float);
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -99,56 +106,51 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Stages atom i's neighbors; returns the radial count, sets the angular one.
-template <bool FAST, bool DERIV>
-__device__ __forceinline__ int stage(const AevArgs& a, int i, int lane, const float4& hi_i, const float4& lo_i,
-                                     NbrStage& s, int& mA) {
-    const int cnt = min(a.nbr_cnt[i], a.cap);
-    const int* row = a.nbr + (size_t)i * a.cap;
-    int mR = 0;
-    mA = 0;
-    for (int base = 0; base < cnt; base += 32) {
-        int q = base + lane;
-        bool inR = false, inA = false;
-        float3 d = make_float3(0.f, 0.f, 0.f);
-        float r = 0.f;
-        int sj = 0, j = 0;
-        if (q < cnt) {
-            j = row[q];
-            float4 hj = a.hi[j], lj = a.lo[j];
-            d = displacement(hi_i, lo_i, hj, lj, a.box);
-            r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-            inR = r < kRcRad;
-            inA = r < kRcAng;
-            sj = species_of(hj);
-        }
-        unsigned bR = __ballot_sync(kFull, inR);
-        unsigned bA = __ballot_sync(kFull, inA);
-        int pR = mR + __popc(bR & lanemask_lt());
-        int pA = mA + __popc(bA & lanemask_lt());
-        if (inR && pR < kMaxRad) {
-            s.d[pR] = make_float4(d.x, d.y, d.z, r);
-            s.sp[pR] = sj;
-            s.idx[pR] = j;
-            s.fc[pR] = 0.5f * M<FAST>::cpi(r * (1.f / kRcRad)) + 0.5f;
-            if (DERIV) s.dfc[pR] = -0.5f * (3.14159265358979f / kRcRad) * M<FAST>::spi(r * (1.f / kRcRad));
-            if (inA && pA < kMaxAng) {
-                s.ang[pA] = pR;
-                s.fca[pA] = 0.5f * M<FAST>::cpi(r * (1.f / kRcAng)) + 0.5f;
-                if (DERIV) s.dfca[pA] = -0.5f * (3.14159265358979f / kRcAng) * M<FAST>::spi(r * (1.f / kRcAng));
-            }
-        }
-        mR += __popc(bR);
-        mA += __popc(bA);
+// One neighbor per lane: displacement, distance, element, atom index.
+struct NbrLane {
+    float3 d;
+    float r;
+    int sp, j;
+    bool inR, inA;
+};
+
+__device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* row, int q, int cnt,
+                                                 const float4& hi_i, const float4& lo_i) {
+    NbrLane nl;
+    nl.d = make_float3(0.f, 0.f, 0.f);
+    nl.r = 1.f;
+    nl.sp = 0;
+    nl.j = 0;
+    nl.inR = nl.inA = false;
+    if (q < cnt) {
+        nl.j = row[q];
+        const float4 hj = a.hi[nl.j], lj = a.lo[nl.j];
+        nl.d = displacement(hi_i, lo_i, hj, lj, a.box);
+        nl.r = sqrtf(nl.d.x * nl.d.x + nl.d.y * nl.d.y + nl.d.z * nl.d.z);
+        nl.inR = nl.r < kRcRad;
+        nl.inA = nl.r < kRcAng;
+        nl.sp = species_of(hj);
     }
-    if (mR > kMaxRad || mA > kMaxAng) {
-        // the evaluation is reported invalid by the host; keep every index in range
-        if (lane == 0) atomicMax(&a.ctr->ang_overflow, max(mR, mA));
-        mR = min(mR, kMaxRad);
-        mA = 0;
+    return nl;
+}
+
+// Appends this chunk's angular neighbors to the stage; returns the new count.
+template <bool FAST>
+__device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage& s, const AevArgs& a) {
+    const unsigned bA = __ballot_sync(kFull, nl.inA);
+    const int pA = mA + __popc(bA & lanemask_lt());
+    if (nl.inA && pA < kMaxAng) {
+        const float ir = M<FAST>::rcp(nl.r);
+        s.u[pA] = make_float4(nl.d.x * ir, nl.d.y * ir, nl.d.z * ir, nl.r);
+        s.invr[pA] = ir;
+        s.fc[pA] = 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcAng)) + 0.5f;
+        s.dfc[pA] = -0.5f * (3.14159265358979f / kRcAng) * M<FAST>::spi(nl.r * (1.f / kRcAng));
+        s.sp[pA] = nl.sp;
+        s.idx[pA] = nl.j;
     }
-    __syncwarp();
-    return mR;
+    const int m = mA + __popc(bA);
+    if (m > kMaxAng && (threadIdx.x & 31) == 0) atomicMax(&a.ctr->ang_overflow, m);
+    return m;
 }
 
 // Next unordered pair (j < k) `step` positions further in row-major order.
@@ -160,30 +162,16 @@ __device__ __forceinline__ void advance_pair(int& j, int& k, int step, int m) {
     }
 }
 
-template <bool FAST, typename OutT>
-__device__ __forceinline__ void store_row(OutT* out, const float* acc, int lane);
+__device__ __forceinline__ float row_value(const float* acc, int c) {
+    return c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
+}
 
-template <>
-__device__ __forceinline__ void store_row<false, float>(float* out, const float* acc, int lane) {
-    for (int c = lane; c < kAevLd; c += 32) {
-        float v = c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
-        out[c] = v;
-    }
-}
-template <>
-__device__ __forceinline__ void store_row<true, float>(float* out, const float* acc, int lane) {
-    store_row<false, float>(out, acc, lane);
-}
 // BF16 row; with out_lo != nullptr also the BF16 rounding of the remainder
 // (G = G_hi + G_lo to ~16 bits), for the split-precision network.
-template <bool FAST>
 __device__ __forceinline__ void store_row_bf16(__nv_bfloat16* out, __nv_bfloat16* out_lo, const float* acc,
                                                int lane) {
     for (int c = 2 * lane; c < kAevLd; c += 64) {
-        float v0, v1;
-        v0 = c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
-        int c1 = c + 1;
-        v1 = c1 < kRadLen ? acc[c1] + acc[kRadLen + c1] : (c1 < kAevLen ? acc[kRadLen + c1] : 0.f);
+        const float v0 = row_value(acc, c), v1 = row_value(acc, c + 1);
         const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
         *reinterpret_cast<__nv_bfloat162*>(out + c) = h;
         if (out_lo) {
@@ -200,71 +188,125 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + w;
     if (i >= a.n) return;
-    NbrStage& s = *reinterpret_cast<NbrStage*>(smem + w * kAevSmemPerWarp);
-    float* acc = reinterpret_cast<float*>(smem + w * kAevSmemPerWarp + sizeof(NbrStage));
+    AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kAevSmemPerWarp);
+    float* acc = reinterpret_cast<float*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
-
     for (int c = lane; c < kAccFloats; c += 32) acc[c] = 0.f;
-    int mA;
-    const int mR = stage<FAST, false>(a, i, lane, hi_i, lo_i, s, mA);
+    __syncwarp();
 
-    // radial: lane (h, k) handles neighbors h, h + 2, ... for shift k
-    {
-        const int k = lane & 15, h = lane >> 4;
-        const float Rk = c_aev.shf_r[k];
-        float* accR = acc + h * kRadLen;
-        for (int q = h; q < mR; q += 2) {
-            float dr = s.d[q].w - Rk;
-            accR[s.sp[q] * kRadShifts + k] += 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) * s.fc[q];
+    const int cnt = min(a.nbr_cnt[i], a.cap);
+    const int* row = a.nbr + (size_t)i * a.cap;
+    const int k = lane & 15, h = lane >> 4;
+    const float Rk = c_aev.shf_r[k];
+    float* accR = acc + h * kRadLen;
+    int mA = 0;
+    // radial terms straight from the lanes that loaded the neighbors
+    for (int base = 0; base < cnt; base += 32) {
+        const NbrLane nl = load_neighbor(a, row, base + lane, cnt, hi_i, lo_i);
+        const float fcr = nl.inR ? 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcRad)) + 0.5f : 0.f;
+        const int nq = min(32, cnt - base);
+        for (int q = 0; q < nq; q += 2) {
+            const int src = q + h;
+            const float rr = __shfl_sync(kFull, nl.r, src);
+            const int ss = __shfl_sync(kFull, nl.sp, src);
+            const float ff = __shfl_sync(kFull, fcr, src);
+            if (src < nq && ff > 0.f) {
+                const float dr = rr - Rk;
+                accR[ss * kRadShifts + k] += 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) * ff;
+            }
         }
+        mA = stage_angular<FAST>(nl, mA, s, a);
     }
-    // angular: four triples per step
+    if (mA > kMaxAng) mA = 0;   // reported as an error by the host; keep every index in range
+    __syncwarp();
+
+    // angular: four pairs per step
     {
         float* accA = acc + 2 * kRadLen;
         const int t = lane >> 3, z = lane & 7;
         const float cz = c_aev.cos_z[z], sz = c_aev.sin_z[z];
         const float Aown = c_aev.shf_a[z & 3];
         const int P = mA * (mA - 1) / 2;
-        int j = 0, k = 1 + t;
-        advance_pair(j, k, 0, mA);
+        int j = 0, kk = 1 + t;
+        advance_pair(j, kk, 0, mA);
         for (int base = 0; base < P; base += 4) {
             float Pz = 0.f, Ra = 0.f, f = 0.f;
             int p = 0;
             if (base + t < P) {
-                const int js = s.ang[j], ks = s.ang[k];
-                const float4 dj = s.d[js], dk = s.d[ks];
-                float cos0 = M<FAST>::dv(dj.x * dk.x + dj.y * dk.y + dj.z * dk.z, dj.w * dk.w);
-                float c = 0.95f * cos0;
-                float sn = M<FAST>::sq(1.f - c * c);
-                float b = 0.5f + 0.5f * (c * cz + sn * sz);
+                const float4 uj = s.u[j], uk = s.u[kk];
+                const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
+                const float sn = M<FAST>::sq(1.f - c * c);
+                const float b = 0.5f + 0.5f * (c * cz + sn * sz);
                 Pz = 2.f * M<FAST>::pw(b, kZeta);
-                float dr = 0.5f * (dj.w + dk.w) - Aown;
+                const float dr = 0.5f * (uj.w + uk.w) - Aown;
                 Ra = M<FAST>::ex(-kEtaAng * dr * dr);
-                f = s.fca[j] * s.fca[k];
-                p = pair_index(s.sp[js], s.sp[ks]);
+                f = s.fc[j] * s.fc[kk];
+                p = pair_index(s.sp[j], s.sp[kk]);
             }
 #pragma unroll
             for (int tt = 0; tt < 4; ++tt) {
-                float Pv = __shfl_sync(kFull, Pz, tt * 8 + (lane & 7));
-                float Rv = __shfl_sync(kFull, Ra, tt * 8 + (lane >> 3));
-                float fv = __shfl_sync(kFull, f, tt * 8);
-                int pv = __shfl_sync(kFull, p, tt * 8);
+                const float Pv = __shfl_sync(kFull, Pz, tt * 8 + (lane & 7));
+                const float Rv = __shfl_sync(kFull, Ra, tt * 8 + (lane >> 3));
+                const float fv = __shfl_sync(kFull, f, tt * 8);
+                const int pv = __shfl_sync(kFull, p, tt * 8);
                 if (base + tt < P) accA[pv * 32 + lane] += Pv * Rv * fv;
             }
-            advance_pair(j, k, 4, mA);
+            advance_pair(j, kk, 4, mA);
         }
     }
     __syncwarp();
     const int si = species_of(hi_i);
-    const int row = row_base(a.ctr->species, si) + a.rank[i];
+    const int rw = row_base(a.ctr->species, si) + a.rank[i];
     if constexpr (sizeof(OutT) == 4) {
-        store_row<FAST, float>(reinterpret_cast<float*>(G) + (size_t)row * kAevLd, acc, lane);
+        float* out = reinterpret_cast<float*>(G) + (size_t)rw * kAevLd;
+        for (int c = lane; c < kAevLd; c += 32) out[c] = row_value(acc, c);
     } else {
-        store_row_bf16<FAST>(reinterpret_cast<__nv_bfloat16*>(G) + (size_t)row * kAevLd,
-                             G_lo ? reinterpret_cast<__nv_bfloat16*>(G_lo) + (size_t)row * kAevLd : nullptr, acc,
-                             lane);
+        store_row_bf16(reinterpret_cast<__nv_bfloat16*>(G) + (size_t)rw * kAevLd,
+                       G_lo ? reinterpret_cast<__nv_bfloat16*>(G_lo) + (size_t)rw * kAevLd : nullptr, acc, lane);
     }
-    if (lane == 0) row_atom[row] = i;
+    if (lane == 0) row_atom[rw] = i;
+}
+
+// d/dr of sum_k g_k 0.25 exp(-eta (r - R_k)^2) fc(r): the radial part of the
+// backward for one neighbor (g = the 16 dE/dG entries of its element).
+template <bool FAST>
+__device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, float dfc) {
+    float s = 0.f;
+    if (!FAST) {
+#pragma unroll
+        for (int k = 0; k < kRadShifts; ++k) {
+            const float dk = r - c_aev.shf_r[k];
+            s += g[k] * M<false>::ex(-kEtaRad * dk * dk) * (-2.f * kEtaRad * dk * fc + dfc);
+        }
+        return 0.25f * s;
+    }
+    // Gaussians by a two-sided recurrence from the shift nearest to r:
+    //   G_{k+1} = G_k m_k, m_{k+1} = m_k C ;  G_{k-1} = G_k n_k, n_{k-1} = n_k C,
+    // m_k = exp(2 eta D d_k - eta D^2), n_k = exp(-2 eta D d_k - eta D^2),
+    // C = exp(-2 eta D^2), d_k = r - R_k, D the shift spacing.
+    const float R0 = c_aev.shf_r[0];
+    const float D = c_aev.shf_r[1] - c_aev.shf_r[0];
+    const float C = __expf(-2.f * kEtaRad * D * D);
+    int kc = __float2int_rn((r - R0) * (1.f / D));
+    kc = min(max(kc, 0), kRadShifts - 1);
+    const float dc = r - c_aev.shf_r[kc];
+    const float Gc = __expf(-kEtaRad * dc * dc);
+    s = g[kc] * Gc * (-2.f * kEtaRad * dc * fc + dfc);
+    float gu = Gc, mu = __expf(2.f * kEtaRad * D * dc - kEtaRad * D * D), du = dc;
+    for (int kk = kc + 1; kk < kRadShifts; ++kk) {
+        gu *= mu;
+        mu *= C;
+        du -= D;
+        s += g[kk] * gu * (-2.f * kEtaRad * du * fc + dfc);
+    }
+    float gd = Gc, nd = __expf(-2.f * kEtaRad * D * dc - kEtaRad * D * D), dd = dc;
+    for (int kk = kc - 1; kk >= 0; --kk) {
+        gd *= nd;
+        nd *= C;
+        dd += D;
+        s += g[kk] * gd * (-2.f * kEtaRad * dd * fc + dfc);
+    }
+    return 0.25f * s;
 }
 
 template <bool FAST>
@@ -274,116 +316,116 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kWarps + w;
     if (i >= a.n) return;
-    NbrStage& s = *reinterpret_cast<NbrStage*>(smem + w * kForceSmemPerWarp);
-    float* gs = reinterpret_cast<float*>(smem + w * kForceSmemPerWarp + sizeof(NbrStage));
+    AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kForceSmemPerWarp);
+    float* gs = reinterpret_cast<float*>(smem + w * kForceSmemPerWarp + sizeof(AngStage));
     float* fslot = gs + kAevLen;
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
     const int si = species_of(hi_i);
-    const int row = row_base(a.ctr->species, si) + a.rank[i];
-    const float* grow = dG + (size_t)row * kAevLd;
+    const int rw = row_base(a.ctr->species, si) + a.rank[i];
+    const float* grow = dG + (size_t)rw * kAevLd;
     for (int c = lane; c < kAevLen; c += 32) gs[c] = grow[c];
-    for (int c = lane; c < 3 * kMaxRad; c += 32) fslot[c] = 0.f;
-    int mA;
-    const int mR = stage<FAST, true>(a, i, lane, hi_i, lo_i, s, mA);
+    for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
+    __syncwarp();
 
     float fix = 0.f, fiy = 0.f, fiz = 0.f;   // dE/dr_i partial sums of this lane
-    // radial: dT/dr = 0.25 exp(-eta (r-R)^2) (-2 eta (r-R) fc + fc')
-    {
-        const int k = lane & 15, h = lane >> 4;
-        const float Rk = c_aev.shf_r[k];
-        const int nq = (mR + 1) >> 1;
-        for (int q2 = 0; q2 < nq; ++q2) {
-            const int q = 2 * q2 + h;
-            float term = 0.f;
-            if (q < mR) {
-                float dr = s.d[q].w - Rk;
-                term = gs[s.sp[q] * kRadShifts + k] * 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) *
-                       (-2.f * kEtaRad * dr * s.fc[q] + s.dfc[q]);
-            }
-            term += __shfl_xor_sync(kFull, term, 8);
-            term += __shfl_xor_sync(kFull, term, 4);
-            term += __shfl_xor_sync(kFull, term, 2);
-            term += __shfl_xor_sync(kFull, term, 1);
-            if (q < mR && k == 0) {
-                const float4 d = s.d[q];
-                const float sc = M<FAST>::dv(term, d.w);
-                fslot[3 * q] += sc * d.x;
-                fslot[3 * q + 1] += sc * d.y;
-                fslot[3 * q + 2] += sc * d.z;
-                fix -= sc * d.x;
-                fiy -= sc * d.y;
-                fiz -= sc * d.z;
-            }
+    const int cnt = min(a.nbr_cnt[i], a.cap);
+    const int* row = a.nbr + (size_t)i * a.cap;
+    int mA = 0;
+    // radial: one neighbor per lane, gradient straight to the FP64 sums
+    for (int base = 0; base < cnt; base += 32) {
+        const NbrLane nl = load_neighbor(a, row, base + lane, cnt, hi_i, lo_i);
+        if (nl.inR) {
+            const float x = nl.r * (1.f / kRcRad);
+            const float fc = 0.5f * M<FAST>::cpi(x) + 0.5f;
+            const float dfc = -0.5f * (3.14159265358979f / kRcRad) * M<FAST>::spi(x);
+            const float sc = radial_dEdr<FAST>(gs + nl.sp * kRadShifts, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
+            const float gx = sc * nl.d.x, gy = sc * nl.d.y, gz = sc * nl.d.z;
+            atomicAdd(&grad[3 * (size_t)nl.j], (double)gx);
+            atomicAdd(&grad[3 * (size_t)nl.j + 1], (double)gy);
+            atomicAdd(&grad[3 * (size_t)nl.j + 2], (double)gz);
+            fix -= gx;
+            fiy -= gy;
+            fiz -= gz;
         }
+        mA = stage_angular<FAST>(nl, mA, s, a);
     }
+    if (mA > kMaxAng) mA = 0;
     __syncwarp();
+
     // angular
     {
         const int t = lane >> 3, z = lane & 7;
         const float cz = c_aev.cos_z[z], sz = c_aev.sin_z[z];
+        const float Aown = c_aev.shf_a[z & 3];
         const int P = mA * (mA - 1) / 2;
-        int j = 0, k = 1 + t;
-        advance_pair(j, k, 0, mA);
+        int j = 0, kk = 1 + t;
+        advance_pair(j, kk, 0, mA);
         for (int base = 0; base < P; base += 4) {
             const bool valid = base + t < P;
-            float Sc = 0.f, Srj = 0.f, Srk = 0.f;
-            float4 dj = make_float4(0.f, 0.f, 0.f, 1.f), dk = dj;
-            int js = 0, ks = 0;
-            float cos0 = 0.f;
+            float4 uj = make_float4(1.f, 0.f, 0.f, 1.f), uk = uj;
+            float cos0 = 0.f, Pz = 0.f, dPdc = 0.f, rbar = 0.f, Ra = 0.f;
+            float fj = 0.f, fk = 0.f, dfj = 0.f, dfk = 0.f;
+            int p = 0;
             if (valid) {
-                js = s.ang[j];
-                ks = s.ang[k];
-                dj = s.d[js];
-                dk = s.d[ks];
-                cos0 = M<FAST>::dv(dj.x * dk.x + dj.y * dk.y + dj.z * dk.z, dj.w * dk.w);
+                uj = s.u[j];
+                uk = s.u[kk];
+                cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
                 const float c = 0.95f * cos0;
                 const float sn = M<FAST>::sq(1.f - c * c);
                 const float cm = c * cz + sn * sz;
                 const float sm = sn * cz - c * sz;
                 const float b = 0.5f + 0.5f * cm;
-                const float Pz = 2.f * M<FAST>::pw(b, kZeta);
-                const float dPdc = M<FAST>::dv(kZeta * Pz * sm, 2.f * b * sn);
-                const float fj = s.fca[j], fk = s.fca[k], dfj = s.dfca[j], dfk = s.dfca[k];
-                const float f = fj * fk;
-                const float rbar = 0.5f * (dj.w + dk.w);
-                const int p = pair_index(s.sp[js], s.sp[ks]);
-                const float* gp = gs + kRadLen + 32 * p + z;
+                Pz = 2.f * M<FAST>::pw(b, kZeta);
+                dPdc = kZeta * Pz * sm * M<FAST>::rcp(2.f * b * sn);
+                rbar = 0.5f * (uj.w + uk.w);
+                const float dr = rbar - Aown;
+                Ra = M<FAST>::ex(-kEtaAng * dr * dr);
+                fj = s.fc[j];
+                fk = s.fc[kk];
+                dfj = s.dfc[j];
+                dfk = s.dfc[kk];
+                p = pair_index(s.sp[j], s.sp[kk]);
+            }
+            // distance factors of the four shifts from the lanes that computed them
+            float S1 = 0.f, S2 = 0.f;   // sum_a g R_a, sum_a g dR_a/drbar
+            const float* gp = gs + kRadLen + 32 * p + z;
 #pragma unroll
-                for (int aa = 0; aa < kAngA; ++aa) {
-                    const float dr = rbar - c_aev.shf_a[aa];
-                    const float R = M<FAST>::ex(-kEtaAng * dr * dr);
-                    const float dR = -2.f * kEtaAng * dr * R;
+            for (int aa = 0; aa < kAngA; ++aa) {
+                const float R = __shfl_sync(kFull, Ra, (lane & ~7) + aa);
+                if (valid) {
                     const float gg = gp[8 * aa];
-                    Sc += gg * dPdc * R * f;
-                    Srj += gg * Pz * (0.5f * dR * f + R * dfj * fk);
-                    Srk += gg * Pz * (0.5f * dR * f + R * fj * dfk);
+                    const float dR = -2.f * kEtaAng * (rbar - c_aev.shf_a[aa]) * R;
+                    S1 = fmaf(gg, R, S1);
+                    S2 = fmaf(gg, dR, S2);
                 }
             }
+            const float f = fj * fk;
+            float Sc = dPdc * f * S1;
+            float Srj = Pz * (0.5f * f * S2 + dfj * fk * S1);
+            float Srk = Pz * (0.5f * f * S2 + fj * dfk * S1);
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {
                 Sc += __shfl_xor_sync(kFull, Sc, o);
                 Srj += __shfl_xor_sync(kFull, Srj, o);
                 Srk += __shfl_xor_sync(kFull, Srk, o);
             }
-            if (valid && z == 0) {
-                const float rj = dj.w, rk = dk.w;
-                const float A = 0.95f * Sc * M<FAST>::dv(1.f, rj * rk);
-                const float Bj = 0.95f * Sc * cos0 * M<FAST>::dv(1.f, rj * rj) - M<FAST>::dv(Srj, rj);
-                const float Bk = 0.95f * Sc * cos0 * M<FAST>::dv(1.f, rk * rk) - M<FAST>::dv(Srk, rk);
-                // dE/d(d_ij) = A d_ik - Bj d_ij ; dE/d(d_ik) = A d_ij - Bk d_ik
-                const float gjx = A * dk.x - Bj * dj.x, gjy = A * dk.y - Bj * dj.y, gjz = A * dk.z - Bj * dj.z;
-                const float gkx = A * dj.x - Bk * dk.x, gky = A * dj.y - Bk * dk.y, gkz = A * dj.z - Bk * dk.z;
-                atomicAdd(&fslot[3 * js], gjx);
-                atomicAdd(&fslot[3 * js + 1], gjy);
-                atomicAdd(&fslot[3 * js + 2], gjz);
-                atomicAdd(&fslot[3 * ks], gkx);
-                atomicAdd(&fslot[3 * ks + 1], gky);
-                atomicAdd(&fslot[3 * ks + 2], gkz);
-                fix -= gjx + gkx;
-                fiy -= gjy + gky;
-                fiz -= gjz + gkz;
+            if (valid && z < 6) {
+                // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k;
+                // lane z takes one of the six components
+                const bool onk = z >= 3;
+                const int cpt = onk ? z - 3 : z;
+                const float4 ua = onk ? uk : uj, ub = onk ? uj : uk;
+                const float ia = onk ? s.invr[kk] : s.invr[j];
+                const float Sr = onk ? Srk : Srj;
+                const float va = cpt == 0 ? ua.x : (cpt == 1 ? ua.y : ua.z);
+                const float vb = cpt == 0 ? ub.x : (cpt == 1 ? ub.y : ub.z);
+                const float gcomp = 0.95f * Sc * ia * (vb - cos0 * va) + Sr * va;
+                atomicAdd(&fslot[3 * (onk ? kk : j) + cpt], gcomp);
+                if (cpt == 0) fix -= gcomp;
+                else if (cpt == 1) fiy -= gcomp;
+                else fiz -= gcomp;
             }
-            advance_pair(j, k, 4, mA);
+            advance_pair(j, kk, 4, mA);
         }
     }
     __syncwarp();
@@ -398,11 +440,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
         atomicAdd(&grad[3 * (size_t)i + 1], (double)fiy);
         atomicAdd(&grad[3 * (size_t)i + 2], (double)fiz);
     }
-    for (int q = lane; q < mR; q += 32) {
-        const int j = s.idx[q];
-        atomicAdd(&grad[3 * (size_t)j], (double)fslot[3 * q]);
-        atomicAdd(&grad[3 * (size_t)j + 1], (double)fslot[3 * q + 1]);
-        atomicAdd(&grad[3 * (size_t)j + 2], (double)fslot[3 * q + 2]);
+    for (int q = lane; q < mA; q += 32) {
+        const int jj = s.idx[q];
+        atomicAdd(&grad[3 * (size_t)jj], (double)fslot[3 * q]);
+        atomicAdd(&grad[3 * (size_t)jj + 1], (double)fslot[3 * q + 1]);
+        atomicAdd(&grad[3 * (size_t)jj + 2], (double)fslot[3 * q + 2]);
     }
 }
 
