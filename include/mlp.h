@@ -216,8 +216,10 @@ MLP_API int mlp_wait(mlp_server *s, mlp_ticket t, int64_t timeout_ns, double *en
 
 typedef struct {
     int64_t submitted, completed, batches, atoms;
-    int64_t inflight_bytes, peak_inflight_bytes;
+    int64_t inflight_bytes, peak_inflight_bytes;  /* device bytes held by batches in flight */
     double mean_batch_atoms;
+    int64_t slot_bytes;                           /* device bytes reserved per slot        */
+    int32_t slots;                                /* slots created (<= streams, by budget) */
 } mlp_server_stats;
 
 MLP_API int mlp_server_get_stats(mlp_server *s, mlp_server_stats *out);

@@ -52,7 +52,8 @@ class ServerOpts(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("atoms", ctypes.c_int64), ("inflight_bytes", ctypes.c_int64),
-                ("peak_inflight_bytes", ctypes.c_int64), ("mean_batch_atoms", ctypes.c_double)]
+                ("peak_inflight_bytes", ctypes.c_int64), ("mean_batch_atoms", ctypes.c_double),
+                ("slot_bytes", ctypes.c_int64), ("slots", ctypes.c_int32)]
 
 
 vp = ctypes.c_void_p

@@ -433,6 +433,8 @@ int mlp_server_get_stats(mlp_server* S, mlp_server_stats* out) {
     *out = S->st;
     out->inflight_bytes = S->inflight_bytes;
     out->mean_batch_atoms = S->st.batches ? (double)S->st.atoms / (double)S->st.batches : 0.0;
+    out->slot_bytes = (int64_t)slot_bytes(S->o);
+    out->slots = (int32_t)S->slots.size();
     return MLP_OK;
 }
 
