@@ -93,6 +93,29 @@ int sys_finish_pending(mlp_system* s) {
     cudaError_t e = cudaEventSynchronize(s->done);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize");
     s->pending = false;
+    int rc = check_counters(s->ws);
+    if (rc) return rc;
+    // errors of earlier evaluations that were not checked one by one
+    int sticky = 0;
+    e = cudaMemcpy(&sticky, s->ws.err_sticky, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(error flags)");
+    if (sticky) {
+        cudaMemset(s->ws.err_sticky, 0, sizeof(int));
+        if (sticky & 4) return set_error(MLP_EINVAL, "element code outside [0, 7) in an earlier evaluation");
+        return set_error(MLP_EOVERFLOW, "neighbor capacity exceeded in an earlier evaluation");
+    }
+    return MLP_OK;
+}
+
+// Device-path calls do not wait for the previous evaluation: its flags are
+// checked here when it has already finished, otherwise they stay in the
+// device's sticky error word until mlp_sync (or a host-path call) reads them.
+int sys_check_if_done(mlp_system* s) {
+    if (!s->pending) return MLP_OK;
+    cudaError_t q = cudaEventQuery(s->done);
+    if (q == cudaErrorNotReady) return MLP_OK;
+    if (q != cudaSuccess) return cuda_error(q, "cudaEventQuery");
+    s->pending = false;
     return check_counters(s->ws);
 }
 
@@ -466,7 +489,7 @@ int mlp_energy_forces(mlp_system* s, const double* coords, double* energy, float
 int mlp_energy_forces_device(mlp_system* s, const double* d_coords, double* d_energy, float* d_forces, void* stream) {
     clear_error();
     if (!s || !d_coords || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
-    int rc = sys_finish_pending(s);
+    int rc = sys_check_if_done(s);
     if (rc) return rc;
     s->kept = false;
     EvalSpec sp = sys_spec(s, d_coords);
@@ -478,7 +501,7 @@ int mlp_energy_forces_device(mlp_system* s, const double* d_coords, double* d_en
 int mlp_forward_device(mlp_system* s, const double* d_coords, double* d_energy, int keep_aev, void* stream) {
     clear_error();
     if (!s || !d_coords || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
-    int rc = sys_finish_pending(s);
+    int rc = sys_check_if_done(s);
     if (rc) return rc;
     EvalSpec sp = sys_spec(s, d_coords);
     sp.network_backward = false;
@@ -493,7 +516,7 @@ int mlp_backward_device(mlp_system* s, const double* d_coords, const double* d_g
                         void* stream) {
     clear_error();
     if (!s || !d_coords || !d_grad_coords) return set_error(MLP_EINVAL, "NULL argument");
-    int rc = sys_finish_pending(s);
+    int rc = sys_check_if_done(s);
     if (rc) return rc;
     EvalSpec sp = sys_spec(s, d_coords);
     sp.reuse_aev = s->kept && s->kept_coords == d_coords;

@@ -76,6 +76,7 @@ void plan_workspace(Plan& P, Workspace& ws) {
     P.add(&ws.e, n);
     P.add(&ws.dG, R * kAevLd);
     P.add(&ws.tc_err, 4);
+    P.add(&ws.err_sticky, 4);
     if (ws.precision == 0) {
         P.add(&ws.G32, R * kAevLd);
         P.add(&ws.fb.Z1, R * kH1);
@@ -215,7 +216,7 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.grad, fast);
     launch_finalize(st, sp.n_mols, sp.d_mol_start, n, ws.e, ws.grad, sp.energy ? sp.d_E : nullptr,
-                    sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign);
+                    sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign, ws.ctr, ws.err_sticky);
     ce = cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (ce != cudaSuccess) return cuda_error(ce, "cudaMemcpyAsync(counters)");
     ce = cudaGetLastError();

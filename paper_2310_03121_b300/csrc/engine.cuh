@@ -67,6 +67,7 @@ struct Workspace {
     int *cell_of_atom = nullptr, *cell_rank = nullptr, *cell_count = nullptr, *cell_start = nullptr,
         *cell_atoms = nullptr;
     int* tc_err = nullptr;
+    int* err_sticky = nullptr;   // error flags of all evaluations since the host last cleared them
     Counters* h_ctr = nullptr;   // pinned host copy of the counters of the last evaluation
 };
 

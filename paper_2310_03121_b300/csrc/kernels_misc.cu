@@ -14,7 +14,13 @@ constexpr int kEBlock = 128;
 // mol_start == nullptr means one molecule made of all n_atoms atoms.
 __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_atoms, const float* __restrict__ e,
                            const double* __restrict__ grad, double* __restrict__ E, float* __restrict__ F,
-                           const double* __restrict__ grad_scale, float sign) {
+                           const double* __restrict__ grad_scale, float sign, const Counters* __restrict__ ctr,
+                           int* __restrict__ sticky) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && sticky) {
+        // error flags of this evaluation, kept until the host reads and clears them
+        const int f = (ctr->nbr_overflow ? 1 : 0) | (ctr->ang_overflow ? 2 : 0) | (ctr->bad_species ? 4 : 0);
+        if (f) atomicOr(sticky, f);
+    }
     if ((int)blockIdx.x < n_mols) {
         const int m = blockIdx.x;
         const int a = mol_start ? mol_start[m] : 0;
@@ -34,6 +40,7 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
         return;
     }
     const double scale = (grad_scale ? *grad_scale : 1.0) * (double)sign;
+    if (!F) return;
     const int fb = blockIdx.x - n_mols;
     const int nfb = gridDim.x - n_mols;
     for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) F[q] = (float)(scale * grad[q]);
@@ -42,13 +49,14 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
 }  // namespace
 
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
-                     const double* grad, double* E, float* F, const double* grad_scale, float sign) {
+                     const double* grad, double* E, float* F, const double* grad_scale, float sign,
+                     const Counters* ctr, int* sticky) {
     const int fblocks = F ? (3 * n_atoms + kEBlock * 4 - 1) / (kEBlock * 4) : 0;
     const int eblocks = E ? n_mols : 0;
-    if (eblocks + fblocks == 0) return;
+    const int blocks = eblocks + fblocks > 0 ? eblocks + fblocks : 1;
     MLP_LAUNCH("finalize", st,
-               k_finalize<<<eblocks + fblocks, kEBlock, 0, st>>>(eblocks, mol_start, n_atoms, e, grad, E, F,
-                                                                 grad_scale, sign));
+               k_finalize<<<blocks, kEBlock, 0, st>>>(eblocks, mol_start, n_atoms, e, grad, E, F, grad_scale, sign,
+                                                      ctr, sticky));
 }
 
 }  // namespace mlp

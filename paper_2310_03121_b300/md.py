@@ -1,0 +1,130 @@
+"""Velocity-Verlet test harness around the energy+force evaluation.
+
+Not part of the evaluation itself: a driver that integrates Newton's
+equations with the library's forces, to check energy conservation (the
+672-atom ligand-in-water system) and to time a persistent system with a
+skin neighbor list (the 21,080-atom periodic box: list radius 5.1 + 0.5 A,
+rebuilt every 10 steps or when an atom moved more than half the skin).
+
+Units: A, fs, amu, eV. Acceleration F/m in eV/(A amu) = 9.6485e-3 A/fs^2;
+kinetic energy 0.5 m v^2 (amu A^2/fs^2) = 103.6427 eV per unit.
+Positions and velocities stay on the device; the host reads the potential
+and kinetic energy every `report_every` steps.
+
+    python -m paper_2310_03121_b300.md --workload 1 --steps 10000 --precision fp32
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import time
+
+import numpy as np
+
+ACC = 9.648533212e-3        # (eV / A / amu) -> A / fs^2
+KE = 103.6426965           # amu A^2 / fs^2 -> eV
+KB = 8.617333262e-5         # eV / K
+MASSES = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
+
+
+def _min_pair_distance_ok(coords_t, cell, limit, lib):
+    """True if no pair is closer than `limit` (allocation-free neighbor search)."""
+    import torch
+
+    n = coords_t.shape[0]
+    counts = torch.zeros(n, dtype=torch.int32, device=coords_t.device)
+    lst = torch.zeros((n, 4), dtype=torch.int32, device=coords_t.device)
+    cl = None if cell is None else np.ascontiguousarray(cell, dtype=np.float64)
+    rc = lib.mlp_neighbors_static(ctypes.c_void_p(coords_t.data_ptr()), n,
+                                  None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  float(limit), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(lst.data_ptr()),
+                                  4, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        return True   # too large for the static search: skip the guard
+    return int(counts.max().item()) == 0
+
+
+def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=300.0, seed=0, report_every=10,
+        guard_every=1000, min_pair=0.5):
+    """Integrates `steps` velocity-Verlet steps; returns a dict of results."""
+    import torch
+
+    from . import _lib
+
+    dev = torch.device("cuda")
+    m = torch.as_tensor(MASSES[np.asarray(species)], dtype=torch.float64, device=dev)[:, None]
+    x = torch.as_tensor(np.asarray(coords, dtype=np.float64), device=dev).contiguous()
+    rng = np.random.default_rng(seed)
+    sigma = np.sqrt(KB * temperature / (MASSES[np.asarray(species)] * KE))[:, None]
+    v0 = rng.normal(size=(len(species), 3)) * sigma
+    mass = MASSES[np.asarray(species)][:, None]
+    v0 -= (mass * v0).sum(0) / mass.sum()              # no centre-of-mass motion
+    v = torch.as_tensor(v0, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    F = torch.zeros((len(species), 3), dtype=torch.float32, device=dev)
+    lib = _lib.load()
+    system.energy_forces_device(x, E, F)
+    a = F.double() * (ACC / m)
+    t_series, e_pot, e_kin = [], [], []
+    aborted = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(1, steps + 1):
+        v.add_(a, alpha=0.5 * dt_fs)
+        x.add_(v, alpha=dt_fs)
+        system.energy_forces_device(x, E, F)
+        a = F.double() * (ACC / m)
+        v.add_(a, alpha=0.5 * dt_fs)
+        if step % report_every == 0:
+            ke = 0.5 * KE * float((m * v * v).sum().item())
+            t_series.append(step * dt_fs)
+            e_pot.append(float(E.item()))
+            e_kin.append(ke)
+        if guard_every and step % guard_every == 0 and not _min_pair_distance_ok(x, cell, min_pair, lib):
+            aborted = f"pair closer than {min_pair} A at step {step}"
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    system.sync()
+    n = len(species)
+    tt = np.array(t_series)
+    et = np.array(e_pot) + np.array(e_kin)
+    slope = float(np.polyfit(tt, et, 1)[0]) if len(tt) > 2 else float("nan")   # eV / fs
+    done = step if aborted is None else step
+    return {"atoms": n, "steps": done, "dt_fs": dt_fs, "wall_s": wall, "atom_steps_per_s": n * done / wall,
+            "drift_eV_per_atom_per_ps": slope * 1000.0 / n,
+            "etot_rms_fluct_eV_per_atom": float(np.std(et - np.polyval(np.polyfit(tt, et, 1), tt)) / n)
+            if len(tt) > 2 else None,
+            "etot_first": float(et[0]) if len(et) else None, "etot_last": float(et[-1]) if len(et) else None,
+            "temperature_K_last": float(2 * e_kin[-1] / (3 * n * KB)) if e_kin else None, "aborted": aborted}
+
+
+def main():
+    import gen
+
+    from . import System, Weights
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 4])
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--dt", type=float, default=0.5)
+    ap.add_argument("--precision", default=None)
+    args = ap.parse_args()
+    c = gen.make_config(args.workload)
+    W = Weights(gen.make_weights())
+    if args.workload == 1:
+        steps = args.steps or 10000
+        prec = args.precision or "fp32"
+        s = System(W, c.species, c.coords, c.cell, precision=prec)
+    else:
+        steps = args.steps or 1000
+        prec = args.precision or "bf16"
+        s = System(W, c.species, c.coords, c.cell, precision=prec, skin=0.5)
+    res = run(s, c.species, c.coords, c.cell, dt_fs=args.dt, steps=steps)
+    res.update({"workload": c.name, "precision": prec})
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
