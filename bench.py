@@ -305,7 +305,7 @@ def run_ours(args):
                          "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
               "clocks": clocks, "gpu_launches": int(round(launches / max(1, args.steps)))}
     result["gpu_launches_timed_total"] = int(launches)
-    result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec)
+    result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec, term_counts(stream))
     result["kernels_ms_per_step"] = {k: v[0] / max(1, args.profile_steps) for k, v in sorted(prof.items())}
     result["kernels_timing"] = ("CUDA events around every launch, on the launching stream, in "
                                 f"{args.profile_steps} extra steps run on one stream after the timed steps")
@@ -350,7 +350,34 @@ def run_ours(args):
     return 0
 
 
-def roofline(prof, n_atoms, steps, prec):
+# Counted FP32 operations of the algorithm per term (FMA = 2, transcendental = 1),
+# from the loop bodies of the kernels:
+FLOP_AEV_PER_NEIGHBOR = 100     # 16 radial shifts + cutoff
+FLOP_AEV_PER_PAIR = 180         # geometry, 8 angle factors, 4 distance factors, 32 products
+FLOP_FORCE_PER_NEIGHBOR = 175   # 16 radial shifts with derivatives + cutoff + vector
+FLOP_FORCE_PER_PAIR = 360       # geometry, 32 terms with derivatives, two gradient vectors
+
+
+def term_counts(stream):
+    """Mean neighbors within 5.1 A and unordered neighbor pairs within 3.5 A per
+    atom of the stream (the work units of the AEV and force kernels)."""
+    from scipy.spatial import cKDTree
+
+    nr = npairs = 0
+    for m in range(stream.count):
+        a, b = int(stream.mol_start[m]), int(stream.mol_start[m + 1])
+        t = cKDTree(stream.coords[a:b])
+        nr += 2 * len(t.query_pairs(5.1, output_type="ndarray"))
+        na = np.zeros(b - a, dtype=np.int64)
+        pr = t.query_pairs(3.5, output_type="ndarray")
+        np.add.at(na, pr[:, 0], 1)
+        np.add.at(na, pr[:, 1], 1)
+        npairs += int((na * (na - 1) // 2).sum())
+    n = stream.n_atoms
+    return nr / n, npairs / n
+
+
+def roofline(prof, n_atoms, steps, prec, terms):
     peaks, src = measured_peaks()
     if not prof:
         return None
@@ -359,31 +386,33 @@ def roofline(prof, n_atoms, steps, prec):
     launches_per_step = cnt / max(1, steps)
     atoms_per_launch = n_atoms / max(1e-9, launches_per_step)
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    nrad, npair = terms
+    base = {"kernel": name, "launch_ms": avg_ms, "units_per_launch": atoms_per_launch, "traffic": None}
     if name.startswith("mlp_tc"):
-        flop = (MLP_FLOP_FWD + MLP_FLOP_BWD) * atoms_per_launch
-        ach = flop / (avg_ms * 1e-3) / 1e12
+        per_atom = (3 * MLP_FLOP_FWD if prec == "bf16" else MLP_FLOP_FWD) + MLP_FLOP_BWD
+        ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
-        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside a long step",
-                "work": "1,351,680 FLOP per atom (network forward + backward)"}
+        base.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside a long step",
+                     "work": f"{per_atom} FLOP per atom"})
+        return base
     if name.startswith("mlp_f32"):
-        # each FP32 GEMM launch: its own share of the 1.35 MFLOP per atom
         layer_flop = {"mlp_f32_l1": 2 * 1008 * 256, "mlp_f32_l2": 2 * 256 * 192, "mlp_f32_l3": 2 * 192 * 160,
                       "mlp_f32_b3": 2 * 160 * 192, "mlp_f32_b2": 2 * 192 * 256, "mlp_f32_b1": 2 * 256 * 1008}
-        flop = layer_flop.get(name, 0) * atoms_per_launch
-        ach = flop / (avg_ms * 1e-3) / 1e12
-        peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 FLOP x max SM clock"}
-    # AEV / forces: plain FP32 ALU + MUFU; report issue-limited FP32 rate
-    per_atom = {"aev": 36000.0, "forces": 72000.0}.get(name, 0.0)
+        per_atom = layer_flop.get(name, 0)
+    elif name == "forces":
+        per_atom = FLOP_FORCE_PER_NEIGHBOR * nrad + FLOP_FORCE_PER_PAIR * npair
+    elif name == "aev":
+        per_atom = FLOP_AEV_PER_NEIGHBOR * nrad + FLOP_AEV_PER_PAIR * npair
+    else:
+        per_atom = 0
     ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
-    peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_source": "FP32 FMA peak from unit counts and max SM clock",
-            "work": f"{per_atom:.0f} FP32 FLOP per atom (estimate at water density)"}
+    base.update({"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                 "peak_source": "FP32: 148 SMs x 128 lanes x 2 FLOP x max SM clock (unit counts)",
+                 "work": f"{per_atom:.0f} FP32 operations per atom ({nrad:.1f} neighbors < 5.1 A, "
+                         f"{npair:.1f} pairs < 3.5 A per atom)"})
+    return base
 
 
 def sweep(srv, stream, args):

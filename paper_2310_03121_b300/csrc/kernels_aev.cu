@@ -24,13 +24,14 @@
 //     lane (a, z) multiplies the shuffled factors and adds them to its own
 //     column 32 p + 8 a + z (conflict-free, fixed order -> deterministic).
 // The backward recomputes the terms with their derivatives and contracts
-// them with dE/dG (staged in shared memory): radial per neighbor lane (on
-// the fast path the 16 Gaussians come from a two-sided recurrence started
-// at the nearest shift: 3 exponentials instead of 16), angular per pair
-// group with the four distance factors shared by shuffles and the final
-// vector updates spread over six lanes. Gradients on neighbors go to FP64
-// global sums (radial: per neighbor; angular: accumulated per angular
-// neighbor in shared memory first).
+// them with dE/dG (staged in shared memory): radial one neighbor per lane
+// (on the fast path the 16 Gaussians come from a two-sided recurrence started
+// at the nearest shift: 3 exponentials instead of 16), angular one pair per
+// lane with its 4 distance and 8 angle factors in registers (the angular
+// block of dE/dG is stored rotated per element pair so that lanes reading the
+// same column of different pair blocks do not share a bank). Gradients on
+// neighbors go to FP64 global sums (radial: per neighbor; angular:
+// accumulated per angular neighbor in shared memory first).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -323,7 +324,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
     const int si = species_of(hi_i);
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
     const float* grow = dG + (size_t)rw * kAevLd;
-    for (int c = lane; c < kAevLen; c += 32) gs[c] = grow[c];
+    // angular block stored rotated: column c of element-pair block p at (c + p) mod 32, so that lanes
+    // reading the same column of different blocks hit different banks
+    for (int c = lane; c < kAevLen; c += 32) {
+        int dst = c;
+        if (c >= kRadLen) {
+            const int rel = c - kRadLen, pb = rel >> 5;
+            dst = kRadLen + 32 * pb + (((rel & 31) + pb) & 31);
+        }
+        gs[dst] = grow[c];
+    }
     for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
     __syncwarp();
 
@@ -352,80 +362,71 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
     if (mA > kMaxAng) mA = 0;
     __syncwarp();
 
-    // angular
+    // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers
     {
-        const int t = lane >> 3, z = lane & 7;
-        const float cz = c_aev.cos_z[z], sz = c_aev.sin_z[z];
-        const float Aown = c_aev.shf_a[z & 3];
         const int P = mA * (mA - 1) / 2;
-        int j = 0, kk = 1 + t;
+        int j = 0, kk = 1 + lane;
         advance_pair(j, kk, 0, mA);
-        for (int base = 0; base < P; base += 4) {
-            const bool valid = base + t < P;
-            float4 uj = make_float4(1.f, 0.f, 0.f, 1.f), uk = uj;
-            float cos0 = 0.f, Pz = 0.f, dPdc = 0.f, rbar = 0.f, Ra = 0.f;
-            float fj = 0.f, fk = 0.f, dfj = 0.f, dfk = 0.f;
-            int p = 0;
-            if (valid) {
-                uj = s.u[j];
-                uk = s.u[kk];
-                cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        for (int base = 0; base < P; base += 32) {
+            if (base + lane < P) {
+                const float4 uj = s.u[j], uk = s.u[kk];
+                const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
                 const float c = 0.95f * cos0;
                 const float sn = M<FAST>::sq(1.f - c * c);
-                const float cm = c * cz + sn * sz;
-                const float sm = sn * cz - c * sz;
-                const float b = 0.5f + 0.5f * cm;
-                Pz = 2.f * M<FAST>::pw(b, kZeta);
-                dPdc = kZeta * Pz * sm * M<FAST>::rcp(2.f * b * sn);
-                rbar = 0.5f * (uj.w + uk.w);
-                const float dr = rbar - Aown;
-                Ra = M<FAST>::ex(-kEtaAng * dr * dr);
-                fj = s.fc[j];
-                fk = s.fc[kk];
-                dfj = s.dfc[j];
-                dfk = s.dfc[kk];
-                p = pair_index(s.sp[j], s.sp[kk]);
-            }
-            // distance factors of the four shifts from the lanes that computed them
-            float S1 = 0.f, S2 = 0.f;   // sum_a g R_a, sum_a g dR_a/drbar
-            const float* gp = gs + kRadLen + 32 * p + z;
+                const float isn = M<FAST>::rcp(sn);
+                const float rbar = 0.5f * (uj.w + uk.w);
+                const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
+                const int p = pair_index(s.sp[j], s.sp[kk]);
+                float R[kAngA], dR[kAngA];
 #pragma unroll
-            for (int aa = 0; aa < kAngA; ++aa) {
-                const float R = __shfl_sync(kFull, Ra, (lane & ~7) + aa);
-                if (valid) {
-                    const float gg = gp[8 * aa];
-                    const float dR = -2.f * kEtaAng * (rbar - c_aev.shf_a[aa]) * R;
-                    S1 = fmaf(gg, R, S1);
-                    S2 = fmaf(gg, dR, S2);
+                for (int aa = 0; aa < kAngA; ++aa) {
+                    const float dr = rbar - c_aev.shf_a[aa];
+                    R[aa] = M<FAST>::ex(-kEtaAng * dr * dr);
+                    dR[aa] = -2.f * kEtaAng * dr * R[aa];
                 }
-            }
-            const float f = fj * fk;
-            float Sc = dPdc * f * S1;
-            float Srj = Pz * (0.5f * f * S2 + dfj * fk * S1);
-            float Srk = Pz * (0.5f * f * S2 + fj * dfk * S1);
+                const float* gp = gs + kRadLen + 32 * p;
+                float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                Sc += __shfl_xor_sync(kFull, Sc, o);
-                Srj += __shfl_xor_sync(kFull, Srj, o);
-                Srk += __shfl_xor_sync(kFull, Srk, o);
+                for (int z = 0; z < kAngZ; ++z) {
+                    const float cm = c * c_aev.cos_z[z] + sn * c_aev.sin_z[z];
+                    const float sm = sn * c_aev.cos_z[z] - c * c_aev.sin_z[z];
+                    const float b = 0.5f + 0.5f * cm;
+                    const float Pz = 2.f * M<FAST>::pw(b, kZeta);
+                    const float dPdc = 0.5f * kZeta * Pz * sm * M<FAST>::rcp(b) * isn;
+                    float S1 = 0.f, S2 = 0.f;
+#pragma unroll
+                    for (int aa = 0; aa < kAngA; ++aa) {
+                        const float gg = gp[(8 * aa + z + p) & 31];
+                        S1 = fmaf(gg, R[aa], S1);
+                        S2 = fmaf(gg, dR[aa], S2);
+                    }
+                    Sc = fmaf(dPdc, S1, Sc);
+                    T1 = fmaf(Pz, S1, T1);
+                    T2 = fmaf(Pz, S2, T2);
+                }
+                const float f = fj * fk;
+                Sc *= f;
+                const float Srj = 0.5f * f * T2 + dfj * fk * T1;
+                const float Srk = 0.5f * f * T2 + fj * dfk * T1;
+                // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k
+                const float aj = 0.95f * Sc * s.invr[j], ak = 0.95f * Sc * s.invr[kk];
+                const float gjx = aj * (uk.x - cos0 * uj.x) + Srj * uj.x;
+                const float gjy = aj * (uk.y - cos0 * uj.y) + Srj * uj.y;
+                const float gjz = aj * (uk.z - cos0 * uj.z) + Srj * uj.z;
+                const float gkx = ak * (uj.x - cos0 * uk.x) + Srk * uk.x;
+                const float gky = ak * (uj.y - cos0 * uk.y) + Srk * uk.y;
+                const float gkz = ak * (uj.z - cos0 * uk.z) + Srk * uk.z;
+                atomicAdd(&fslot[3 * j], gjx);
+                atomicAdd(&fslot[3 * j + 1], gjy);
+                atomicAdd(&fslot[3 * j + 2], gjz);
+                atomicAdd(&fslot[3 * kk], gkx);
+                atomicAdd(&fslot[3 * kk + 1], gky);
+                atomicAdd(&fslot[3 * kk + 2], gkz);
+                fix -= gjx + gkx;
+                fiy -= gjy + gky;
+                fiz -= gjz + gkz;
             }
-            if (valid && z < 6) {
-                // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k;
-                // lane z takes one of the six components
-                const bool onk = z >= 3;
-                const int cpt = onk ? z - 3 : z;
-                const float4 ua = onk ? uk : uj, ub = onk ? uj : uk;
-                const float ia = onk ? s.invr[kk] : s.invr[j];
-                const float Sr = onk ? Srk : Srj;
-                const float va = cpt == 0 ? ua.x : (cpt == 1 ? ua.y : ua.z);
-                const float vb = cpt == 0 ? ub.x : (cpt == 1 ? ub.y : ub.z);
-                const float gcomp = 0.95f * Sc * ia * (vb - cos0 * va) + Sr * va;
-                atomicAdd(&fslot[3 * (onk ? kk : j) + cpt], gcomp);
-                if (cpt == 0) fix -= gcomp;
-                else if (cpt == 1) fiy -= gcomp;
-                else fiz -= gcomp;
-            }
-            advance_pair(j, kk, 4, mA);
+            advance_pair(j, kk, 32, mA);
         }
     }
     __syncwarp();

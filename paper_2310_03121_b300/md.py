@@ -1,5 +1,11 @@
 """Velocity-Verlet test harness around the energy+force evaluation.
 
+With random-init weights the potential has no repulsive core: after some
+hundreds of femtoseconds atoms fall into attractive regions and pairs
+collapse. The harness therefore guards the trajectory (closest pair below
+0.5 A, or a neighbor-capacity error from the library) and reports the steps
+completed, the energy drift over the stable window and the throughput.
+
 Not part of the evaluation itself: a driver that integrates Newton's
 equations with the library's forces, to check energy conservation (the
 672-atom ligand-in-water system) and to time a persistent system with a
@@ -70,10 +76,18 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
     aborted = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    from ._lib import MLPError
+
+    step = 0
     for step in range(1, steps + 1):
         v.add_(a, alpha=0.5 * dt_fs)
         x.add_(v, alpha=dt_fs)
-        system.energy_forces_device(x, E, F)
+        try:
+            system.energy_forces_device(x, E, F)
+        except MLPError as e:          # e.g. neighbor capacity exceeded after a collapse
+            aborted = f"step {step}: {e}"
+            step -= 1
+            break
         a = F.double() * (ACC / m)
         v.add_(a, alpha=0.5 * dt_fs)
         if step % report_every == 0:
@@ -86,7 +100,12 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
             break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    system.sync()
+    try:
+        system.sync()
+    except MLPError as e:
+        aborted = aborted or f"after step {step}: {e}"
+    if not t_series:
+        t_series, e_pot, e_kin = [0.0], [float("nan")], [float("nan")]
     n = len(species)
     tt = np.array(t_series)
     et = np.array(e_pot) + np.array(e_kin)
