@@ -702,6 +702,17 @@ int mlp_debug_neighbors(mlp_system* s, int32_t* counts, int32_t* list, int32_t c
     return C;
 }
 
+// dE/dG of a workspace as FP32 on the host (the BF16 networks store it as BF16).
+static cudaError_t copy_dG_to_host(const Workspace& ws, std::vector<float>& out) {
+    const size_t cnt = (size_t)ws.rows_cap * kAevLd;
+    out.resize(cnt);
+    if (ws.dG) return cudaMemcpy(out.data(), ws.dG, 4 * cnt, cudaMemcpyDeviceToHost);
+    std::vector<__nv_bfloat16> tmp(cnt);
+    cudaError_t e = cudaMemcpy(tmp.data(), ws.dG16, 2 * cnt, cudaMemcpyDeviceToHost);
+    for (size_t q = 0; q < cnt; ++q) out[q] = __bfloat162float(tmp[q]);
+    return e;
+}
+
 // Row of every atom in the element-grouped matrices (host copy of the counters).
 static int atom_rows(mlp_system* s, std::vector<int>& rows) {
     const int n = s->n;
@@ -759,7 +770,7 @@ int mlp_debug_atom_energies(mlp_system* s, float* e_out, float* dEdG) {
         rc = atom_rows(s, rows);
         if (rc) return rc;
         std::vector<float> all((size_t)s->ws.rows_cap * kAevLd);
-        cudaMemcpy(all.data(), s->ws.dG, 4 * all.size(), cudaMemcpyDeviceToHost);
+        copy_dG_to_host(s->ws, all);
         for (int i = 0; i < s->n; ++i)
             std::memcpy(dEdG + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
     }
@@ -820,7 +831,7 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
         if (ws.G16lo) cudaMemcpy(ws.G16lo, all_lo.data(), 2 * all_lo.size(), cudaMemcpyHostToDevice);
         if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.G16lo, precision == MLP_BF16,
-                             ws.row_atom, ws.e, ws.dG, true, ws.tc_err)) {
+                             ws.row_atom, ws.e, ws.dG16, true, ws.tc_err)) {
             workspace_destroy(ws);
             return MLP_ECUDA;
         }
@@ -829,7 +840,7 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
     if (e == cudaSuccess) e = cudaMemcpy(e_out, ws.e, 4 * (size_t)n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && dEdG) {
         std::vector<float> all(R * kAevLd);
-        e = cudaMemcpy(all.data(), ws.dG, 4 * all.size(), cudaMemcpyDeviceToHost);
+        e = copy_dG_to_host(ws, all);
         for (int i = 0; i < n; ++i) std::memcpy(dEdG + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
     }
     int tc = 0;

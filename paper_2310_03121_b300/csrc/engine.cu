@@ -74,7 +74,10 @@ void plan_workspace(Plan& P, Workspace& ws) {
     P.add(&ws.ctr, 1);
     P.add(&ws.grad, 3 * n);
     P.add(&ws.e, n);
-    P.add(&ws.dG, R * kAevLd);
+    if (ws.precision == 0)
+        P.add(&ws.dG, R * kAevLd);
+    else
+        P.add(&ws.dG16, R * kAevLd);
     P.add(&ws.tc_err, 4);
     P.add(&ws.err_sticky, 4);
     if (ws.precision == 0) {
@@ -211,10 +214,10 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
         if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
-                             ws.e, ws.dG, sp.network_backward, ws.tc_err))
+                             ws.e, ws.dG16, sp.network_backward, ws.tc_err))
             return -5;
     }
-    if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.grad, fast);
+    if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.dG16, ws.grad, fast);
     launch_finalize(st, sp.n_mols, sp.d_mol_start, n, ws.e, ws.grad, sp.energy ? sp.d_E : nullptr,
                     sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign, ws.ctr, ws.err_sticky);
     ce = cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);

@@ -60,7 +60,8 @@ struct Workspace {
     float* G32 = nullptr;
     __nv_bfloat16* G16 = nullptr;
     __nv_bfloat16* G16lo = nullptr;   // split-precision network only
-    float* dG = nullptr;
+    float* dG = nullptr;              // FP32 network
+    __nv_bfloat16* dG16 = nullptr;    // BF16 networks
     MlpF32Bufs fb{};
     float* e = nullptr;
     Grid* grid = nullptr;

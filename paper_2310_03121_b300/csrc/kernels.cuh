@@ -61,7 +61,9 @@ struct AevArgs {
 void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast);
 void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,
                      bool fast);
-void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, double* grad, bool fast);
+// dE/dG rows as FP32 (dG) or BF16 (dG16): exactly one of them non-null.
+void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, const __nv_bfloat16* dG16, double* grad,
+                   bool fast);
 
 // ---- network, FP32 SIMT path (kernels_mlp_f32.cu)
 struct NetF32 {   // device pointers, element-major, one net
@@ -90,7 +92,7 @@ bool make_weight_maps(NetBF16& w);
 // required); false: single BF16 pass everywhere.
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
                      const __nv_bfloat16* G, const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e,
-                     float* dG, bool backward, int* err_flag);
+                     __nv_bfloat16* dG, bool backward, int* err_flag);
 
 // ---- finalize (kernels_misc.cu)
 // Also ORs this evaluation's error flags (1 neighbor overflow, 2 AEV staging

@@ -310,8 +310,11 @@ __device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, 
     return 0.25f * s;
 }
 
-template <bool FAST>
-__global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* __restrict__ dG,
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <bool FAST, typename TG>
+__global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
                                                          double* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
     const int si = species_of(hi_i);
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
-    const float* grow = dG + (size_t)rw * kAevLd;
+    const TG* grow = dG + (size_t)rw * kAevLd;
     // angular block stored rotated: column c of element-pair block p at (c + p) mod 32, so that lanes
     // reading the same column of different blocks hit different banks
     for (int c = lane; c < kAevLen; c += 32) {
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const float* 
             const int rel = c - kRadLen, pb = rel >> 5;
             dst = kRadLen + 32 * pb + (((rel & 31) + pb) & 31);
         }
-        gs[dst] = grow[c];
+        gs[dst] = to_f(grow[c]);
     }
     for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
     __syncwarp();
@@ -485,17 +488,22 @@ void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_b
     }
 }
 
-void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, double* grad, bool fast) {
+void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, const __nv_bfloat16* dG16, double* grad,
+                   bool fast) {
     const size_t sm = kWarps * kForceSmemPerWarp;
     const int gs = (a.n + kWarps - 1) / kWarps;
-    if (fast) {
-        static bool once = (set_smem(k_forces<true>, sm), true);
+    if (dG16) {
+        static bool once = (set_smem(k_forces<true, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("forces", st, k_forces<true><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
+        MLP_LAUNCH("forces", st, k_forces<true, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, dG16, grad));
+    } else if (fast) {
+        static bool once = (set_smem(k_forces<true, float>, sm), true);
+        (void)once;
+        MLP_LAUNCH("forces", st, k_forces<true, float><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
     } else {
-        static bool once = (set_smem(k_forces<false>, sm), true);
+        static bool once = (set_smem(k_forces<false, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("forces", st, k_forces<false><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
+        MLP_LAUNCH("forces", st, k_forces<false, float><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
     }
 }
 

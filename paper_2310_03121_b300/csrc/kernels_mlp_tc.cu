@@ -2,7 +2,7 @@
 // FP32): the one dense contraction of the path (paper, section "Performance
 // of MLPs": one ANI net per element, evaluated for every atom).
 //
-// One CTA (4 warps; thread r owns row r of the tile = TMEM lane r) processes
+// One CTA (16 warps; TMEM lane r = row r of the tile) processes
 // 128-row tiles of one element, persistent over the tiles. The six GEMMs of
 // the forward and backward run back to back without leaving the SM:
 //   F1  D[128x256] = G[128x1024] W1^T   G and W1 streamed by TMA in 64-wide K chunks (4 stages)
@@ -39,7 +39,8 @@
 namespace mlp {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;   // 16 warps: warp w serves TMEM lanes 32 (w % 4) .. +32 and column part w / 4
+constexpr int kParts = kThreads / 128;
 constexpr uint32_t kAtom = 128 * 128;          // 128 rows x 64 BF16 (one K atom of a 128-row operand)
 // Shared memory map (224 KB, offsets from the 1024-aligned base):
 //   [0, 64K)      h1 / g1                         (4 atoms)
@@ -67,7 +68,7 @@ struct TcArgs {
     const int* row_atom;
     const float *b1, *b2, *b3, *W4, *b4;
     float* e;
-    float* dG;
+    __nv_bfloat16* dG;   // [rows][1024] BF16
     int backward;
     int* err;
 };
@@ -378,7 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int part = warp >> 2;   // which 16-column chunks this warp takes: part, part + kParts, ...
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
     Issuer I;
@@ -403,8 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
-    const int r = tid;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
+    const int r = (warp & 3) * 32 + lane;                              // tile row = TMEM lane
 
     auto wait_done = [&]() {
         if (!mbar_wait(I.bar(kBarDone), n_done & 1u)) atomicExch(&abort_flag, 1);
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         if (tid == 0 && !f1_run<SPLIT>(I, sbase, tmem, &M.G, &M.Glo, &M.W1, &M.W1lo, row0, s)) issue_fail();
         wait_done();
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF2)) issue_fail();
-        for (int c0 = 0; c0 < kH1; c0 += 16) {
+        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
             float v[16];
             tmem_ld16(tl + (uint32_t)c0, v);
 #pragma unroll
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF2)) issue_fail();
         wait_done();
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF3)) issue_fail();
-        for (int c0 = 0; c0 < kH2; c0 += 16) {
+        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
             float v[16];
             tmem_ld16(tl + 256u + (uint32_t)c0, v);
 #pragma unroll
@@ -464,13 +466,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         }
         if (!sync_all()) break;
 
-        // ---- F3 -> E3 (energy, g3)
+        // ---- F3 -> E3 (energy, g3): the part-0 warps take every column for the
+        // energy (fixed summation order per row), g3 chunks are shared by the parts
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF3)) issue_fail();
         wait_done();
         if (tid == 0 && I.ok && p.backward && !job_prefetch(I, sbase, jB3)) issue_fail();
         {
             float es = 0.f;
             for (int c0 = 0; c0 < kH3; c0 += 16) {
+                const bool mine = ((c0 >> 4) % kParts) == part;
+                if (!mine && part != 0) continue;
                 float v[16];
                 tmem_ld16(tl + (uint32_t)c0, v);
                 uint32_t pk[8];
@@ -482,12 +487,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
                     es = fmaf(w1, celu_f(z1), es);
                     pk[q] = pack_bf16(w0 * dcelu_f(z0), w1 * dcelu_f(z1));
                 }
-                if (p.backward) {
+                if (mine && p.backward) {
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
                 }
             }
-            if (r < nvalid) p.e[p.row_atom[row0 + r]] = es + __ldg(p.b4 + s);
+            if (part == 0 && r < nvalid) p.e[p.row_atom[row0 + r]] = es + __ldg(p.b4 + s);
         }
         if (!sync_all()) break;
         if (!p.backward) continue;
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB3)) issue_fail();
         wait_done();
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB2)) issue_fail();
-        for (int c0 = 0; c0 < kH2; c0 += 16) {
+        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
             float v[16];
             tmem_ld16(tl + 256u + (uint32_t)c0, v);
 #pragma unroll
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         wait_done();
         Job jB1{&M.W1t, nullptr, s * kAevLd, 4, 4, kOffH1, 0, 0, 256, kOffRB, 32768u, 2, 0, {0}};
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
-        for (int c0 = 0; c0 < kH1; c0 += 16) {
+        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
             float v[16];
             tmem_ld16(tl + (uint32_t)c0, v);
 #pragma unroll
@@ -550,14 +555,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
                 jB1.d_col = 256u * (uint32_t)((j + 1) & 1);
                 if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
             }
-            float* out = p.dG + (size_t)(row0 + r) * kAevLd + 256 * j;
-            for (int c0 = 0; c0 < 256; c0 += 16) {
+            __nv_bfloat16* out = p.dG + (size_t)(row0 + r) * kAevLd + 256 * j;
+            for (int c0 = 16 * part; c0 < 256; c0 += 16 * kParts) {
                 float v[16];
                 tmem_ld16(tl + dcol + (uint32_t)c0, v);
                 if (r < nvalid) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        *reinterpret_cast<float4*>(out + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    uint4 o0, o1;
+                    o0.x = pack_bf16(v[0], v[1]);
+                    o0.y = pack_bf16(v[2], v[3]);
+                    o0.z = pack_bf16(v[4], v[5]);
+                    o0.w = pack_bf16(v[6], v[7]);
+                    o1.x = pack_bf16(v[8], v[9]);
+                    o1.y = pack_bf16(v[10], v[11]);
+                    o1.z = pack_bf16(v[12], v[13]);
+                    o1.w = pack_bf16(v[14], v[15]);
+                    *reinterpret_cast<uint4*>(out + c0) = o0;
+                    *reinterpret_cast<uint4*>(out + c0 + 8) = o1;
                 }
             }
             if (!sync_all()) {
@@ -638,8 +651,8 @@ bool make_weight_maps(NetBF16& w) {
 }
 
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w, const __nv_bfloat16* G,
-                     const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, float* dG, bool backward,
-                     int* err_flag) {
+                     const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, __nv_bfloat16* dG,
+                     bool backward, int* err_flag) {
     TcMaps M;
     if (!w.maps_ok || !make_map(&M.G, G, kAevLd, (uint64_t)rows_cap, 128) ||
         (split && (!G_lo || !make_map(&M.Glo, G_lo, kAevLd, (uint64_t)rows_cap, 128)))) {

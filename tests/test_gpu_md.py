@@ -1,10 +1,12 @@
 """Velocity-Verlet harness: energy conservation on the 672-atom open system
-(FP32 path, 0.5 fs, 100 steps: with random-init weights the potential has no
-repulsive core and pairs collapse after ~100 fs, so the check stays inside the
-stable window) and the persistent skin list on the 21,080-atom periodic
-box (BF16 path, list radius 5.6 A, rebuilt every 10 steps or by the
-displacement guard): after a short trajectory the persistent system's
-energy and forces equal a fresh evaluation at the same coordinates.
+(FP32 path, 0.1 fs, 100 steps: with random-init weights the potential has no
+repulsive core and the first pairs come closer than 0.5 A after ~25 fs, so
+the check stays inside that window) and the persistent skin list on the
+21,080-atom periodic box (BF16 path, list radius 5.6 A, rebuilt every 10
+steps or by the displacement guard): after a short trajectory the persistent
+system's energy and forces equal a fresh evaluation at the same coordinates
+up to FP32 summation order (the skin list holds the neighbors in another
+order).
 """
 import numpy as np
 import pytest
@@ -30,11 +32,11 @@ def test_energy_conservation_fp32(P):
     c = gen.make_config(1)
     W = P.Weights(gen.make_weights())
     s = P.System(W, c.species, c.coords, None, precision="fp32")
-    res = md.run(s, c.species, c.coords, None, dt_fs=0.5, steps=100, report_every=5, guard_every=50)
+    res = md.run(s, c.species, c.coords, None, dt_fs=0.1, steps=100, report_every=5, guard_every=0)
     assert res["aborted"] is None
     # total energy drift well below the kinetic energy scale (kT ~ 0.026 eV per atom)
     assert abs(res["drift_eV_per_atom_per_ps"]) < 1e-3, res
-    assert res["etot_rms_fluct_eV_per_atom"] < 1e-3, res
+    assert res["etot_rms_fluct_eV_per_atom"] < 1e-4, res
 
 
 def test_skin_list_trajectory_matches_fresh(P):
@@ -53,7 +55,7 @@ def test_skin_list_trajectory_matches_fresh(P):
     s.sync()
     fresh = P.System(W, c.species, x.cpu().numpy(), c.cell, precision="bf16")
     E2, F2 = fresh.energy_forces()
-    assert abs(E.item() - E2) <= 1e-9 * abs(E2)
-    assert np.abs(F.cpu().numpy() - F2).max() <= 1e-5
+    assert abs(E.item() - E2) <= 1e-7 * abs(E2)
+    assert np.abs(F.cpu().numpy() - F2).max() <= 1e-4
     res = md.run(s, c.species, x.cpu().numpy(), c.cell, dt_fs=0.5, steps=50, report_every=10, guard_every=50)
     assert res["steps"] > 0 and res["atom_steps_per_s"] > 0
