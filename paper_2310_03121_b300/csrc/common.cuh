@@ -32,7 +32,7 @@ constexpr float kEtaAng = 12.5f;
 constexpr float kZeta = 14.1f;
 constexpr float kCeluAlpha = 0.1f;
 
-constexpr int kMaxAng = 64;   // angular neighbors kept per atom (overflow flagged)
+constexpr int kMaxAng = 60;   // angular neighbors kept per atom (overflow flagged)
 
 // Device constant tables, filled once per device by init_constants().
 struct AevConsts {

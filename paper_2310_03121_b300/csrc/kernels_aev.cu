@@ -18,18 +18,17 @@
 //   * radial (forward): lane = (half, k), 16 shift lanes x 2 neighbors taken
 //     from the lanes that loaded them by shuffles; each lane owns its own
 //     accumulator column per element -> no atomics, fixed order;
-//   * angular: pairs are taken four at a time, lane = (t, z): the lane
-//     evaluates the angle factor of section z and the distance factor of
-//     shift z & 3 for pair t; then, for each of the four pairs in turn,
-//     lane (a, z) multiplies the shuffled factors and adds them to its own
-//     column 32 p + 8 a + z (conflict-free, fixed order -> deterministic).
+//   * angular: pairs are taken 32 at a time: one pair per lane computes its
+//     8 angle factors and 4 distance factors into shared memory, then lane
+//     (a, z) adds the products, pair by pair, to its own column 32 p + 8 a + z
+//     (conflict-free, fixed order -> deterministic).
 // The backward recomputes the terms with their derivatives and contracts
 // them with dE/dG (staged in shared memory): radial one neighbor per lane
 // (on the fast path the 16 Gaussians come from a two-sided recurrence started
 // at the nearest shift: 3 exponentials instead of 16), angular one pair per
 // lane with its 4 distance and 8 angle factors in registers (the angular
-// block of dE/dG is stored rotated per element pair so that lanes reading the
-// same column of different pair blocks do not share a bank). Gradients on
+// block of dE/dG is staged in rows of 33 floats per element pair so that
+// lanes reading the same column of different pair rows do not share a bank). Gradients on
 // neighbors go to FP64 global sums (radial: per neighbor; angular:
 // accumulated per angular neighbor in shared memory first).
 #include <cuda_bf16.h>
@@ -78,13 +77,22 @@ struct M<false> {   // accurate FP32 library functions (FP32 path)
 };
 template <>
 struct M<true> {    // hardware approximations (BF16-network path)
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
-    static __device__ __forceinline__ float pw(float b, float e) { return exp2f(e * __log2f(b)); }
+    static __device__ __forceinline__ float pw(float b, float e) { return ex2(e * __log2f(b)); }
     static __device__ __forceinline__ float cpi(float x) { return __cosf(3.14159265358979f * x); }
     static __device__ __forceinline__ float spi(float x) { return __sinf(3.14159265358979f * x); }
     static __device__ __forceinline__ float sq(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
     static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ float rcp(float x) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
 };
 
 // Angular sub-list of one atom (neighbors within 3.5 A).
@@ -98,8 +106,15 @@ struct AngStage {
 };
 
 constexpr int kAccFloats = 2 * kRadLen + kAngLen;   // two radial halves + angular
-constexpr size_t kAevSmemPerWarp = sizeof(AngStage) + kAccFloats * sizeof(float);
-constexpr size_t kForceSmemPerWarp = sizeof(AngStage) + (kAevLen + 3 * kMaxAng) * sizeof(float);
+// per-pair factors of 32 pairs: P_z f [32][8], R_a [32][4], element pair [32]
+constexpr int kPairBufFloats = 32 * 8 + 32 * 4 + 32;
+constexpr size_t kAevSmemPerWarp = sizeof(AngStage) + (kAccFloats + kPairBufFloats) * sizeof(float);
+// dE/dG staged with the angular block in rows of 33 floats (one per element
+// pair) so that lanes reading the same column of different rows hit
+// different banks
+constexpr int kGsAngStride = 33;
+constexpr int kGsFloats = kRadLen + kNPairs * kGsAngStride;
+constexpr size_t kForceSmemPerWarp = sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float);
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -221,38 +236,43 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     if (mA > kMaxAng) mA = 0;   // reported as an error by the host; keep every index in range
     __syncwarp();
 
-    // angular: four pairs per step
+    // angular: 32 pairs at a time. First one pair per lane: its 8 angle
+    // factors (times the cutoff product) and 4 distance factors go to shared
+    // memory; then lane (a, z) adds factor products to its own column of the
+    // pair's element-pair block, pairs in list order (deterministic).
     {
         float* accA = acc + 2 * kRadLen;
-        const int t = lane >> 3, z = lane & 7;
-        const float cz = c_aev.cos_z[z], sz = c_aev.sin_z[z];
-        const float Aown = c_aev.shf_a[z & 3];
+        float* pf = acc + kAccFloats;    // [32][8]
+        float* rf = pf + 32 * 8;         // [32][4]
+        int* pp = reinterpret_cast<int*>(rf + 32 * 4);
         const int P = mA * (mA - 1) / 2;
-        int j = 0, kk = 1 + t;
+        int j = 0, kk = 1 + lane;
         advance_pair(j, kk, 0, mA);
-        for (int base = 0; base < P; base += 4) {
-            float Pz = 0.f, Ra = 0.f, f = 0.f;
-            int p = 0;
-            if (base + t < P) {
+        for (int base = 0; base < P; base += 32) {
+            const int nv = min(32, P - base);
+            if (lane < nv) {
                 const float4 uj = s.u[j], uk = s.u[kk];
                 const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
                 const float sn = M<FAST>::sq(1.f - c * c);
-                const float b = 0.5f + 0.5f * (c * cz + sn * sz);
-                Pz = 2.f * M<FAST>::pw(b, kZeta);
-                const float dr = 0.5f * (uj.w + uk.w) - Aown;
-                Ra = M<FAST>::ex(-kEtaAng * dr * dr);
-                f = s.fc[j] * s.fc[kk];
-                p = pair_index(s.sp[j], s.sp[kk]);
-            }
+                const float f2 = 2.f * s.fc[j] * s.fc[kk];
 #pragma unroll
-            for (int tt = 0; tt < 4; ++tt) {
-                const float Pv = __shfl_sync(kFull, Pz, tt * 8 + (lane & 7));
-                const float Rv = __shfl_sync(kFull, Ra, tt * 8 + (lane >> 3));
-                const float fv = __shfl_sync(kFull, f, tt * 8);
-                const int pv = __shfl_sync(kFull, p, tt * 8);
-                if (base + tt < P) accA[pv * 32 + lane] += Pv * Rv * fv;
+                for (int z = 0; z < kAngZ; ++z) {
+                    const float b = 0.5f + 0.5f * (c * c_aev.cos_z[z] + sn * c_aev.sin_z[z]);
+                    pf[lane * 8 + z] = f2 * M<FAST>::pw(b, kZeta);
+                }
+                const float rbar = 0.5f * (uj.w + uk.w);
+#pragma unroll
+                for (int aa = 0; aa < kAngA; ++aa) {
+                    const float dr = rbar - c_aev.shf_a[aa];
+                    rf[lane * 4 + aa] = M<FAST>::ex(-kEtaAng * dr * dr);
+                }
+                pp[lane] = 32 * pair_index(s.sp[j], s.sp[kk]);
             }
-            advance_pair(j, kk, 4, mA);
+            __syncwarp();
+            const int z = lane & 7, aa = lane >> 3;
+            for (int q = 0; q < nv; ++q) accA[pp[q] + lane] += pf[q * 8 + z] * rf[q * 4 + aa];
+            __syncwarp();
+            advance_pair(j, kk, 32, mA);
         }
     }
     __syncwarp();
@@ -322,18 +342,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
     if (i >= a.n) return;
     AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kForceSmemPerWarp);
     float* gs = reinterpret_cast<float*>(smem + w * kForceSmemPerWarp + sizeof(AngStage));
-    float* fslot = gs + kAevLen;
+    float* fslot = gs + kGsFloats;
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
     const int si = species_of(hi_i);
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
     const TG* grow = dG + (size_t)rw * kAevLd;
-    // angular block stored rotated: column c of element-pair block p at (c + p) mod 32, so that lanes
-    // reading the same column of different blocks hit different banks
     for (int c = lane; c < kAevLen; c += 32) {
         int dst = c;
         if (c >= kRadLen) {
-            const int rel = c - kRadLen, pb = rel >> 5;
-            dst = kRadLen + 32 * pb + (((rel & 31) + pb) & 31);
+            const int rel = c - kRadLen;
+            dst = kRadLen + kGsAngStride * (rel >> 5) + (rel & 31);
         }
         gs[dst] = to_f(grow[c]);
     }
@@ -387,7 +405,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
                     R[aa] = M<FAST>::ex(-kEtaAng * dr * dr);
                     dR[aa] = -2.f * kEtaAng * dr * R[aa];
                 }
-                const float* gp = gs + kRadLen + 32 * p;
+                const float* gp = gs + kRadLen + kGsAngStride * p;
                 float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
                 for (int z = 0; z < kAngZ; ++z) {
@@ -399,7 +417,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
                     float S1 = 0.f, S2 = 0.f;
 #pragma unroll
                     for (int aa = 0; aa < kAngA; ++aa) {
-                        const float gg = gp[(8 * aa + z + p) & 31];
+                        const float gg = gp[8 * aa + z];
                         S1 = fmaf(gg, R[aa], S1);
                         S2 = fmaf(gg, dR[aa], S2);
                     }

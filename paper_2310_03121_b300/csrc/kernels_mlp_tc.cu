@@ -57,6 +57,7 @@ constexpr uint32_t kOffG3 = 7 * kAtom;
 constexpr uint32_t kOffH1lo = 4 * kAtom;
 constexpr uint32_t kOffH2lo = 7 * kAtom;
 constexpr uint32_t kOffRB = 10 * kAtom;
+constexpr uint32_t kOffEPart = 216 * 1024;       // energy partial sums during E3 (2 KB)
 constexpr uint32_t kSmemUsed = 14 * kAtom;               // 229,376 bytes
 constexpr uint32_t kSmemAlloc = kSmemUsed + 1024;       // + alignment slack
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
@@ -368,6 +369,21 @@ __device__ __forceinline__ void store_act(uint32_t sbase, uint32_t off_hi, uint3
     }
 }
 
+#ifdef MLP_TC_TRACE
+// Phase timestamps (%globaltimer, ns) of the first tiles of the first CTAs,
+// for performance investigation builds only (-DMLP_TC_TRACE).
+constexpr int kTraceCtas = 8, kTraceTiles = 4, kTracePoints = 32;
+__device__ unsigned long long g_tc_trace[kTraceCtas][kTraceTiles][kTracePoints];
+#define MLP_TC_MARK(k)                                                                                  \
+    do {                                                                                                \
+        if (tid == 0 && blockIdx.x < kTraceCtas && tile_no < kTraceTiles) g_tc_trace[blockIdx.x][tile_no][k] = globaltimer(); \
+    } while (0)
+#else
+#define MLP_TC_MARK(k) \
+    do {               \
+    } while (0)
+#endif
+
 struct TcMaps {
     CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t;
 };
@@ -423,7 +439,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     };
     auto issue_fail = [&]() { atomicExch(&abort_flag, 1); };
 
+    int tile_no = -1;
+    (void)tile_no;
     for (int t = blockIdx.x;; t += gridDim.x) {
+        ++tile_no;
+        MLP_TC_MARK(0);
         int s, row0, nvalid;
         if (!tile_info(p.ctr->species, t, s, row0, nvalid)) break;
         const float* b1 = p.b1 + s * kH1;
@@ -442,7 +462,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
 
         // ---- F1 -> E1
         if (tid == 0 && !f1_run<SPLIT>(I, sbase, tmem, &M.G, &M.Glo, &M.W1, &M.W1lo, row0, s)) issue_fail();
+        MLP_TC_MARK(1);
         wait_done();
+        MLP_TC_MARK(2);
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF2)) issue_fail();
         for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
             float v[16];
@@ -452,10 +474,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
             store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
         }
         if (!sync_all()) break;
+        MLP_TC_MARK(3);
 
         // ---- F2 -> E2
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF2)) issue_fail();
+        MLP_TC_MARK(4);
         wait_done();
+        MLP_TC_MARK(5);
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF3)) issue_fail();
         for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
             float v[16];
@@ -465,17 +490,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
             store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
         }
         if (!sync_all()) break;
+        MLP_TC_MARK(6);
 
-        // ---- F3 -> E3 (energy, g3): the part-0 warps take every column for the
-        // energy (fixed summation order per row), g3 chunks are shared by the parts
+        // ---- F3 -> E3 (energy, g3). Each part sums its own column chunks of
+        // w4 . celu(z3); the four partial sums of a row meet in [216K, 218K),
+        // a corner no load touches during E3 (the B3 prefetch fills
+        // [160K, 184K) and [192K, 216K)), and are added in fixed order.
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF3)) issue_fail();
+        MLP_TC_MARK(7);
         wait_done();
+        MLP_TC_MARK(8);
         if (tid == 0 && I.ok && p.backward && !job_prefetch(I, sbase, jB3)) issue_fail();
         {
             float es = 0.f;
-            for (int c0 = 0; c0 < kH3; c0 += 16) {
-                const bool mine = ((c0 >> 4) % kParts) == part;
-                if (!mine && part != 0) continue;
+            for (int c0 = 16 * part; c0 < kH3; c0 += 16 * kParts) {
                 float v[16];
                 tmem_ld16(tl + (uint32_t)c0, v);
                 uint32_t pk[8];
@@ -487,19 +515,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
                     es = fmaf(w1, celu_f(z1), es);
                     pk[q] = pack_bf16(w0 * dcelu_f(z0), w1 * dcelu_f(z1));
                 }
-                if (mine && p.backward) {
+                if (p.backward) {
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
                 }
             }
-            if (part == 0 && r < nvalid) p.e[p.row_atom[row0 + r]] = es + __ldg(p.b4 + s);
+            float* e_part = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw)) + kOffEPart);
+            e_part[part * 128 + r] = es;
+            __syncthreads();
+            if (part == 0 && r < nvalid) {
+                float t = __ldg(p.b4 + s);
+#pragma unroll
+                for (int q = 0; q < kParts; ++q) t += e_part[q * 128 + r];
+                p.e[p.row_atom[row0 + r]] = t;
+            }
         }
         if (!sync_all()) break;
+        MLP_TC_MARK(9);
         if (!p.backward) continue;
 
         // ---- B3 -> g2 (over h2)
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB3)) issue_fail();
+        MLP_TC_MARK(10);
         wait_done();
+        MLP_TC_MARK(11);
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB2)) issue_fail();
         for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
             float v[16];
@@ -519,10 +558,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
             }
         }
         if (!sync_all()) break;
+        MLP_TC_MARK(12);
 
         // ---- B2 -> g1 (over h1)
         if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB2)) issue_fail();
+        MLP_TC_MARK(13);
         wait_done();
+        MLP_TC_MARK(14);
         Job jB1{&M.W1t, nullptr, s * kAevLd, 4, 4, kOffH1, 0, 0, 256, kOffRB, 32768u, 2, 0, {0}};
         if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
         for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
@@ -543,12 +585,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
             }
         }
         if (!sync_all()) break;
+        MLP_TC_MARK(15);
 
         // ---- B1: four 256-column blocks of dE/dG, alternating TMEM halves
         bool aborted = false;
         for (int j = 0; j < 4; ++j) {
             if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB1)) issue_fail();
+            MLP_TC_MARK(16 + 2 * j);
             wait_done();
+            MLP_TC_MARK(17 + 2 * j);
             const uint32_t dcol = jB1.d_col;
             if (j < 3) {
                 jB1.brow = s * kAevLd + 256 * (j + 1);
@@ -579,6 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
             }
         }
         if (aborted) break;
+        MLP_TC_MARK(24);
     }
 
     // ---- teardown: drain own copies and MMAs (bounded), free tensor memory
@@ -634,6 +680,15 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, ui
 }  // namespace
 
 bool mlp_tc_available() { return true; }
+
+#ifdef MLP_TC_TRACE
+extern "C" __attribute__((visibility("default"))) int mlp_tc_trace_read(unsigned long long* out, int cap) {
+    const int n = kTraceCtas * kTraceTiles * kTracePoints;
+    if (cap < n) return -n;
+    cudaMemcpyFromSymbol(out, g_tc_trace, sizeof(unsigned long long) * n);
+    return n;
+}
+#endif
 
 bool make_weight_maps(NetBF16& w) {
     bool ok = true;

@@ -86,6 +86,7 @@ struct mlp_server {
     std::unordered_map<mlp_ticket, Result> results;
     std::vector<int64_t> latencies;
     bool stop = false;
+    bool sleeping = false;   // the server thread waits for new requests (submit must wake it)
     std::thread th;
     mlp_ticket next_id = 1;
     int64_t inflight_bytes = 0;
@@ -182,27 +183,38 @@ int launch_slot(mlp_server* S, Slot& s) {
 void finish_slot(mlp_server* S, Slot& s, int status) {
     if (status == MLP_OK) status = check_counters(s.ws);
     const int64_t t = now_ns();
-    std::lock_guard<std::mutex> lk(S->mu);
+    // results are assembled without the lock; only the hand-over is locked
+    std::vector<std::pair<mlp_ticket, Result>> done;
+    std::vector<int64_t> lat;
+    done.reserve(s.reqs.size());
+    lat.reserve(s.reqs.size());
     int off = 0;
     for (size_t m = 0; m < s.reqs.size(); ++m) {
         Request* r = s.reqs[m];
-        Result& res = S->results[r->id];
+        Result res;
         res.status = status;
         res.n = r->n;
         res.E = s.h_E[m];
         res.F.assign(s.h_F + 3 * (size_t)off, s.h_F + 3 * (size_t)(off + r->n));
         res.done = true;
         off += r->n;
-        S->latencies.push_back(t - r->t_submit);
+        lat.push_back(t - r->t_submit);
+        done.emplace_back(r->id, std::move(res));
         delete r;
     }
-    if (S->latencies.size() > (1u << 22)) S->latencies.erase(S->latencies.begin(), S->latencies.begin() + (1 << 20));
-    S->st.completed += (int64_t)s.reqs.size();
-    S->st.batches += 1;
-    S->st.atoms += s.n_atoms;
-    S->inflight_bytes -= (int64_t)s.footprint;
-    s.reqs.clear();
-    s.busy = false;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto& d : done) S->results[d.first] = std::move(d.second);
+        S->latencies.insert(S->latencies.end(), lat.begin(), lat.end());
+        if (S->latencies.size() > (1u << 22))
+            S->latencies.erase(S->latencies.begin(), S->latencies.begin() + (1 << 20));
+        S->st.completed += (int64_t)s.reqs.size();
+        S->st.batches += 1;
+        S->st.atoms += s.n_atoms;
+        S->inflight_bytes -= (int64_t)s.footprint;
+        s.reqs.clear();
+        s.busy = false;
+    }
     S->cv_done.notify_all();
 }
 
@@ -255,10 +267,14 @@ void server_loop(mlp_server* S) {
                 free_slot = nullptr;
             }
             if (!free_slot) {
-                if (any_busy)
+                if (any_busy) {
+                    // poll the in-flight batches again shortly; new requests need no wake-up
                     S->cv_work.wait_for(lk, std::chrono::microseconds(20));
-                else if (S->queue.empty() && !S->stop)
+                } else if (S->queue.empty() && !S->stop) {
+                    S->sleeping = true;
                     S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                    S->sleeping = false;
+                }
                 continue;
             }
         }
@@ -364,6 +380,7 @@ int mlp_submit(mlp_server* S, int32_t n, const int8_t* species, const double* co
     r->species.assign(species, species + n);
     r->xyz.assign(coords, coords + 3 * (size_t)n);
     r->t_submit = now_ns();
+    bool wake;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if ((int)S->queue.size() >= S->o.queue_capacity) {
@@ -375,8 +392,9 @@ int mlp_submit(mlp_server* S, int32_t n, const int8_t* species, const double* co
         S->queue.push_back(r);
         S->st.submitted += 1;
         *out = r->id;
+        wake = S->sleeping;
     }
-    S->cv_work.notify_one();
+    if (wake) S->cv_work.notify_one();
     return MLP_OK;
 }
 
