@@ -102,6 +102,7 @@ int sys_finish_pending(mlp_system* s) {
     if (sticky) {
         cudaMemset(s->ws.err_sticky, 0, sizeof(int));
         if (sticky & 4) return set_error(MLP_EINVAL, "element code outside [0, 7) in an earlier evaluation");
+        if (sticky & 8) return set_error(MLP_ECUDA, "tensor-core network kernel error in an earlier evaluation");
         return set_error(MLP_EOVERFLOW, "neighbor capacity exceeded in an earlier evaluation");
     }
     return MLP_OK;

@@ -67,7 +67,8 @@ struct Counters {
     int ang_overflow;      // largest radial/angular count above the staging limits (0 = fine)
     int bad_species;       // 1 if an element code outside [0, 7) was seen
     int rebuild;           // 1 if this evaluation rebuilds the neighbor list
-    int pad[4];
+    int net_error;         // tensor-core network kernel gave up on a bounded wait (0 = fine; else a code)
+    int pad[3];
     // bounding box of an open system as order-preserving unsigned keys of
     // max(x) and max(-x), so that an all-zero reset is the identity
     unsigned bbox_max_key[3];

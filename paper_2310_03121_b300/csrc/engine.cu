@@ -214,7 +214,7 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
         if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
-                             ws.e, ws.dG16, sp.network_backward, ws.tc_err))
+                             ws.e, ws.dG16, sp.network_backward, &ws.ctr->net_error))
             return -5;
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.dG16, ws.grad, fast);
@@ -235,8 +235,10 @@ int check_counters(const Workspace& ws) {
         return set_error(-7, "neighbor list overflow: an atom has %d neighbors (capacity %d)", c.nbr_overflow,
                          ws.nbr_cap);
     if (c.ang_overflow)
-        return set_error(-7, "too many neighbors inside the AEV cutoffs (%d; limits 160 radial / 64 angular)",
-                         c.ang_overflow);
+        return set_error(-7, "too many neighbors inside the AEV cutoffs (%d; limits 160 radial / %d angular)",
+                         c.ang_overflow, kMaxAng);
+    if (c.net_error)
+        return set_error(-5, "tensor-core network kernel gave up on a bounded wait (code %#x)", c.net_error);
     return 0;
 }
 

@@ -96,7 +96,8 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
 
 // ---- finalize (kernels_misc.cu)
 // Also ORs this evaluation's error flags (1 neighbor overflow, 2 AEV staging
-// overflow, 4 bad element code) into *sticky when sticky != nullptr.
+// overflow, 4 bad element code, 8 network kernel error) into *sticky when
+// sticky != nullptr.
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,
                      const Counters* ctr, int* sticky);

@@ -18,7 +18,8 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
                            int* __restrict__ sticky) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && sticky) {
         // error flags of this evaluation, kept until the host reads and clears them
-        const int f = (ctr->nbr_overflow ? 1 : 0) | (ctr->ang_overflow ? 2 : 0) | (ctr->bad_species ? 4 : 0);
+        const int f = (ctr->nbr_overflow ? 1 : 0) | (ctr->ang_overflow ? 2 : 0) | (ctr->bad_species ? 4 : 0) |
+                      (ctr->net_error ? 8 : 0);
         if (f) atomicOr(sticky, f);
     }
     if ((int)blockIdx.x < n_mols) {

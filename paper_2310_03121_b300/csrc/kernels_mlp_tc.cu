@@ -2,31 +2,44 @@
 // FP32): the one dense contraction of the path (paper, section "Performance
 // of MLPs": one ANI net per element, evaluated for every atom).
 //
-// One CTA (16 warps; TMEM lane r = row r of the tile) processes
-// 128-row tiles of one element, persistent over the tiles. The six GEMMs of
-// the forward and backward run back to back without leaving the SM:
-//   F1  D[128x256] = G[128x1024] W1^T   G and W1 streamed by TMA in 64-wide K chunks (4 stages)
+// One persistent CTA per SM processes 128-row tiles of one element (TMEM lane
+// r = row r of the tile). The six GEMMs of the forward and backward run back
+// to back without leaving the SM:
+//   F1  D[128x256] = G[128x1024] W1^T   G and W1 streamed by TMA in 64-wide K chunks
 //   E1  h1 = celu(D + b1)               -> shared memory, BF16, A-operand layout
-//   F2  D[128x192] = h1 W2^T            W2 streamed (2 stages)
+//   F2  D[128x192] = h1 W2^T            W2 streamed
 //   E2  h2 = celu(D + b2)               -> shared memory
 //   F3  D[128x160] = h2 W3^T            W3 streamed
 //   E3  e = w4 . celu(D + b3) + b4      -> global; g3 = w4 * celu'(z3) -> shared memory
 //   B3  D[128x192] = g3 W3              W3^T streamed;  g2 = D * celu'(z2) (over h2)
 //   B2  D[128x256] = g2 W2              W2^T streamed;  g1 = D * celu'(z1) (over h1)
-//   B1  dE/dG[128x1024] = g1 W1         W1^T streamed in four 256-column blocks -> global FP32
+//   B1  dE/dG[128x1024] = g1 W1         W1^T streamed, four 256-column blocks -> global BF16 by TMA store
 // celu'(z) comes from the stored BF16 activation: 1 if h > 0 else h / alpha + 1.
 // Split mode (the default BF16 precision): every forward GEMM is computed from
 // BF16 hi/lo pairs of both operands, X = X_hi + X_lo with X_lo the BF16
 // rounding of the remainder, as A_hi B_hi + A_lo B_hi + A_hi B_lo (three MMAs
 // per K step, FP32 accumulation), so the energy carries ~16 bits of operand
 // precision; the backward (forces) uses the single BF16 terms.
-// Accumulators live in tensor memory (512 columns: two 256-column halves).
-// Thread 0 issues the TMA loads (cp.async.bulk.tensor) and the tcgen05.mma
-// instructions; all 128 threads run the epilogues (tcgen05.ld -> registers ->
-// shared or global memory). Operands in shared memory use the 128-byte
-// swizzled K-major layout that TMA writes. Every wait is bounded in time: on
-// expiry the CTA records an error, drains its own copies and MMAs, frees its
-// tensor memory and returns.
+//
+// Warp roles (14 warps, at most 4 per SM sub-partition so that the epilogue
+// warps get up to 128 registers):
+//   warp 0       TMA producer (one lane): streams G and weight sub-chunks into
+//                shared-memory rings as soon as slots free up, running ahead
+//                across GEMMs, and prefetches the next tile's G into L2;
+//   warp 1       MMA issuer (one lane): tcgen05.mma into tensor memory (512
+//                columns: two 256-column accumulator halves), tcgen05.commit
+//                to the ring-slot and accumulator barriers;
+//   warps 2..13  epilogues (tcgen05.ld -> registers -> shared operand or
+//                global); warp w reads TMEM lanes 32 (w % 4) .. +32 and takes
+//                column part (w - 2) / 4 of 3: the 16-column chunks
+//                part, part + 3, part + 6, ...
+// Every hand-off is an mbarrier: ring slot full / empty (producer <-> MMA),
+// accumulator half full (MMA -> epilogue), operand ready and B1 half read
+// (epilogue -> MMA), tile done with shared memory (epilogue -> producer). Every
+// wait is bounded in time and also gives up when another role has aborted; on
+// abort the CTA records an error, drains its own copies, MMAs and stores,
+// frees its tensor memory and returns. Operands in shared memory use the
+// 128-byte swizzled K-major layout that TMA writes.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -39,39 +52,59 @@
 namespace mlp {
 namespace {
 
-constexpr int kThreads = 512;   // 16 warps: warp w serves TMEM lanes 32 (w % 4) .. +32 and column part w / 4
-constexpr int kParts = kThreads / 128;
-constexpr uint32_t kAtom = 128 * 128;          // 128 rows x 64 BF16 (one K atom of a 128-row operand)
+constexpr int kEpiWarps = 12;
+constexpr int kParts = kEpiWarps / 4;            // column parts per TMEM lane quarter
+constexpr int kThreads = 32 * (2 + kEpiWarps);   // 448
+constexpr uint32_t kAtom = 128 * 128;            // 128 rows x 64 BF16 (one K atom of a 128-row operand)
 // Shared memory map (224 KB, offsets from the 1024-aligned base):
-//   [0, 64K)      h1 / g1                         (4 atoms)
-//   [64K, 112K)   h2 / g2                         (3 atoms)
-//   [112K, 160K)  g3                              (3 atoms, 160 of 192 columns used)
-//   [160K, 224K)  weight ring of the backward GEMMs (2 x 32 KB)
-// Split mode also keeps h1_lo at [64K, 128K) during F2 (ring [128K, 224K),
-// 4 x 24 KB) and h2_lo at [112K, 160K) during F3 (ring [160K, 224K), 3 x 20 KB).
-// F1 streams G and W1 chunks through stages overlaying [0, 192K): 4 x 48 KB,
-// or 2 x 96 KB in split mode (G_hi, G_lo, W1_hi, W1_lo per chunk).
+//   [0, 64K)      h1 / g1                          (4 atoms)
+//   [64K, 112K)   h2 / g2                          (3 atoms)
+//   [112K, 160K)  g3 (3 atoms, 160 of 192 columns; column chunk 160..167 of
+//                 each row holds the three E3 energy partial sums of the row)
+//   split only:   h1_lo [64K, 128K) from E1 to F2, h2_lo [112K, 160K) from E2 to F3
+//   B1 only:      dE/dG staging [64K, 112K), one 32-row x 64-column box (4 KB) per epilogue warp
+//   weight rings: F2 [128K, 224K) 4 x 24 KB, F3 [160K, 224K) 3 x 20 KB,
+//                 B3 [160K, 224K) 2 x 32 KB, B2 and B1 [128K, 224K) 3 x 32 KB
+//   F1 stages over [0, 192K): 2 x 96 KB (split: G_hi, G_lo, W1_hi, W1_lo) or 4 x 48 KB
+// The producer switches between region layouts only after the MMAs reading
+// the previous layout have completed, and starts a tile's F1 only after the
+// previous tile's epilogues are done with shared memory.
 constexpr uint32_t kOffH1 = 0;
 constexpr uint32_t kOffH2 = 4 * kAtom;
 constexpr uint32_t kOffG3 = 7 * kAtom;
 constexpr uint32_t kOffH1lo = 4 * kAtom;
 constexpr uint32_t kOffH2lo = 7 * kAtom;
-constexpr uint32_t kOffRB = 10 * kAtom;
-constexpr uint32_t kOffEPart = 216 * 1024;       // energy partial sums during E3 (2 KB)
-constexpr uint32_t kSmemUsed = 14 * kAtom;               // 229,376 bytes
-constexpr uint32_t kSmemAlloc = kSmemUsed + 1024;       // + alignment slack
+constexpr uint32_t kOffStage = 4 * kAtom;
+constexpr uint32_t kOffEPart = kOffG3 + 2 * kAtom;   // + row * 128 + (4 ^ (row & 7)) * 16
+constexpr uint32_t kSmemUsed = 14 * kAtom;           // 229,376 bytes
+constexpr uint32_t kSmemAlloc = kSmemUsed + 1024;    // + alignment slack
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
-enum { kBarF1Full = 0, kBarF1Empty = 4, kBarRBFull = 8, kBarRBEmpty = 12, kBarDone = 16, kNBars = 17 };
+enum {
+    kBarF1Full = 0,     // 4: F1 stage loaded (expect_tx + TMA bytes)
+    kBarF1Empty = 4,    // 4: F1 stage consumed (MMA commit)
+    kBarRFull = 8,      // 4: weight ring slot loaded
+    kBarREmpty = 12,    // 4: weight ring slot consumed
+    kBarAcc = 16,       // 2: accumulator half complete (MMA commit)
+    kBarOp = 18,        // 1: an epilogue finished (operand written, accumulator read); one arrival per epilogue warp
+    kBarB1Free = 19,    // 2: a B1 accumulator half read; one arrival per epilogue warp
+    kBarStage = 21,     // 1: a tile's epilogues are done with shared memory; one arrival per epilogue warp
+    kBarEPart = 22,     // 1: E3 partial sums written; one arrival per epilogue warp
+    kBarDrain = 23,     // 1: teardown MMA drain
+    kNBars = 24
+};
 
 struct TcArgs {
     const Counters* ctr;
     const int* row_atom;
     const float *b1, *b2, *b3, *W4, *b4;
     float* e;
-    __nv_bfloat16* dG;   // [rows][1024] BF16
     int backward;
     int* err;
+};
+
+struct TcMaps {
+    CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t, dG;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -89,18 +122,40 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// try_wait with a suspend-time hint: a waiting thread is parked by the
+// hardware until the phase completes (or the hint expires) instead of
+// spinning, so waiting roles take no issue slots from the working ones.
+constexpr uint32_t kSuspendNs = 1000000u;
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait on a phase: false after kWaitNs.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on a phase: false after kWaitNs (and the abort flag is set), or
+// as soon as another role has set the abort flag.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abrt) {
     if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        {
+            if (*abrt) return false;
+            if (globaltimer() - t0 > kWaitNs) {   // record the waiting warp and barrier
+                *abrt = (int)(0x40000000u | ((threadIdx.x >> 5) << 20) | bar);
+                return false;
+            }
+        }
+    }
+}
+// Bounded wait used by the teardown drains (no abort check).
+__device__ __noinline__ bool mbar_wait_plain(uint32_t bar, uint32_t parity) {
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
@@ -113,6 +168,43 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
             dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+// Same with an L2 eviction-priority policy (createpolicy): the weights stay
+// in L2 while G and dE/dG stream through it.
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src, uint64_t policy) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src), "l"(policy)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -143,8 +235,8 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 consecutive FP32 columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
@@ -152,10 +244,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -182,42 +272,24 @@ __device__ __forceinline__ float celu_f(float x) { return x > 0.f ? x : kCeluAlp
 __device__ __forceinline__ float dcelu_f(float x) { return x > 0.f ? 1.f : __expf(x * (1.f / kCeluAlpha)); }
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : h * (1.f / kCeluAlpha) + 1.f; }
 
-// ------------------------------------------------------------------ issuing thread state
-// Slots 0..3: F1 stages; slots 4..7: weight-ring slots of the other GEMMs.
-struct Issuer {
-    uint32_t bar0;          // shared address of barrier 0 (barriers are 8 bytes apart)
-    uint32_t nfull[8];      // phases consumed per full barrier
-    uint32_t nempty[8];     // phases consumed per empty barrier
-    uint32_t pend;          // slots with an MMA commit not yet waited for
-    uint32_t loaded;        // slots with a TMA load not yet consumed
-    uint32_t f1_next, rb_next;
-    bool ok;
+#ifdef MLP_TC_TRACE
+// Phase timestamps (%globaltimer, ns) of the first tiles of the first CTAs,
+// for performance investigation builds only (-DMLP_TC_TRACE). Points 0..19:
+// epilogue warp 2; 20..26: MMA issuer; 27..31: producer.
+constexpr int kTraceCtas = 8, kTraceTiles = 4, kTracePoints = 32;
+__device__ unsigned long long g_tc_trace[kTraceCtas][kTraceTiles][kTracePoints];
+#define MLP_TC_MARK(k)                                                                   \
+    do {                                                                                 \
+        if (blockIdx.x < kTraceCtas && tile_no < kTraceTiles && (threadIdx.x & 31) == 0) \
+            g_tc_trace[blockIdx.x][tile_no][k] = globaltimer();                          \
+    } while (0)
+#else
+#define MLP_TC_MARK(k) \
+    do {               \
+    } while (0)
+#endif
 
-    __device__ uint32_t bar(int i) const { return bar0 + 8u * (uint32_t)i; }
-    __device__ uint32_t full(int si) const { return si < 4 ? bar(kBarF1Full + si) : bar(kBarRBFull + si - 4); }
-    __device__ uint32_t empty(int si) const { return si < 4 ? bar(kBarF1Empty + si) : bar(kBarRBEmpty + si - 4); }
-
-    __device__ bool acquire(int si) {
-        if (pend & (1u << si)) {
-            if (!mbar_wait(empty(si), nempty[si] & 1u)) return ok = false;
-            nempty[si]++;
-            pend &= ~(1u << si);
-        }
-        return true;
-    }
-    __device__ bool consume(int si) {
-        if (!mbar_wait(full(si), nfull[si] & 1u)) return ok = false;
-        nfull[si]++;
-        loaded &= ~(1u << si);
-        tc_fence_after();
-        return true;
-    }
-    __device__ void release(int si) {
-        mma_commit(empty(si));
-        pend |= 1u << si;
-    }
-};
-
+// ------------------------------------------------------------------ GEMM jobs
 // One GEMM D[128 x N] = A[128 x K] B^T with B streamed by TMA through a ring
 // of slots, one sub-chunk (N rows x 64 K columns) per slot. In split mode
 // every K chunk c brings two sub-chunks, B_hi(c) then B_lo(c), and the MMAs
@@ -234,120 +306,279 @@ struct Job {
     uint32_t ring_off, slot_bytes;
     int slots;
     int split;
-    int st[8];                   // slot of each sub-chunk
     __device__ int nq() const { return split ? 2 * nc : nc; }
+    __device__ uint32_t geom() const { return (ring_off >> 10) | ((slot_bytes >> 10) << 8) | ((uint32_t)slots << 16); }
 };
 
-__device__ __forceinline__ bool load_sub(Issuer& I, uint32_t sbase, Job& J, int q) {
-    const int si = J.st[q];
-    if (!I.acquire(si)) return false;
-    const uint32_t dst = sbase + J.ring_off + (uint32_t)(si - 4) * J.slot_bytes;
-    const int c = J.split ? (q >> 1) : q;
-    const CUtensorMap* m = (J.split && (q & 1)) ? J.map_lo : J.map;
-    mbar_expect_tx(I.full(si), (uint32_t)J.N * 128u);
-    tma_load_2d(dst, m, c * 64, J.brow, I.full(si));
-    I.loaded |= 1u << si;
-    return true;
-}
+enum { kJobF2 = 0, kJobF3 = 1, kJobB3 = 2, kJobB2 = 3, kJobB1 = 4 };   // B1 block j: kJobB1 + j
 
-__device__ bool job_prefetch(Issuer& I, uint32_t sbase, Job& J) {
-    const int nq = J.nq();
-    for (int q = 0; q < J.slots && q < nq; ++q) {
-        J.st[q] = 4 + (int)(I.rb_next % (uint32_t)J.slots);
-        I.rb_next++;
-        if (!load_sub(I, sbase, J, q)) return false;
-    }
-    return true;
-}
-
-__device__ bool job_run(Issuer& I, uint32_t sbase, uint32_t tmem, Job& J) {
-    const uint32_t idesc = idesc_bf16(128, J.N);
-    const int nq = J.nq();
-    bool first = true;
-    for (int q = 0; q < nq; ++q) {
-        const int si = J.st[q];
-        if (!I.consume(si)) return false;
-        const int c = J.split ? (q >> 1) : q;
-        const bool lo_b = J.split && (q & 1);
-        const uint32_t b_base = sbase + J.ring_off + (uint32_t)(si - 4) * J.slot_bytes;
-        const uint32_t a_hi = sbase + J.a_off + (uint32_t)c * kAtom;
-        const uint32_t a_lo = sbase + J.a_lo_off + (uint32_t)c * kAtom;
-        const int ks = (c == J.nc - 1) ? J.lastk : 4;
-        for (int k = 0; k < ks; ++k) {
-            const uint64_t b = sdesc(b_base + 32u * k);
-            mma_bf16(tmem + J.d_col, sdesc(a_hi + 32u * k), b, idesc, first ? 0u : 1u);
-            first = false;
-            if (J.split && !lo_b) mma_bf16(tmem + J.d_col, sdesc(a_lo + 32u * k), b, idesc, 1u);
-        }
-        I.release(si);
-        const int nxt = q - 1 + J.slots;
-        if (q >= 1 && nxt < nq) {
-            J.st[nxt] = J.st[q - 1];
-            if (!load_sub(I, sbase, J, nxt)) return false;
-        }
-    }
-    mma_commit(I.bar(kBarDone));
-    return true;
-}
-
-// Layer 1: A (G) and B (W1) both streamed, K = 1024 in 16 chunks.
 template <bool SPLIT>
-__device__ bool f1_run(Issuer& I, uint32_t sbase, uint32_t tmem, const CUtensorMap* mG, const CUtensorMap* mGlo,
-                       const CUtensorMap* mW1, const CUtensorMap* mW1lo, int row0, int s) {
-    constexpr int nc = kAevLd / 64;                       // 16
+__device__ __forceinline__ Job make_job(const TcMaps& M, int k, int s) {
+    switch (k) {
+        case kJobF2:
+            return Job{&M.W2, &M.W2lo, s * kH2, 4, 4, kOffH1, kOffH1lo, 256, kH2, 8 * kAtom, (uint32_t)kH2 * 128u,
+                       4, SPLIT ? 1 : 0};
+        case kJobF3:
+            return Job{&M.W3, &M.W3lo, s * kH3, 3, 4, kOffH2, kOffH2lo, 0, kH3, 10 * kAtom, (uint32_t)kH3 * 128u,
+                       3, SPLIT ? 1 : 0};
+        case kJobB3:
+            return Job{&M.W3t, nullptr, s * kH2, 3, 2, kOffG3, 0, 256, kH2, 10 * kAtom, 32768u, 2, 0};
+        case kJobB2:
+            return Job{&M.W2t, nullptr, s * kH1, 3, 4, kOffH2, 0, 0, kH1, 8 * kAtom, 32768u, 3, 0};
+        default: {
+            const int j = k - kJobB1;
+            return Job{&M.W1t, nullptr, s * kAevLd + 256 * j, 4, 4, kOffH1, 0, 256u * (uint32_t)(j & 1), 256,
+                       8 * kAtom, 32768u, 3, 0};
+        }
+    }
+}
+
+// ------------------------------------------------------------------ producer
+struct ProdState {
+    uint32_t f1_uses[4], f1_freed[4];   // F1 stage loads issued / consumptions observed
+    uint32_t r_uses[4], r_freed[4];     // weight ring slots
+    uint32_t f1pos, rpos, geom;
+};
+
+__device__ __forceinline__ bool prod_free(uint32_t empty_bar, uint32_t& freed, uint32_t uses, volatile int* abrt) {
+    while (freed < uses) {
+        if (!mbar_wait(empty_bar, freed & 1u, abrt)) return false;
+        ++freed;
+    }
+    return true;
+}
+
+__device__ bool prod_drain_ring(ProdState& P, uint32_t bar0, volatile int* abrt) {
+    for (int si = 0; si < 4; ++si)
+        if (!prod_free(bar0 + 8u * (kBarREmpty + si), P.r_freed[si], P.r_uses[si], abrt)) return false;
+    return true;
+}
+__device__ bool prod_drain_f1(ProdState& P, uint32_t bar0, volatile int* abrt) {
+    for (int st = 0; st < 4; ++st)
+        if (!prod_free(bar0 + 8u * (kBarF1Empty + st), P.f1_freed[st], P.f1_uses[st], abrt)) return false;
+    return true;
+}
+
+__device__ __noinline__ bool prod_job(ProdState& P, const Job& Jref, uint32_t sbase, uint32_t bar0,
+                                      volatile int* abrt) {
+    const Job J = Jref;
+    const uint64_t keep = policy_evict_last();
+    if (J.geom() != P.geom) {   // new slot layout: every slot of the old one must be consumed
+        if (!prod_drain_ring(P, bar0, abrt)) return false;
+        P.geom = J.geom();
+        P.rpos = 0;
+    }
+    const int nq = J.nq();
+    for (int q = 0; q < nq; ++q) {
+        const int si = (int)(P.rpos++ % (uint32_t)J.slots);
+        if (!prod_free(bar0 + 8u * (kBarREmpty + si), P.r_freed[si], P.r_uses[si], abrt)) return false;
+        const int c = J.split ? (q >> 1) : q;
+        const CUtensorMap* m = (J.split && (q & 1)) ? J.map_lo : J.map;
+        const uint32_t full = bar0 + 8u * (kBarRFull + si);
+        mbar_expect_tx(full, (uint32_t)J.N * 128u);
+        tma_load_2d_hint(sbase + J.ring_off + (uint32_t)si * J.slot_bytes, m, c * 64, J.brow, full, keep);
+        P.r_uses[si]++;
+    }
+    return true;
+}
+
+__device__ void prefetch_g(const TcMaps& M, int row0, bool split) {
+    for (int c = 0; c < kAevLd / 64; ++c) {
+        tma_prefetch_2d(&M.G, c * 64, row0);
+        if (split) tma_prefetch_2d(&M.Glo, c * 64, row0);
+    }
+}
+
+template <bool SPLIT>
+__device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t bar0, volatile int* abrt,
+                         bool backward, ProdState& P) {
     constexpr int nst = SPLIT ? 2 : 4;
     constexpr uint32_t stage = SPLIT ? 98304u : 49152u;   // A (+A_lo) 16 KB each, B (+B_lo) 32 KB each
-    const uint32_t idesc = idesc_bf16(128, kH1);
-    int st[nc];
-    auto load = [&](int c) -> bool {
-        const int si = st[c];
-        if (!I.acquire(si)) return false;
-        const uint32_t dst = sbase + (uint32_t)si * stage;
-        mbar_expect_tx(I.full(si), stage);
-        tma_load_2d(dst, mG, c * 64, row0, I.full(si));
-        if (SPLIT) {
-            tma_load_2d(dst + 16384u, mGlo, c * 64, row0, I.full(si));
-            tma_load_2d(dst + 32768u, mW1, c * 64, s * kH1, I.full(si));
-            tma_load_2d(dst + 65536u, mW1lo, c * 64, s * kH1, I.full(si));
-        } else {
-            tma_load_2d(dst + 16384u, mW1, c * 64, s * kH1, I.full(si));
-        }
-        I.loaded |= 1u << si;
-        return true;
-    };
-    for (int c = 0; c < nst; ++c) {
-        st[c] = (int)(I.f1_next % (uint32_t)nst);
-        I.f1_next++;
-        if (!load(c)) return false;
-    }
-    for (int c = 0; c < nc; ++c) {
-        const int si = st[c];
-        if (!I.consume(si)) return false;
-        const uint32_t base = sbase + (uint32_t)si * stage;
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-            if (SPLIT) {
-                const uint64_t ah = sdesc(base + 32u * k), al = sdesc(base + 16384u + 32u * k);
-                const uint64_t bh = sdesc(base + 32768u + 32u * k), bl = sdesc(base + 65536u + 32u * k);
-                mma_bf16(tmem, ah, bh, idesc, acc);
-                mma_bf16(tmem, al, bh, idesc, 1u);
-                mma_bf16(tmem, ah, bl, idesc, 1u);
-            } else {
-                mma_bf16(tmem, sdesc(base + 32u * k), sdesc(base + 16384u + 32u * k), idesc, acc);
+    const CUtensorMap* maps[12] = {&M.G, &M.Glo, &M.W1, &M.W1lo, &M.W2, &M.W2lo, &M.W3, &M.W3lo, &M.W3t, &M.W2t,
+                                   &M.W1t, &M.dG};
+    for (int q = 0; q < 12; ++q) prefetch_map(maps[q]);
+    const uint64_t keep = policy_evict_last();
+    int tile_no = 0;
+    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
+        int s, row0, nvalid;
+        if (!tile_info(counts, t, s, row0, nvalid)) break;
+        if (tile_no == 0) prefetch_g(M, row0, SPLIT);
+        // F1 stages cover every region: the previous tile's epilogues and MMAs must be done with them
+        if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
+        if (!prod_drain_ring(P, bar0, abrt)) break;
+        bool ok = true;
+        for (int c = 0; c < kAevLd / 64 && ok; ++c) {
+            const int st = (int)(P.f1pos++ % (uint32_t)nst);
+            if (!prod_free(bar0 + 8u * (kBarF1Empty + st), P.f1_freed[st], P.f1_uses[st], abrt)) {
+                ok = false;
+                break;
             }
+            const uint32_t full = bar0 + 8u * (kBarF1Full + st), dst = sbase + (uint32_t)st * stage;
+            mbar_expect_tx(full, stage);
+            tma_load_2d(dst, &M.G, c * 64, row0, full);
+            if (SPLIT) {
+                tma_load_2d(dst + 16384u, &M.Glo, c * 64, row0, full);
+                tma_load_2d_hint(dst + 32768u, &M.W1, c * 64, s * kH1, full, keep);
+                tma_load_2d_hint(dst + 65536u, &M.W1lo, c * 64, s * kH1, full, keep);
+            } else {
+                tma_load_2d_hint(dst + 16384u, &M.W1, c * 64, s * kH1, full, keep);
+            }
+            P.f1_uses[st]++;
+            if (c == 0) MLP_TC_MARK(27);
         }
-        I.release(si);
-        if (c >= 1 && c - 1 + nst < nc) {
-            st[c - 1 + nst] = st[c - 1];
-            if (!load(c - 1 + nst)) return false;
+        if (!ok) break;
+        MLP_TC_MARK(28);
+        // the F2 ring overlays the F1 stages
+        if (!prod_drain_f1(P, bar0, abrt)) break;
+        if (!prod_job(P, make_job<SPLIT>(M, kJobF2, s), sbase, bar0, abrt)) break;
+        MLP_TC_MARK(29);
+        if (!prod_job(P, make_job<SPLIT>(M, kJobF3, s), sbase, bar0, abrt)) break;
+        int sn, rown, nvn;
+        const bool has_next = tile_info(counts, t + (int)gridDim.x, sn, rown, nvn);
+        if (!backward) {
+            if (has_next) prefetch_g(M, rown, SPLIT);
+            continue;
         }
+        if (!prod_job(P, make_job<SPLIT>(M, kJobB3, s), sbase, bar0, abrt)) break;
+        if (has_next) prefetch_g(M, rown, SPLIT);
+        if (!prod_job(P, make_job<SPLIT>(M, kJobB2, s), sbase, bar0, abrt)) break;
+        for (int j = 0; j < 4 && ok; ++j) ok = prod_job(P, make_job<SPLIT>(M, kJobB1 + j, s), sbase, bar0, abrt);
+        if (!ok) break;
+        MLP_TC_MARK(30);
     }
-    mma_commit(I.bar(kBarDone));
-    return true;
 }
 
-// Epilogue helper: 16 values of this thread's row -> BF16 hi (and lo) in the
-// operand layout at column c0.
+// ------------------------------------------------------------------ MMA issuer
+struct MmaState {
+    uint32_t f1_full[4], r_full[4];   // loads consumed per F1 stage / ring slot
+    uint32_t f1pos, rpos, geom;
+};
+
+// The job and the ring position are copied into registers first: the MMA
+// asm statements clobber memory, so fields read through references would be
+// reloaded from local memory before every MMA.
+__device__ __noinline__ bool mma_job(MmaState& S, const Job& Jref, uint32_t sbase, uint32_t tmem, uint32_t bar0,
+                                     volatile int* abrt) {
+    const Job J = Jref;
+    const uint32_t geom = J.geom();
+    uint32_t rpos = S.geom == geom ? S.rpos : 0u;
+    S.geom = geom;
+    const uint32_t idesc = idesc_bf16(128, J.N);
+    const uint32_t d = tmem + J.d_col;
+    const int nq = J.nq(), nc = J.nc, lastk = J.lastk, slots = J.slots;
+    const bool split = J.split != 0;
+    const uint32_t ring = sbase + J.ring_off, slot_bytes = J.slot_bytes;
+    const uint32_t a0 = sbase + J.a_off, a0lo = sbase + J.a_lo_off;
+    bool ok = true;
+    for (int q = 0; q < nq; ++q) {
+        const int si = (int)(rpos++ % (uint32_t)slots);
+        const uint32_t nf = S.r_full[si];
+        if (!mbar_wait(bar0 + 8u * (kBarRFull + si), nf & 1u, abrt)) {
+            ok = false;
+            break;
+        }
+        S.r_full[si] = nf + 1u;
+        tc_fence_after();
+        const int c = split ? (q >> 1) : q;
+        const bool lo_b = split && (q & 1);
+        const uint32_t b_base = ring + (uint32_t)si * slot_bytes;
+        const uint32_t a_hi = a0 + (uint32_t)c * kAtom;
+        const uint32_t a_lo = a0lo + (uint32_t)c * kAtom;
+        const int ks = (c == nc - 1) ? lastk : 4;
+        for (int k = 0; k < ks; ++k) {
+            const uint64_t b = sdesc(b_base + 32u * k);
+            if (lo_b) {
+                mma_bf16(d, sdesc(a_hi + 32u * k), b, idesc, 1u);
+            } else {
+                mma_bf16(d, sdesc(a_hi + 32u * k), b, idesc, (q == 0 && k == 0) ? 0u : 1u);
+                if (split) mma_bf16(d, sdesc(a_lo + 32u * k), b, idesc, 1u);
+            }
+        }
+        mma_commit(bar0 + 8u * (kBarREmpty + si));
+    }
+    S.rpos = rpos;
+    return ok;
+}
+
+template <bool SPLIT>
+__device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t tmem, uint32_t bar0,
+                           volatile int* abrt, bool backward, MmaState& S) {
+    constexpr int nst = SPLIT ? 2 : 4;
+    constexpr uint32_t stage = SPLIT ? 98304u : 49152u;
+    const uint32_t idesc1 = idesc_bf16(128, kH1);
+    uint32_t n_op = 0, n_b1[2] = {0, 0};
+    auto wait_op = [&]() -> bool {
+        if (!mbar_wait(bar0 + 8u * kBarOp, n_op & 1u, abrt)) return false;
+        ++n_op;
+        tc_fence_after();
+        return true;
+    };
+    auto wait_b1 = [&](int h) -> bool {
+        if (!mbar_wait(bar0 + 8u * (kBarB1Free + h), n_b1[h] & 1u, abrt)) return false;
+        ++n_b1[h];
+        tc_fence_after();
+        return true;
+    };
+    auto job = [&](int k, int s, int half) -> bool {
+        if (!mma_job(S, make_job<SPLIT>(M, k, s), sbase, tmem, bar0, abrt)) return false;
+        mma_commit(bar0 + 8u * (kBarAcc + half));
+        return true;
+    };
+    int tile_no = 0;
+    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
+        int s, row0, nvalid;
+        if (!tile_info(counts, t, s, row0, nvalid)) break;
+        // F1 writes accumulator half 0: the previous tile's last reader of it must be done
+        if (tile_no > 0 && !(backward ? wait_b1(0) : wait_op())) break;
+        MLP_TC_MARK(20);
+        bool ok = true;
+        for (int c = 0; c < kAevLd / 64; ++c) {
+            const int st = (int)(S.f1pos++ % (uint32_t)nst);
+            if (!mbar_wait(bar0 + 8u * (kBarF1Full + st), S.f1_full[st] & 1u, abrt)) {
+                ok = false;
+                break;
+            }
+            S.f1_full[st]++;
+            tc_fence_after();
+            const uint32_t base = sbase + (uint32_t)st * stage;
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                if (SPLIT) {
+                    const uint64_t ah = sdesc(base + 32u * k), al = sdesc(base + 16384u + 32u * k);
+                    const uint64_t bh = sdesc(base + 32768u + 32u * k), bl = sdesc(base + 65536u + 32u * k);
+                    mma_bf16(tmem, ah, bh, idesc1, acc);
+                    mma_bf16(tmem, al, bh, idesc1, 1u);
+                    mma_bf16(tmem, ah, bl, idesc1, 1u);
+                } else {
+                    mma_bf16(tmem, sdesc(base + 32u * k), sdesc(base + 16384u + 32u * k), idesc1, acc);
+                }
+            }
+            mma_commit(bar0 + 8u * (kBarF1Empty + st));
+        }
+        if (!ok) break;
+        mma_commit(bar0 + 8u * kBarAcc);
+        MLP_TC_MARK(21);
+        // F2 writes half 1: the previous tile's last B1 block must have been read
+        if (backward && tile_no > 0 && !wait_b1(1)) break;
+        if (!wait_op() || !job(kJobF2, s, 1)) break;   // after E1
+        MLP_TC_MARK(22);
+        if (!wait_op() || !job(kJobF3, s, 0)) break;   // after E2
+        MLP_TC_MARK(23);
+        if (!backward) continue;
+        if (!wait_op() || !job(kJobB3, s, 1)) break;   // after E3
+        MLP_TC_MARK(24);
+        if (!wait_op() || !job(kJobB2, s, 0)) break;   // after EB3
+        MLP_TC_MARK(25);
+        if (!wait_op() || !job(kJobB1 + 0, s, 0)) break;   // after EB2
+        if (!job(kJobB1 + 1, s, 1)) break;
+        if (!wait_b1(0) || !job(kJobB1 + 2, s, 0)) break;
+        if (!wait_b1(1) || !job(kJobB1 + 3, s, 1)) break;
+        MLP_TC_MARK(26);
+    }
+}
+
+// ------------------------------------------------------------------ epilogues
+// 16 values of this thread's row -> BF16 hi (and lo) in the operand layout at column c0.
 template <bool SPLIT>
 __device__ __forceinline__ void store_act(uint32_t sbase, uint32_t off_hi, uint32_t off_lo, int r, int c0,
                                           const float (&h)[16]) {
@@ -369,147 +600,121 @@ __device__ __forceinline__ void store_act(uint32_t sbase, uint32_t off_hi, uint3
     }
 }
 
-#ifdef MLP_TC_TRACE
-// Phase timestamps (%globaltimer, ns) of the first tiles of the first CTAs,
-// for performance investigation builds only (-DMLP_TC_TRACE).
-constexpr int kTraceCtas = 8, kTraceTiles = 4, kTracePoints = 32;
-__device__ unsigned long long g_tc_trace[kTraceCtas][kTraceTiles][kTracePoints];
-#define MLP_TC_MARK(k)                                                                                  \
-    do {                                                                                                \
-        if (tid == 0 && blockIdx.x < kTraceCtas && tile_no < kTraceTiles) g_tc_trace[blockIdx.x][tile_no][k] = globaltimer(); \
-    } while (0)
-#else
-#define MLP_TC_MARK(k) \
-    do {               \
-    } while (0)
-#endif
+// g = D * celu'(h) over the stored activation h (in place), 16 columns at c0.
+__device__ __forceinline__ void store_grad(uint32_t sbase, uint32_t off, int r, int c0, const uint32_t (&d)[16]) {
+#pragma unroll
+    for (int hlf = 0; hlf < 2; ++hlf) {
+        const uint32_t a = sbase + off + op_off(r, c0 + 8 * hlf);
+        const uint4 h = ld_shared_v4(a);
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float d0 = __uint_as_float(d[8 * hlf + 2 * q]), d1 = __uint_as_float(d[8 * hlf + 2 * q + 1]);
+            o[q] = pack_bf16(d0 * dcelu_h(bf_lo(hw[q])), d1 * dcelu_h(bf_hi(hw[q])));
+        }
+        st_shared_v4(a, o[0], o[1], o[2], o[3]);
+    }
+}
 
-struct TcMaps {
-    CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t;
+struct EpiCtx {
+    uint32_t sbase, bar0, tl;   // tl: TMEM address of this warp's lane quarter
+    volatile int* abrt;
+    int lane, part, r;
+    uint32_t n_acc[2];
 };
 
-template <bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ TcMaps M, TcArgs p) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) unsigned long long bars[kNBars];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int part = warp >> 2;   // which 16-column chunks this warp takes: part, part + kParts, ...
-    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
-
-    Issuer I;
-    I.bar0 = smem_u32(&bars[0]);
-    for (int q = 0; q < 8; ++q) I.nfull[q] = I.nempty[q] = 0;
-    I.pend = I.loaded = 0;
-    I.f1_next = I.rb_next = 0;
-    I.ok = true;
-    uint32_t n_done = 0;
-
-    if (tid == 0) {
-        for (int q = 0; q < kNBars; ++q) mbar_init(smem_u32(&bars[q]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_flag = 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
+// Lane 0 waits, the warp follows (one decision per warp).
+__device__ __forceinline__ bool epi_wait(EpiCtx& X, uint32_t bar, uint32_t parity) {
+    int ok = 1;
+    if (X.lane == 0) ok = mbar_wait(bar, parity, X.abrt) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
-    const int r = (warp & 3) * 32 + lane;                              // tile row = TMEM lane
+    return ok != 0;
+}
+__device__ __forceinline__ bool epi_acc(EpiCtx& X, int half) {
+    const bool ok = epi_wait(X, X.bar0 + 8u * (kBarAcc + half), X.n_acc[half] & 1u);
+    X.n_acc[half]++;
+    return ok;
+}
+// This warp's shared-memory writes and TMEM reads are done: one arrival.
+__device__ __forceinline__ void epi_arrive(EpiCtx& X, uint32_t bar) {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncwarp();
+    if (X.lane == 0) mbar_arrive(bar);
+}
 
-    auto wait_done = [&]() {
-        if (!mbar_wait(I.bar(kBarDone), n_done & 1u)) atomicExch(&abort_flag, 1);
-        n_done++;
-        __syncwarp();   // the epilogue's tcgen05.ld are warp-collective
-        tc_fence_after();
-    };
-    auto sync_all = [&]() -> bool {
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        return abort_flag == 0;
-    };
-    auto issue_fail = [&]() { atomicExch(&abort_flag, 1); };
-
-    int tile_no = -1;
-    (void)tile_no;
-    for (int t = blockIdx.x;; t += gridDim.x) {
-        ++tile_no;
-        MLP_TC_MARK(0);
+// Epilogue loops take one 16-column chunk per iteration, chunks c0 = 16
+// (part + kParts k) < N, and are kept rolled: the code of every phase stays
+// small, so the epilogue warps keep hitting in the instruction cache.
+template <bool SPLIT>
+__device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, EpiCtx& X, int warp) {
+    const uint32_t sbase = X.sbase, bar0 = X.bar0;
+    const uint32_t op_bar = bar0 + 8u * kBarOp;
+    const int r = X.r, part = X.part;
+    const uint32_t stage_box = sbase + kOffStage + (uint32_t)(warp - 2) * 4096u;
+    const uint64_t stream_out = policy_evict_first();
+    uint32_t n_epart = 0;
+    int tile_no = 0;
+    (void)warp;
+    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
         int s, row0, nvalid;
-        if (!tile_info(p.ctr->species, t, s, row0, nvalid)) break;
+        if (!tile_info(counts, t, s, row0, nvalid)) break;
+        if (warp == 2) MLP_TC_MARK(0);
         const float* b1 = p.b1 + s * kH1;
         const float* b2 = p.b2 + s * kH2;
         const float* b3 = p.b3 + s * kH3;
         const float* w4 = p.W4 + s * kH3;
-        // forward jobs (ring geometry depends on the mode), backward jobs
-        Job jF2 = SPLIT ? Job{&M.W2, &M.W2lo, s * kH2, 4, 4, kOffH1, kOffH1lo, 256, kH2, 8 * kAtom,
-                              (uint32_t)kH2 * 128u, 4, 1, {0}}
-                        : Job{&M.W2, nullptr, s * kH2, 4, 4, kOffH1, 0, 256, kH2, kOffRB, 32768u, 2, 0, {0}};
-        Job jF3 = SPLIT ? Job{&M.W3, &M.W3lo, s * kH3, 3, 4, kOffH2, kOffH2lo, 0, kH3, kOffRB, (uint32_t)kH3 * 128u,
-                              3, 1, {0}}
-                        : Job{&M.W3, nullptr, s * kH3, 3, 4, kOffH2, 0, 0, kH3, kOffRB, 32768u, 2, 0, {0}};
-        Job jB3{&M.W3t, nullptr, s * kH2, 3, 2, kOffG3, 0, 256, kH2, kOffRB, 32768u, 2, 0, {0}};
-        Job jB2{&M.W2t, nullptr, s * kH1, 3, 4, kOffH2, 0, 0, kH1, kOffRB, 32768u, 2, 0, {0}};
 
-        // ---- F1 -> E1
-        if (tid == 0 && !f1_run<SPLIT>(I, sbase, tmem, &M.G, &M.Glo, &M.W1, &M.W1lo, row0, s)) issue_fail();
-        MLP_TC_MARK(1);
-        wait_done();
-        MLP_TC_MARK(2);
-        if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF2)) issue_fail();
+        // ---- E1: h1 = celu(D + b1)
+        if (!epi_acc(X, 0)) break;
+        if (warp == 2) MLP_TC_MARK(1);
+#pragma unroll 1
         for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
+            uint32_t d[16];
+            tmem_ld16(X.tl + (uint32_t)c0, d);
+            tmem_wait_ld();
             float v[16];
-            tmem_ld16(tl + (uint32_t)c0, v);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = celu_f(v[q] + __ldg(b1 + c0 + q));
+            for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b1 + c0 + q));
             store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
         }
-        if (!sync_all()) break;
-        MLP_TC_MARK(3);
+        epi_arrive(X, op_bar);
+        if (warp == 2) MLP_TC_MARK(2);
 
-        // ---- F2 -> E2
-        if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF2)) issue_fail();
-        MLP_TC_MARK(4);
-        wait_done();
-        MLP_TC_MARK(5);
-        if (tid == 0 && I.ok && !job_prefetch(I, sbase, jF3)) issue_fail();
+        // ---- E2: h2 = celu(D + b2)
+        if (!epi_acc(X, 1)) break;
+        if (warp == 2) MLP_TC_MARK(3);
+#pragma unroll 1
         for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
+            uint32_t d[16];
+            tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
+            tmem_wait_ld();
             float v[16];
-            tmem_ld16(tl + 256u + (uint32_t)c0, v);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = celu_f(v[q] + __ldg(b2 + c0 + q));
+            for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b2 + c0 + q));
             store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
         }
-        if (!sync_all()) break;
-        MLP_TC_MARK(6);
+        epi_arrive(X, op_bar);
+        if (warp == 2) MLP_TC_MARK(4);
 
-        // ---- F3 -> E3 (energy, g3). Each part sums its own column chunks of
-        // w4 . celu(z3); the four partial sums of a row meet in [216K, 218K),
-        // a corner no load touches during E3 (the B3 prefetch fills
-        // [160K, 184K) and [192K, 216K)), and are added in fixed order.
-        if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jF3)) issue_fail();
-        MLP_TC_MARK(7);
-        wait_done();
-        MLP_TC_MARK(8);
-        if (tid == 0 && I.ok && p.backward && !job_prefetch(I, sbase, jB3)) issue_fail();
+        // ---- E3: energy (four column-part partial sums per row, added in
+        // fixed order by part 0) and g3 = w4 * celu'(z3)
+        if (!epi_acc(X, 0)) break;
+        if (warp == 2) MLP_TC_MARK(5);
         {
             float es = 0.f;
+#pragma unroll 1
             for (int c0 = 16 * part; c0 < kH3; c0 += 16 * kParts) {
-                float v[16];
-                tmem_ld16(tl + (uint32_t)c0, v);
+                uint32_t d[16];
+                tmem_ld16(X.tl + (uint32_t)c0, d);
+                tmem_wait_ld();
                 uint32_t pk[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const float z0 = v[2 * q] + __ldg(b3 + c0 + 2 * q), z1 = v[2 * q + 1] + __ldg(b3 + c0 + 2 * q + 1);
+                    const float z0 = __uint_as_float(d[2 * q]) + __ldg(b3 + c0 + 2 * q);
+                    const float z1 = __uint_as_float(d[2 * q + 1]) + __ldg(b3 + c0 + 2 * q + 1);
                     const float w0 = __ldg(w4 + c0 + 2 * q), w1 = __ldg(w4 + c0 + 2 * q + 1);
                     es = fmaf(w0, celu_f(z0), es);
                     es = fmaf(w1, celu_f(z1), es);
@@ -520,128 +725,208 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
                 }
             }
-            float* e_part = reinterpret_cast<float*>(smem_raw + (sbase - smem_u32(smem_raw)) + kOffEPart);
-            e_part[part * 128 + r] = es;
-            __syncthreads();
-            if (part == 0 && r < nvalid) {
-                float t = __ldg(p.b4 + s);
-#pragma unroll
-                for (int q = 0; q < kParts; ++q) t += e_part[q * 128 + r];
-                p.e[p.row_atom[row0 + r]] = t;
-            }
-        }
-        if (!sync_all()) break;
-        MLP_TC_MARK(9);
-        if (!p.backward) continue;
-
-        // ---- B3 -> g2 (over h2)
-        if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB3)) issue_fail();
-        MLP_TC_MARK(10);
-        wait_done();
-        MLP_TC_MARK(11);
-        if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB2)) issue_fail();
-        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
-            float v[16];
-            tmem_ld16(tl + 256u + (uint32_t)c0, v);
-#pragma unroll
-            for (int hlf = 0; hlf < 2; ++hlf) {
-                const uint32_t a = sbase + kOffH2 + op_off(r, c0 + 8 * hlf);
-                const uint4 h = ld_shared_v4(a);
-                const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
-                uint32_t o[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float* vv = v + 8 * hlf + 2 * q;
-                    o[q] = pack_bf16(vv[0] * dcelu_h(bf_lo(hw[q])), vv[1] * dcelu_h(bf_hi(hw[q])));
-                }
-                st_shared_v4(a, o[0], o[1], o[2], o[3]);
-            }
-        }
-        if (!sync_all()) break;
-        MLP_TC_MARK(12);
-
-        // ---- B2 -> g1 (over h1)
-        if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB2)) issue_fail();
-        MLP_TC_MARK(13);
-        wait_done();
-        MLP_TC_MARK(14);
-        Job jB1{&M.W1t, nullptr, s * kAevLd, 4, 4, kOffH1, 0, 0, 256, kOffRB, 32768u, 2, 0, {0}};
-        if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
-        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
-            float v[16];
-            tmem_ld16(tl + (uint32_t)c0, v);
-#pragma unroll
-            for (int hlf = 0; hlf < 2; ++hlf) {
-                const uint32_t a = sbase + kOffH1 + op_off(r, c0 + 8 * hlf);
-                const uint4 h = ld_shared_v4(a);
-                const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
-                uint32_t o[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float* vv = v + 8 * hlf + 2 * q;
-                    o[q] = pack_bf16(vv[0] * dcelu_h(bf_lo(hw[q])), vv[1] * dcelu_h(bf_hi(hw[q])));
-                }
-                st_shared_v4(a, o[0], o[1], o[2], o[3]);
-            }
-        }
-        if (!sync_all()) break;
-        MLP_TC_MARK(15);
-
-        // ---- B1: four 256-column blocks of dE/dG, alternating TMEM halves
-        bool aborted = false;
-        for (int j = 0; j < 4; ++j) {
-            if (tid == 0 && I.ok && !job_run(I, sbase, tmem, jB1)) issue_fail();
-            MLP_TC_MARK(16 + 2 * j);
-            wait_done();
-            MLP_TC_MARK(17 + 2 * j);
-            const uint32_t dcol = jB1.d_col;
-            if (j < 3) {
-                jB1.brow = s * kAevLd + 256 * (j + 1);
-                jB1.d_col = 256u * (uint32_t)((j + 1) & 1);
-                if (tid == 0 && I.ok && !job_prefetch(I, sbase, jB1)) issue_fail();
-            }
-            __nv_bfloat16* out = p.dG + (size_t)(row0 + r) * kAevLd + 256 * j;
-            for (int c0 = 16 * part; c0 < 256; c0 += 16 * kParts) {
-                float v[16];
-                tmem_ld16(tl + dcol + (uint32_t)c0, v);
+            const uint32_t ep = sbase + kOffEPart + (uint32_t)r * 128u + (uint32_t)((4 ^ (r & 7)) << 4);
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(ep + 4u * (uint32_t)part), "f"(es) : "memory");
+            __syncwarp();
+            if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarEPart);
+            if (part == 0) {
+                if (!epi_wait(X, bar0 + 8u * kBarEPart, n_epart & 1u)) break;
                 if (r < nvalid) {
-                    uint4 o0, o1;
-                    o0.x = pack_bf16(v[0], v[1]);
-                    o0.y = pack_bf16(v[2], v[3]);
-                    o0.z = pack_bf16(v[4], v[5]);
-                    o0.w = pack_bf16(v[6], v[7]);
-                    o1.x = pack_bf16(v[8], v[9]);
-                    o1.y = pack_bf16(v[10], v[11]);
-                    o1.z = pack_bf16(v[12], v[13]);
-                    o1.w = pack_bf16(v[14], v[15]);
-                    *reinterpret_cast<uint4*>(out + c0) = o0;
-                    *reinterpret_cast<uint4*>(out + c0 + 8) = o1;
+                    const uint4 v = ld_shared_v4(ep);
+                    float e = __ldg(p.b4 + s);
+                    e += __uint_as_float(v.x);
+                    e += __uint_as_float(v.y);
+                    e += __uint_as_float(v.z);
+                    p.e[p.row_atom[row0 + r]] = e;
                 }
             }
-            if (!sync_all()) {
-                aborted = true;
+            ++n_epart;
+        }
+        epi_arrive(X, op_bar);
+        if (warp == 2) MLP_TC_MARK(6);
+        if (!p.backward) {
+            __syncwarp();
+            if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
+            continue;
+        }
+
+        // ---- EB3: g2 = D * celu'(z2) over h2
+        if (!epi_acc(X, 1)) break;
+        if (warp == 2) MLP_TC_MARK(7);
+#pragma unroll 1
+        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
+            uint32_t d[16];
+            tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
+            tmem_wait_ld();
+            store_grad(sbase, kOffH2, r, c0, d);
+        }
+        epi_arrive(X, op_bar);
+        if (warp == 2) MLP_TC_MARK(8);
+
+        // ---- EB2: g1 = D * celu'(z1) over h1
+        if (!epi_acc(X, 0)) break;
+        if (warp == 2) MLP_TC_MARK(9);
+#pragma unroll 1
+        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
+            uint32_t d[16];
+            tmem_ld16(X.tl + (uint32_t)c0, d);
+            tmem_wait_ld();
+            store_grad(sbase, kOffH1, r, c0, d);
+        }
+        epi_arrive(X, op_bar);
+        if (warp == 2) MLP_TC_MARK(10);
+
+        // ---- EB1: four 256-column blocks of dE/dG, 16 boxes of 64 columns
+        // per tile; box g = 4 j + b goes to part g % 3. A warp converts its
+        // boxes (its 32 rows) to BF16 in its 4 KB swizzled staging box and
+        // writes each with one TMA store.
+        bool ok = true;
+        for (int j = 0; j < 4; ++j) {
+            const int h = j & 1;
+            if (!epi_acc(X, h)) {
+                ok = false;
                 break;
             }
+            if (warp == 2) MLP_TC_MARK(11 + 2 * j);
+            int nb = 0;
+#pragma unroll 1
+            for (int b = 0; b < 4; ++b) {
+                if ((4 * j + b) % kParts != part) continue;
+                uint32_t d[4][16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tmem_ld16(X.tl + 256u * (uint32_t)h + (uint32_t)(64 * b + 16 * k), d[k]);
+                tmem_wait_ld();
+                ++nb;
+                if (X.lane == 0) bulk_wait_read0();   // the previous store has read the staging box
+                __syncwarp();
+                const uint32_t rowb = stage_box + (uint32_t)X.lane * 128u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint32_t* v = d[k] + 8 * hh;
+                        const uint32_t chunk = (uint32_t)((2 * k + hh) ^ (X.lane & 7));
+                        st_shared_v4(rowb + chunk * 16u, pack_bf16(__uint_as_float(v[0]), __uint_as_float(v[1])),
+                                     pack_bf16(__uint_as_float(v[2]), __uint_as_float(v[3])),
+                                     pack_bf16(__uint_as_float(v[4]), __uint_as_float(v[5])),
+                                     pack_bf16(__uint_as_float(v[6]), __uint_as_float(v[7])));
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (X.lane == 0) tma_store_2d(&M.dG, 256 * j + 64 * b, row0 + 32 * (warp & 3), stage_box, stream_out);
+            }
+            (void)nb;
+            // this warp is done reading accumulator half h
+            tc_fence_before();
+            __syncwarp();
+            if (X.lane == 0) mbar_arrive(bar0 + 8u * (kBarB1Free + h));
+            if (warp == 2) MLP_TC_MARK(12 + 2 * j);
         }
-        if (aborted) break;
-        MLP_TC_MARK(24);
+        if (!ok) break;
+        if (X.lane == 0) {
+            bulk_wait_read0();
+            mbar_arrive(bar0 + 8u * kBarStage);
+        }
+        __syncwarp();
+        if (warp == 2) MLP_TC_MARK(19);
     }
+}
 
-    // ---- teardown: drain own copies and MMAs (bounded), free tensor memory
-    __syncthreads();
-    if (abort_flag) {
-        if (tid == 0) {
-            atomicOr(p.err, 1);
-            for (int si = 0; si < 8; ++si)
-                if (I.loaded & (1u << si)) (void)mbar_wait(I.full(si), I.nfull[si] & 1u);
-            mma_commit(I.bar(kBarDone));
-            (void)mbar_wait(I.bar(kBarDone), n_done & 1u);
+// ------------------------------------------------------------------ kernel
+template <bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ TcMaps M, TcArgs p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) unsigned long long bars[kNBars];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int counts[8];
+    __shared__ uint32_t consumed[8];   // teardown: loads consumed per F1 stage (0..3) and ring slot (4..7)
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    volatile int* abrt = &abort_flag;
+
+    if (tid == 0) {
+        for (int q = 0; q < kNBars; ++q) {
+            const bool epi = q == kBarOp || q == kBarB1Free || q == kBarB1Free + 1 || q == kBarStage || q == kBarEPart;
+            mbar_init(bar0 + 8u * q, epi ? (uint32_t)kEpiWarps : 1u);
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (tid < 8) counts[tid] = tid < kNSpecies ? p.ctr->species[tid] : 0;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    const uint32_t tmem = tmem_slot;
+    const bool backward = p.backward != 0;
+
+    ProdState P;
+    MmaState S;
+    for (int q = 0; q < 4; ++q) {
+        P.f1_uses[q] = P.f1_freed[q] = P.r_uses[q] = P.r_freed[q] = 0;
+        S.f1_full[q] = S.r_full[q] = 0;
+    }
+    P.f1pos = P.rpos = S.f1pos = S.rpos = 0;
+    P.geom = S.geom = 0xffffffffu;
+
+    if (warp == 0) {
+        if (lane == 0) producer<SPLIT>(M, counts, sbase, bar0, abrt, backward, P);
+    } else if (warp == 1) {
+        if (lane == 0) mma_issuer<SPLIT>(M, counts, sbase, tmem, bar0, abrt, backward, S);
+    } else {
+        EpiCtx X;
+        X.sbase = sbase;
+        X.bar0 = bar0;
+        X.tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        X.abrt = abrt;
+        X.lane = lane;
+        X.part = (warp - 2) >> 2;
+        X.r = (warp & 3) * 32 + lane;
+        X.n_acc[0] = X.n_acc[1] = 0;
+        epilogue<SPLIT>(M, p, counts, X, warp);
+    }
+    __syncwarp();
+
+    // ---- teardown: drain own copies, MMAs and stores (bounded), free tensor memory
+    if (warp == 1 && lane == 0) {
+        for (int q = 0; q < 4; ++q) {
+            consumed[q] = S.f1_full[q];
+            consumed[4 + q] = S.r_full[q];
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane == 0 && abort_flag) {
+        for (int q = 0; q < 4; ++q) {
+            for (uint32_t ph = consumed[q]; ph < P.f1_uses[q]; ++ph)
+                (void)mbar_wait_plain(bar0 + 8u * (kBarF1Full + q), ph & 1u);
+            for (uint32_t ph = consumed[4 + q]; ph < P.r_uses[q]; ++ph)
+                (void)mbar_wait_plain(bar0 + 8u * (kBarRFull + q), ph & 1u);
+        }
+    }
+    if (warp == 1 && lane == 0) {
+        mma_commit(bar0 + 8u * kBarDrain);
+        (void)mbar_wait_plain(bar0 + 8u * kBarDrain, 0u);
+    }
+    if (warp >= 2 && lane == 0) bulk_wait0();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && abort_flag) {
+        // 1 | warp << 4 | barrier index << 12 for a timed-out wait
+        const uint32_t a = (uint32_t)abort_flag;
+        const uint32_t code = (a & 0x40000000u) ? 1u | (((a >> 20) & 0x3fu) << 4) | ((((a & 0xfffffu) - bar0) / 8u) << 12) : 1u;
+        atomicOr(p.err, (int)code);
+    }
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ host side
@@ -710,11 +995,13 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
                      bool backward, int* err_flag) {
     TcMaps M;
     if (!w.maps_ok || !make_map(&M.G, G, kAevLd, (uint64_t)rows_cap, 128) ||
-        (split && (!G_lo || !make_map(&M.Glo, G_lo, kAevLd, (uint64_t)rows_cap, 128)))) {
+        (split && (!G_lo || !make_map(&M.Glo, G_lo, kAevLd, (uint64_t)rows_cap, 128))) ||
+        (backward && (!dG || !make_map(&M.dG, dG, kAevLd, (uint64_t)rows_cap, 32)))) {
         set_error(-5, "TMA tensor map creation failed");
         return false;
     }
     if (!split) M.Glo = M.G;
+    if (!backward) M.dG = M.G;   // not used
     M.W1 = w.tmW1;
     M.W1lo = w.tmW1lo;
     M.W2 = w.tmW2;
@@ -739,7 +1026,7 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
     }
     const int tiles = rows_cap / kTileRows;
     const int grid = tiles < sms ? tiles : sms;
-    TcArgs a{ctr, row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, dG, backward ? 1 : 0, err_flag};
+    TcArgs a{ctr, row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, backward ? 1 : 0, err_flag};
     if (split)
         MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
     else
