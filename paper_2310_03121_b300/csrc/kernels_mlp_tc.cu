@@ -138,10 +138,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait on a phase: false after kWaitNs (and the abort flag is set), or
-// as soon as another role has set the abort flag.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abrt) {
-    if (mbar_try(bar, parity)) return true;
+// as soon as another role has set the abort flag. The completed-phase case is
+// a single inline test; only a real wait takes the out-of-line loop.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int* abrt) {
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
@@ -153,6 +162,9 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
             }
         }
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abrt) {
+    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abrt);
 }
 // Bounded wait used by the teardown drains (no abort check).
 __device__ __noinline__ bool mbar_wait_plain(uint32_t bar, uint32_t parity) {
@@ -269,7 +281,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 __device__ __forceinline__ float celu_f(float x) { return x > 0.f ? x : kCeluAlpha * (__expf(x * (1.f / kCeluAlpha)) - 1.f); }
-__device__ __forceinline__ float dcelu_f(float x) { return x > 0.f ? 1.f : __expf(x * (1.f / kCeluAlpha)); }
 __device__ __forceinline__ float dcelu_h(float h) { return h > 0.f ? 1.f : h * (1.f / kCeluAlpha) + 1.f; }
 
 #ifdef MLP_TC_TRACE
@@ -334,50 +345,55 @@ __device__ __forceinline__ Job make_job(const TcMaps& M, int k, int s) {
 }
 
 // ------------------------------------------------------------------ producer
+// Slot state lives in registers as bit masks over 8 slots: bits 0..3 the F1
+// stages, bits 4..7 the weight ring slots. Barrier of slot b: full
+// b < 4 ? b : b + 4, consumed b < 4 ? b + 4 : b + 8.
+__device__ __forceinline__ uint32_t full_bar(uint32_t bar0, int b) { return bar0 + 8u * (uint32_t)(b < 4 ? b : b + 4); }
+__device__ __forceinline__ uint32_t empty_bar(uint32_t bar0, int b) { return bar0 + 8u * (uint32_t)(b < 4 ? b + 4 : b + 8); }
+
 struct ProdState {
-    uint32_t f1_uses[4], f1_freed[4];   // F1 stage loads issued / consumptions observed
-    uint32_t r_uses[4], r_freed[4];     // weight ring slots
+    uint32_t pend;   // slots whose last load has not been seen consumed
+    uint32_t epar;   // parity of the next consumed phase to wait for, per slot
+    uint32_t lpar;   // parity of the number of loads issued, per slot
     uint32_t f1pos, rpos, geom;
 };
 
-__device__ __forceinline__ bool prod_free(uint32_t empty_bar, uint32_t& freed, uint32_t uses, volatile int* abrt) {
-    while (freed < uses) {
-        if (!mbar_wait(empty_bar, freed & 1u, abrt)) return false;
-        ++freed;
+// Wait until slot b may be overwritten (its last load consumed by the MMAs).
+__device__ __forceinline__ bool prod_free(ProdState& P, uint32_t bar0, int b, volatile int* abrt) {
+    const uint32_t m = 1u << b;
+    if (P.pend & m) {
+        if (!mbar_wait(empty_bar(bar0, b), (P.epar >> b) & 1u, abrt)) return false;
+        P.epar ^= m;
+        P.pend &= ~m;
     }
     return true;
 }
-
-__device__ bool prod_drain_ring(ProdState& P, uint32_t bar0, volatile int* abrt) {
-    for (int si = 0; si < 4; ++si)
-        if (!prod_free(bar0 + 8u * (kBarREmpty + si), P.r_freed[si], P.r_uses[si], abrt)) return false;
-    return true;
-}
-__device__ bool prod_drain_f1(ProdState& P, uint32_t bar0, volatile int* abrt) {
-    for (int st = 0; st < 4; ++st)
-        if (!prod_free(bar0 + 8u * (kBarF1Empty + st), P.f1_freed[st], P.f1_uses[st], abrt)) return false;
+__device__ __forceinline__ bool prod_drain(ProdState& P, uint32_t bar0, uint32_t mask, volatile int* abrt) {
+    for (int b = 0; b < 8; ++b)
+        if ((mask >> b) & 1u)
+            if (!prod_free(P, bar0, b, abrt)) return false;
     return true;
 }
 
-__device__ __noinline__ bool prod_job(ProdState& P, const Job& Jref, uint32_t sbase, uint32_t bar0,
-                                      volatile int* abrt) {
-    const Job J = Jref;
-    const uint64_t keep = policy_evict_last();
+__device__ __forceinline__ bool prod_job(ProdState& P, const Job& J, uint32_t sbase, uint32_t bar0, volatile int* abrt,
+                                         uint64_t keep) {
     if (J.geom() != P.geom) {   // new slot layout: every slot of the old one must be consumed
-        if (!prod_drain_ring(P, bar0, abrt)) return false;
+        if (!prod_drain(P, bar0, 0xf0u, abrt)) return false;
         P.geom = J.geom();
         P.rpos = 0;
     }
     const int nq = J.nq();
     for (int q = 0; q < nq; ++q) {
-        const int si = (int)(P.rpos++ % (uint32_t)J.slots);
-        if (!prod_free(bar0 + 8u * (kBarREmpty + si), P.r_freed[si], P.r_uses[si], abrt)) return false;
+        const int si = (int)P.rpos;
+        P.rpos = (P.rpos + 1u == (uint32_t)J.slots) ? 0u : P.rpos + 1u;
+        if (!prod_free(P, bar0, 4 + si, abrt)) return false;
         const int c = J.split ? (q >> 1) : q;
         const CUtensorMap* m = (J.split && (q & 1)) ? J.map_lo : J.map;
-        const uint32_t full = bar0 + 8u * (kBarRFull + si);
+        const uint32_t full = full_bar(bar0, 4 + si);
         mbar_expect_tx(full, (uint32_t)J.N * 128u);
         tma_load_2d_hint(sbase + J.ring_off + (uint32_t)si * J.slot_bytes, m, c * 64, J.brow, full, keep);
-        P.r_uses[si]++;
+        P.pend |= 1u << (4 + si);
+        P.lpar ^= 1u << (4 + si);
     }
     return true;
 }
@@ -398,6 +414,7 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
                                    &M.W1t, &M.dG};
     for (int q = 0; q < 12; ++q) prefetch_map(maps[q]);
     const uint64_t keep = policy_evict_last();
+    auto job = [&](int k, int s) -> bool { return prod_job(P, make_job<SPLIT>(M, k, s), sbase, bar0, abrt, keep); };
     int tile_no = 0;
     for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
         int s, row0, nvalid;
@@ -405,11 +422,12 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
         if (tile_no == 0) prefetch_g(M, row0, SPLIT);
         // F1 stages cover every region: the previous tile's epilogues and MMAs must be done with them
         if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
-        if (!prod_drain_ring(P, bar0, abrt)) break;
+        if (!prod_drain(P, bar0, 0xf0u, abrt)) break;
         bool ok = true;
         for (int c = 0; c < kAevLd / 64 && ok; ++c) {
-            const int st = (int)(P.f1pos++ % (uint32_t)nst);
-            if (!prod_free(bar0 + 8u * (kBarF1Empty + st), P.f1_freed[st], P.f1_uses[st], abrt)) {
+            const int st = (int)P.f1pos;
+            P.f1pos = (P.f1pos + 1u) & (uint32_t)(nst - 1);
+            if (!prod_free(P, bar0, st, abrt)) {
                 ok = false;
                 break;
             }
@@ -423,81 +441,76 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
             } else {
                 tma_load_2d_hint(dst + 16384u, &M.W1, c * 64, s * kH1, full, keep);
             }
-            P.f1_uses[st]++;
+            P.pend |= 1u << st;
+            P.lpar ^= 1u << st;
             if (c == 0) MLP_TC_MARK(27);
         }
         if (!ok) break;
         MLP_TC_MARK(28);
         // the F2 ring overlays the F1 stages
-        if (!prod_drain_f1(P, bar0, abrt)) break;
-        if (!prod_job(P, make_job<SPLIT>(M, kJobF2, s), sbase, bar0, abrt)) break;
+        if (!prod_drain(P, bar0, 0x0fu, abrt)) break;
+        if (!job(kJobF2, s)) break;
         MLP_TC_MARK(29);
-        if (!prod_job(P, make_job<SPLIT>(M, kJobF3, s), sbase, bar0, abrt)) break;
+        if (!job(kJobF3, s)) break;
         int sn, rown, nvn;
         const bool has_next = tile_info(counts, t + (int)gridDim.x, sn, rown, nvn);
         if (!backward) {
             if (has_next) prefetch_g(M, rown, SPLIT);
             continue;
         }
-        if (!prod_job(P, make_job<SPLIT>(M, kJobB3, s), sbase, bar0, abrt)) break;
+        if (!job(kJobB3, s) || !job(kJobB2, s) || !job(kJobB1 + 0, s) || !job(kJobB1 + 1, s) ||
+            !job(kJobB1 + 2, s) || !job(kJobB1 + 3, s))
+            break;
+        // the next tile's G: requested after this tile's last weight load, so
+        // that the weight loads never queue behind it
         if (has_next) prefetch_g(M, rown, SPLIT);
-        if (!prod_job(P, make_job<SPLIT>(M, kJobB2, s), sbase, bar0, abrt)) break;
-        for (int j = 0; j < 4 && ok; ++j) ok = prod_job(P, make_job<SPLIT>(M, kJobB1 + j, s), sbase, bar0, abrt);
-        if (!ok) break;
         MLP_TC_MARK(30);
     }
 }
 
 // ------------------------------------------------------------------ MMA issuer
 struct MmaState {
-    uint32_t f1_full[4], r_full[4];   // loads consumed per F1 stage / ring slot
+    uint32_t fpar;   // parity of the number of loads consumed, per slot (bits as in ProdState)
     uint32_t f1pos, rpos, geom;
 };
 
-// The job and the ring position are copied into registers first: the MMA
-// asm statements clobber memory, so fields read through references would be
-// reloaded from local memory before every MMA.
-__device__ __noinline__ bool mma_job(MmaState& S, const Job& Jref, uint32_t sbase, uint32_t tmem, uint32_t bar0,
-                                     volatile int* abrt) {
-    const Job J = Jref;
+__device__ __forceinline__ bool mma_job(MmaState& S, const Job& J, uint32_t sbase, uint32_t tmem, uint32_t bar0,
+                                        volatile int* abrt) {
     const uint32_t geom = J.geom();
-    uint32_t rpos = S.geom == geom ? S.rpos : 0u;
-    S.geom = geom;
+    if (S.geom != geom) {
+        S.geom = geom;
+        S.rpos = 0;
+    }
     const uint32_t idesc = idesc_bf16(128, J.N);
     const uint32_t d = tmem + J.d_col;
-    const int nq = J.nq(), nc = J.nc, lastk = J.lastk, slots = J.slots;
-    const bool split = J.split != 0;
-    const uint32_t ring = sbase + J.ring_off, slot_bytes = J.slot_bytes;
-    const uint32_t a0 = sbase + J.a_off, a0lo = sbase + J.a_lo_off;
-    bool ok = true;
+    const int nq = J.nq();
     for (int q = 0; q < nq; ++q) {
-        const int si = (int)(rpos++ % (uint32_t)slots);
-        const uint32_t nf = S.r_full[si];
-        if (!mbar_wait(bar0 + 8u * (kBarRFull + si), nf & 1u, abrt)) {
-            ok = false;
-            break;
-        }
-        S.r_full[si] = nf + 1u;
+        const int si = (int)S.rpos;
+        S.rpos = (S.rpos + 1u == (uint32_t)J.slots) ? 0u : S.rpos + 1u;
+        if (!mbar_wait(full_bar(bar0, 4 + si), (S.fpar >> (4 + si)) & 1u, abrt)) return false;
+        S.fpar ^= 1u << (4 + si);
         tc_fence_after();
-        const int c = split ? (q >> 1) : q;
-        const bool lo_b = split && (q & 1);
-        const uint32_t b_base = ring + (uint32_t)si * slot_bytes;
-        const uint32_t a_hi = a0 + (uint32_t)c * kAtom;
-        const uint32_t a_lo = a0lo + (uint32_t)c * kAtom;
-        const int ks = (c == nc - 1) ? lastk : 4;
-        for (int k = 0; k < ks; ++k) {
-            const uint64_t b = sdesc(b_base + 32u * k);
-            if (lo_b) {
-                mma_bf16(d, sdesc(a_hi + 32u * k), b, idesc, 1u);
-            } else {
-                mma_bf16(d, sdesc(a_hi + 32u * k), b, idesc, (q == 0 && k == 0) ? 0u : 1u);
-                if (split) mma_bf16(d, sdesc(a_lo + 32u * k), b, idesc, 1u);
+        const int c = J.split ? (q >> 1) : q;
+        const bool lo_b = J.split && (q & 1);
+        const int ks = (c == J.nc - 1) ? J.lastk : 4;
+        // one 16-wide K step advances a K-major SW128 descriptor by 32 bytes (2 in the address field)
+        const uint64_t bd = sdesc(sbase + J.ring_off + (uint32_t)si * J.slot_bytes);
+        const uint64_t ad = sdesc(sbase + J.a_off + (uint32_t)c * kAtom);
+        const uint64_t ald = sdesc(sbase + J.a_lo_off + (uint32_t)c * kAtom);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < ks) {
+                if (lo_b) {
+                    mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, 1u);
+                } else {
+                    mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (q == 0 && k == 0) ? 0u : 1u);
+                    if (J.split) mma_bf16(d, ald + 2u * k, bd + 2u * k, idesc, 1u);
+                }
             }
         }
-        mma_commit(bar0 + 8u * (kBarREmpty + si));
+        mma_commit(empty_bar(bar0, 4 + si));
     }
-    S.rpos = rpos;
-    return ok;
+    return true;
 }
 
 template <bool SPLIT>
@@ -533,27 +546,29 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
         MLP_TC_MARK(20);
         bool ok = true;
         for (int c = 0; c < kAevLd / 64; ++c) {
-            const int st = (int)(S.f1pos++ % (uint32_t)nst);
-            if (!mbar_wait(bar0 + 8u * (kBarF1Full + st), S.f1_full[st] & 1u, abrt)) {
+            const int st = (int)S.f1pos;
+            S.f1pos = (S.f1pos + 1u) & (uint32_t)(nst - 1);
+            if (!mbar_wait(full_bar(bar0, st), (S.fpar >> st) & 1u, abrt)) {
                 ok = false;
                 break;
             }
-            S.f1_full[st]++;
+            S.fpar ^= 1u << st;
             tc_fence_after();
             const uint32_t base = sbase + (uint32_t)st * stage;
+            const uint64_t ah = sdesc(base), al = sdesc(base + 16384u);
+            const uint64_t bh = sdesc(base + (SPLIT ? 32768u : 16384u)), bl = sdesc(base + 65536u);
+#pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
                 if (SPLIT) {
-                    const uint64_t ah = sdesc(base + 32u * k), al = sdesc(base + 16384u + 32u * k);
-                    const uint64_t bh = sdesc(base + 32768u + 32u * k), bl = sdesc(base + 65536u + 32u * k);
-                    mma_bf16(tmem, ah, bh, idesc1, acc);
-                    mma_bf16(tmem, al, bh, idesc1, 1u);
-                    mma_bf16(tmem, ah, bl, idesc1, 1u);
+                    mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
+                    mma_bf16(tmem, al + 2u * k, bh + 2u * k, idesc1, 1u);
+                    mma_bf16(tmem, ah + 2u * k, bl + 2u * k, idesc1, 1u);
                 } else {
-                    mma_bf16(tmem, sdesc(base + 32u * k), sdesc(base + 16384u + 32u * k), idesc1, acc);
+                    mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
                 }
             }
-            mma_commit(bar0 + 8u * (kBarF1Empty + st));
+            mma_commit(empty_bar(bar0, st));
         }
         if (!ok) break;
         mma_commit(bar0 + 8u * kBarAcc);
@@ -713,12 +728,15 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 uint32_t pk[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
+                    // one exponential per element: exp(min(z, 0) / alpha) gives celu and celu'
                     const float z0 = __uint_as_float(d[2 * q]) + __ldg(b3 + c0 + 2 * q);
                     const float z1 = __uint_as_float(d[2 * q + 1]) + __ldg(b3 + c0 + 2 * q + 1);
                     const float w0 = __ldg(w4 + c0 + 2 * q), w1 = __ldg(w4 + c0 + 2 * q + 1);
-                    es = fmaf(w0, celu_f(z0), es);
-                    es = fmaf(w1, celu_f(z1), es);
-                    pk[q] = pack_bf16(w0 * dcelu_f(z0), w1 * dcelu_f(z1));
+                    const float x0 = __expf(fminf(z0, 0.f) * (1.f / kCeluAlpha));
+                    const float x1 = __expf(fminf(z1, 0.f) * (1.f / kCeluAlpha));
+                    es = fmaf(w0, z0 > 0.f ? z0 : kCeluAlpha * (x0 - 1.f), es);
+                    es = fmaf(w1, z1 > 0.f ? z1 : kCeluAlpha * (x1 - 1.f), es);
+                    pk[q] = pack_bf16(z0 > 0.f ? w0 : w0 * x0, z1 > 0.f ? w1 : w1 * x1);
                 }
                 if (p.backward) {
                     st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
@@ -842,7 +860,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     __shared__ int counts[8];
-    __shared__ uint32_t consumed[8];   // teardown: loads consumed per F1 stage (0..3) and ring slot (4..7)
+    __shared__ uint32_t consumed_par;   // teardown: the MMA issuer's consumed-load parities
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -871,10 +889,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
 
     ProdState P;
     MmaState S;
-    for (int q = 0; q < 4; ++q) {
-        P.f1_uses[q] = P.f1_freed[q] = P.r_uses[q] = P.r_freed[q] = 0;
-        S.f1_full[q] = S.r_full[q] = 0;
-    }
+    P.pend = P.epar = P.lpar = 0;
+    S.fpar = 0;
     P.f1pos = P.rpos = S.f1pos = S.rpos = 0;
     P.geom = S.geom = 0xffffffffu;
 
@@ -897,20 +913,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     __syncwarp();
 
     // ---- teardown: drain own copies, MMAs and stores (bounded), free tensor memory
-    if (warp == 1 && lane == 0) {
-        for (int q = 0; q < 4; ++q) {
-            consumed[q] = S.f1_full[q];
-            consumed[4 + q] = S.r_full[q];
-        }
-    }
+    if (warp == 1 && lane == 0) consumed_par = S.fpar;
     __syncthreads();
     if (warp == 0 && lane == 0 && abort_flag) {
-        for (int q = 0; q < 4; ++q) {
-            for (uint32_t ph = consumed[q]; ph < P.f1_uses[q]; ++ph)
-                (void)mbar_wait_plain(bar0 + 8u * (kBarF1Full + q), ph & 1u);
-            for (uint32_t ph = consumed[4 + q]; ph < P.r_uses[q]; ++ph)
-                (void)mbar_wait_plain(bar0 + 8u * (kBarRFull + q), ph & 1u);
-        }
+        // at most one load per slot is ahead of the MMAs: the one whose count parity differs
+        const uint32_t out = P.lpar ^ consumed_par;
+        for (int b = 0; b < 8; ++b)
+            if ((out >> b) & 1u) (void)mbar_wait_plain(full_bar(bar0, b), (consumed_par >> b) & 1u);
     }
     if (warp == 1 && lane == 0) {
         mma_commit(bar0 + 8u * kBarDrain);
