@@ -151,10 +151,14 @@ __device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* ro
 }
 
 // Appends this chunk's angular neighbors to the stage; returns the new count.
+// pA_out: this lane's slot in the stage (or -1: not an angular neighbor or
+// past the staging limit).
 template <bool FAST>
-__device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage& s, const AevArgs& a) {
+__device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage& s, const AevArgs& a,
+                                             int* pA_out = nullptr) {
     const unsigned bA = __ballot_sync(kFull, nl.inA);
     const int pA = mA + __popc(bA & lanemask_lt());
+    if (pA_out) *pA_out = (nl.inA && pA < kMaxAng) ? pA : -1;
     if (nl.inA && pA < kMaxAng) {
         const float ir = M<FAST>::rcp(nl.r);
         s.u[pA] = make_float4(nl.d.x * ir, nl.d.y * ir, nl.d.z * ir, nl.r);
@@ -169,14 +173,40 @@ __device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage
     return m;
 }
 
-// Next unordered pair (j < k) `step` positions further in row-major order.
-__device__ __forceinline__ void advance_pair(int& j, int& k, int step, int m) {
-    k += step;
-    while (k >= m && j < m) {
-        k = k - m + j + 2;
-        ++j;
+// Unordered pairs of the m angular neighbors, enumerated by rotation: for
+// t = 1 .. (m - 1) / 2 the m pairs (j, (j + t) mod m), j = 0 .. m - 1, then
+// for even m the m / 2 pairs (j, j + m / 2). Each pair appears once; pairs
+// of consecutive positions have distinct j and distinct k as long as they
+// span less than one rotation, so one pair per lane gives (nearly)
+// conflict-free shared-memory traffic on both atoms of the pair.
+struct PairIt {
+    int j, t, m, tfull;
+    __device__ __forceinline__ void init(int m_, int start) {
+        m = m_;
+        tfull = (m - 1) / 2;
+        j = start;
+        t = 1;
+        norm();
     }
-}
+    __device__ __forceinline__ void norm() {
+        while (t <= tfull && j >= m) {
+            j -= m;
+            ++t;
+        }
+    }
+    __device__ __forceinline__ void advance(int step) {
+        j += step;
+        norm();
+    }
+    __device__ __forceinline__ bool valid() const {
+        return m > 1 && (t <= tfull || (t == tfull + 1 && (m & 1) == 0 && j < (m >> 1)));
+    }
+    __device__ __forceinline__ int k() const {
+        if (t > tfull) return j + (m >> 1);
+        const int x = j + t;
+        return x >= m ? x - m : x;
+    }
+};
 
 __device__ __forceinline__ float row_value(const float* acc, int c) {
     return c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
@@ -246,11 +276,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
         float* rf = pf + 32 * 8;         // [32][4]
         int* pp = reinterpret_cast<int*>(rf + 32 * 4);
         const int P = mA * (mA - 1) / 2;
-        int j = 0, kk = 1 + lane;
-        advance_pair(j, kk, 0, mA);
+        PairIt it;
+        it.init(mA, lane);
         for (int base = 0; base < P; base += 32) {
             const int nv = min(32, P - base);
             if (lane < nv) {
+                const int j = it.j, kk = it.k();
                 const float4 uj = s.u[j], uk = s.u[kk];
                 const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
                 const float sn = M<FAST>::sq(1.f - c * c);
@@ -272,7 +303,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
             const int z = lane & 7, aa = lane >> 3;
             for (int q = 0; q < nv; ++q) accA[pp[q] + lane] += pf[q * 8 + z] * rf[q * 4 + aa];
             __syncwarp();
-            advance_pair(j, kk, 32, mA);
+            it.advance(32);
         }
     }
     __syncwarp();
@@ -330,8 +361,21 @@ __device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, 
     return 0.25f * s;
 }
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+// 8 consecutive dE/dG values (16-byte aligned) as floats
+__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[2 * q] = __uint_as_float(w[q] << 16);
+        v[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+    }
+}
 
 template <bool FAST, typename TG>
 __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
@@ -347,13 +391,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
     const int si = species_of(hi_i);
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
     const TG* grow = dG + (size_t)rw * kAevLd;
-    for (int c = lane; c < kAevLen; c += 32) {
-        int dst = c;
-        if (c >= kRadLen) {
-            const int rel = c - kRadLen;
-            dst = kRadLen + kGsAngStride * (rel >> 5) + (rel & 31);
-        }
-        gs[dst] = to_f(grow[c]);
+    // 8 columns per lane and load (16 B of BF16 or 32 B of FP32); the 8 stay
+    // inside one radial block or one 32-column angular row
+    for (int c = 8 * lane; c < kAevLen; c += 256) {
+        float v[8];
+        load8(grow + c, v);
+        const int dst = c < kRadLen ? c : kRadLen + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) gs[dst + q] = v[q];
     }
     for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
     __syncwarp();
@@ -362,34 +407,45 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
     const int cnt = min(a.nbr_cnt[i], a.cap);
     const int* row = a.nbr + (size_t)i * a.cap;
     int mA = 0;
-    // radial: one neighbor per lane, gradient straight to the FP64 sums
+    // radial: one neighbor per lane. The gradient on an angular neighbor goes
+    // to its (still private) shared-memory slot, which the angular terms add
+    // to and which is flushed once; other neighbors go straight to the FP64 sums.
     for (int base = 0; base < cnt; base += 32) {
         const NbrLane nl = load_neighbor(a, row, base + lane, cnt, hi_i, lo_i);
+        int pA;
+        mA = stage_angular<FAST>(nl, mA, s, a, &pA);
         if (nl.inR) {
             const float x = nl.r * (1.f / kRcRad);
             const float fc = 0.5f * M<FAST>::cpi(x) + 0.5f;
             const float dfc = -0.5f * (3.14159265358979f / kRcRad) * M<FAST>::spi(x);
             const float sc = radial_dEdr<FAST>(gs + nl.sp * kRadShifts, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
             const float gx = sc * nl.d.x, gy = sc * nl.d.y, gz = sc * nl.d.z;
-            atomicAdd(&grad[3 * (size_t)nl.j], (double)gx);
-            atomicAdd(&grad[3 * (size_t)nl.j + 1], (double)gy);
-            atomicAdd(&grad[3 * (size_t)nl.j + 2], (double)gz);
+            if (pA >= 0) {
+                fslot[3 * pA] = gx;
+                fslot[3 * pA + 1] = gy;
+                fslot[3 * pA + 2] = gz;
+            } else {
+                atomicAdd(&grad[3 * (size_t)nl.j], (double)gx);
+                atomicAdd(&grad[3 * (size_t)nl.j + 1], (double)gy);
+                atomicAdd(&grad[3 * (size_t)nl.j + 2], (double)gz);
+            }
             fix -= gx;
             fiy -= gy;
             fiz -= gz;
         }
-        mA = stage_angular<FAST>(nl, mA, s, a);
     }
+    const int mS = min(mA, kMaxAng);   // staged slots (flushed even on overflow)
     if (mA > kMaxAng) mA = 0;
     __syncwarp();
 
     // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers
     {
         const int P = mA * (mA - 1) / 2;
-        int j = 0, kk = 1 + lane;
-        advance_pair(j, kk, 0, mA);
+        PairIt it;
+        it.init(mA, lane);
         for (int base = 0; base < P; base += 32) {
             if (base + lane < P) {
+                const int j = it.j, kk = it.k();
                 const float4 uj = s.u[j], uk = s.u[kk];
                 const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
                 const float c = 0.95f * cos0;
@@ -447,7 +503,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
                 fiy -= gjy + gky;
                 fiz -= gjz + gkz;
             }
-            advance_pair(j, kk, 32, mA);
+            it.advance(32);
         }
     }
     __syncwarp();
@@ -462,7 +518,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
         atomicAdd(&grad[3 * (size_t)i + 1], (double)fiy);
         atomicAdd(&grad[3 * (size_t)i + 2], (double)fiz);
     }
-    for (int q = lane; q < mA; q += 32) {
+    for (int q = lane; q < mS; q += 32) {
         const int jj = s.idx[q];
         atomicAdd(&grad[3 * (size_t)jj], (double)fslot[3 * q]);
         atomicAdd(&grad[3 * (size_t)jj + 1], (double)fslot[3 * q + 1]);
