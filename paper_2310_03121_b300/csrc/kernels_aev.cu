@@ -105,16 +105,30 @@ struct AngStage {
     int idx[kMaxAng];      // atom index
 };
 
-constexpr int kAccFloats = 2 * kRadLen + kAngLen;   // two radial halves + angular
-// per-pair factors of 32 pairs: P_z f [32][8], R_a [32][4], element pair [32]
-constexpr int kPairBufFloats = 32 * 8 + 32 * 4 + 32;
-constexpr size_t kAevSmemPerWarp = sizeof(AngStage) + (kAccFloats + kPairBufFloats) * sizeof(float);
+// Forward scratch of one warp (after its angular stage).
+struct AevScratch {
+    float accR[2 * kRadLen];    // radial accumulators, two halves of 16 shift lanes
+    // per pair (one per lane): 2 fc fc P_z for the 8 sections and the 4
+    // distance Gaussians; rows of 9 and 5 floats so that both the writing
+    // lanes (one row each) and the reading lanes (one row, 8 or 4 columns)
+    // hit distinct banks
+    float pf[32 * 9];
+    float rf[32 * 5];
+    int ord[64];                // sorted (by element) position -> stage slot
+    int off[kNPairs + 1];       // first pair of each element pair in pair order
+    int pdesc[kNPairs];         // element groups of the pair: g1 | c1 << 8 | g2 << 16 | c2 << 24
+};
+// per-warp regions start on 16-byte boundaries (the stage holds float4)
+constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+constexpr size_t kAevSmemPerWarp = round16(sizeof(AngStage) + sizeof(AevScratch));
+static_assert(sizeof(AngStage) % 16 == 0, "AngStage must keep the per-warp regions 16-byte aligned");
 // dE/dG staged with the angular block in rows of 33 floats (one per element
 // pair) so that lanes reading the same column of different rows hit
 // different banks
 constexpr int kGsAngStride = 33;
 constexpr int kGsFloats = kRadLen + kNPairs * kGsAngStride;
-constexpr size_t kForceSmemPerWarp = sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float);
+constexpr size_t kForceSmemPerWarp = round16(sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float));
+static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-warp shared regions must be 16-byte aligned");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -198,9 +212,6 @@ struct PairIt {
         j += step;
         norm();
     }
-    __device__ __forceinline__ bool valid() const {
-        return m > 1 && (t <= tfull || (t == tfull + 1 && (m & 1) == 0 && j < (m >> 1)));
-    }
     __device__ __forceinline__ int k() const {
         if (t > tfull) return j + (m >> 1);
         const int x = j + t;
@@ -208,23 +219,14 @@ struct PairIt {
     }
 };
 
-__device__ __forceinline__ float row_value(const float* acc, int c) {
-    return c < kRadLen ? acc[c] + acc[kRadLen + c] : (c < kAevLen ? acc[kRadLen + c] : 0.f);
-}
-
-// BF16 row; with out_lo != nullptr also the BF16 rounding of the remainder
-// (G = G_hi + G_lo to ~16 bits), for the split-precision network.
-__device__ __forceinline__ void store_row_bf16(__nv_bfloat16* out, __nv_bfloat16* out_lo, const float* acc,
-                                               int lane) {
-    for (int c = 2 * lane; c < kAevLd; c += 64) {
-        const float v0 = row_value(acc, c), v1 = row_value(acc, c + 1);
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        *reinterpret_cast<__nv_bfloat162*>(out + c) = h;
-        if (out_lo) {
-            const float2 f = __bfloat1622float2(h);
-            *reinterpret_cast<__nv_bfloat162*>(out_lo + c) = __floats2bfloat162_rn(v0 - f.x, v1 - f.y);
-        }
-    }
+// One AEV value into the output row: FP32, or BF16 and (with out_lo) the
+// BF16 rounding of the remainder (G = G_hi + G_lo to ~16 bits) for the
+// split-precision network.
+__device__ __forceinline__ void put_g(float* out, float*, int c, float v) { out[c] = v; }
+__device__ __forceinline__ void put_g(__nv_bfloat16* out, __nv_bfloat16* out_lo, int c, float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    out[c] = h;
+    if (out_lo) out_lo[c] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
 template <bool FAST, typename OutT>
@@ -235,16 +237,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     const int i = blockIdx.x * kWarps + w;
     if (i >= a.n) return;
     AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kAevSmemPerWarp);
-    float* acc = reinterpret_cast<float*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
+    AevScratch& X = *reinterpret_cast<AevScratch*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
-    for (int c = lane; c < kAccFloats; c += 32) acc[c] = 0.f;
+    for (int c = lane; c < 2 * kRadLen; c += 32) X.accR[c] = 0.f;
     __syncwarp();
 
     const int cnt = min(a.nbr_cnt[i], a.cap);
     const int* row = a.nbr + (size_t)i * a.cap;
     const int k = lane & 15, h = lane >> 4;
     const float Rk = c_aev.shf_r[k];
-    float* accR = acc + h * kRadLen;
+    float* accR = X.accR + h * kRadLen;
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
     for (int base = 0; base < cnt; base += 32) {
@@ -265,57 +267,137 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     }
     if (mA > kMaxAng) mA = 0;   // reported as an error by the host; keep every index in range
     __syncwarp();
+    const int si = species_of(hi_i);
+    const int rw = row_base(a.ctr->species, si) + a.rank[i];
+    OutT* out = G + (size_t)rw * kAevLd;
+    OutT* out_lo = G_lo ? G_lo + (size_t)rw * kAevLd : nullptr;
 
-    // angular: 32 pairs at a time. First one pair per lane: its 8 angle
-    // factors (times the cutoff product) and 4 distance factors go to shared
-    // memory; then lane (a, z) adds factor products to its own column of the
-    // pair's element-pair block, pairs in list order (deterministic).
+    // ---- angular. The sub-list is ordered by element (ord), and the pairs
+    // are enumerated element pair by element pair (p = 0 .. 27), so that a
+    // lane (a, z) sums its column of one 32-column block in a register over
+    // a run of pairs and writes the finished block once; no accumulator
+    // array, fixed order (deterministic).
+    const int sp0 = lane < mA ? s.sp[lane] : -1, sp1 = lane + 32 < mA ? s.sp[lane + 32] : -1;
+    int cnt_e = 0, g_e = 0;   // lane e < 7: size and first sorted position of element e's group
     {
-        float* accA = acc + 2 * kRadLen;
-        float* pf = acc + kAccFloats;    // [32][8]
-        float* rf = pf + 32 * 8;         // [32][4]
-        int* pp = reinterpret_cast<int*>(rf + 32 * 4);
-        const int P = mA * (mA - 1) / 2;
-        PairIt it;
-        it.init(mA, lane);
+        const unsigned lt = lanemask_lt();
+        int base = 0;
+        for (int e = 0; e < kNSpecies; ++e) {
+            const unsigned b0 = __ballot_sync(kFull, sp0 == e), b1 = __ballot_sync(kFull, sp1 == e);
+            const int c0 = __popc(b0), c = c0 + __popc(b1);
+            if (sp0 == e) X.ord[base + __popc(b0 & lt)] = lane;
+            if (sp1 == e) X.ord[base + c0 + __popc(b1 & lt)] = lane + 32;
+            if (lane == e) {
+                cnt_e = c;
+                g_e = base;
+            }
+            base += c;
+        }
+    }
+    {
+        // lane p < 28: element pair (s1 <= s2) in pair_index order, its pair count and first pair
+        int s1 = 0, s2 = 0, l = lane;
+        for (int e = 0; e < kNSpecies; ++e) {
+            const int len = kNSpecies - e;
+            if (l >= 0 && l < len) {
+                s1 = e;
+                s2 = e + l;
+            }
+            l -= len;
+        }
+        const int c1 = __shfl_sync(kFull, cnt_e, s1), c2 = __shfl_sync(kFull, cnt_e, s2);
+        const int g1 = __shfl_sync(kFull, g_e, s1), g2 = __shfl_sync(kFull, g_e, s2);
+        const int n = lane < kNPairs ? (s1 < s2 ? c1 * c2 : c1 * (c1 - 1) / 2) : 0;
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < kNPairs) {
+            X.off[lane] = incl - n;
+            X.pdesc[lane] = g1 | (c1 << 8) | (g2 << 16) | (c2 << 24);
+        }
+        if (lane == kNPairs - 1) X.off[kNPairs] = incl;
+    }
+    __syncwarp();
+    {
+        const int P = X.off[kNPairs];
+        const int z = lane & 7, aa = lane >> 3;
+        float acc = 0.f;
+        int cur_p = -1, next_p = 0, p = 0;
+        auto flush = [&]() {
+            if (cur_p < 0) return;
+            for (; next_p < cur_p; ++next_p) put_g(out, out_lo, kRadLen + 32 * next_p + lane, 0.f);
+            put_g(out, out_lo, kRadLen + 32 * cur_p + lane, acc);
+            next_p = cur_p + 1;
+        };
         for (int base = 0; base < P; base += 32) {
+            const int e = base + lane;
             const int nv = min(32, P - base);
-            if (lane < nv) {
-                const int j = it.j, kk = it.k();
-                const float4 uj = s.u[j], uk = s.u[kk];
+            int myp = kNPairs;
+            if (e < P) {
+                while (e >= X.off[p + 1]) ++p;
+                myp = p;
+                const int l = e - X.off[p];
+                const int dsc = X.pdesc[p];
+                const int g1 = dsc & 255, c1 = (dsc >> 8) & 255, g2 = (dsc >> 16) & 255, c2 = (dsc >> 24) & 255;
+                int jj, kk;
+                if (g1 != g2) {   // two groups: l = ja * c2 + kb
+                    int ja = (int)(((float)l + 0.5f) / (float)c2);
+                    if (ja * c2 > l) --ja;
+                    if ((ja + 1) * c2 <= l) ++ja;
+                    jj = g1 + ja;
+                    kk = g2 + (l - ja * c2);
+                } else {          // one group of c1: row-major pairs (ja < kb), row ja starts at ja (2 c1 - ja - 1) / 2
+                    const int t = 2 * c1 - 1;
+                    int ja = (int)(0.5f * ((float)t - sqrtf((float)(t * t - 8 * l))));
+                    ja = max(0, min(ja, c1 - 2));
+                    while (ja > 0 && ja * (t - ja) / 2 > l) --ja;
+                    while ((ja + 1) * (t - ja - 1) / 2 <= l) ++ja;
+                    jj = g1 + ja;
+                    kk = g1 + (l - ja * (t - ja) / 2) + ja + 1;
+                }
+                const int J = X.ord[jj], K = X.ord[kk];
+                const float4 uj = s.u[J], uk = s.u[K];
                 const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
                 const float sn = M<FAST>::sq(1.f - c * c);
-                const float f2 = 2.f * s.fc[j] * s.fc[kk];
+                const float f2 = 2.f * s.fc[J] * s.fc[K];
 #pragma unroll
-                for (int z = 0; z < kAngZ; ++z) {
-                    const float b = 0.5f + 0.5f * (c * c_aev.cos_z[z] + sn * c_aev.sin_z[z]);
-                    pf[lane * 8 + z] = f2 * M<FAST>::pw(b, kZeta);
+                for (int zz = 0; zz < kAngZ; ++zz) {
+                    const float b = 0.5f + 0.5f * (c * c_aev.cos_z[zz] + sn * c_aev.sin_z[zz]);
+                    X.pf[lane * 9 + zz] = f2 * M<FAST>::pw(b, kZeta);
                 }
                 const float rbar = 0.5f * (uj.w + uk.w);
 #pragma unroll
-                for (int aa = 0; aa < kAngA; ++aa) {
-                    const float dr = rbar - c_aev.shf_a[aa];
-                    rf[lane * 4 + aa] = M<FAST>::ex(-kEtaAng * dr * dr);
+                for (int q = 0; q < kAngA; ++q) {
+                    const float dr = rbar - c_aev.shf_a[q];
+                    X.rf[lane * 5 + q] = M<FAST>::ex(-kEtaAng * dr * dr);
                 }
-                pp[lane] = 32 * pair_index(s.sp[j], s.sp[kk]);
+            }
+            const int prevp = __shfl_up_sync(kFull, myp, 1);
+            unsigned heads = __ballot_sync(kFull, e < P && (lane == 0 || prevp != myp));
+            __syncwarp();
+            while (heads) {   // runs of one element pair inside these 32 pairs
+                const int q0 = __ffs(heads) - 1;
+                heads &= heads - 1;
+                const int q1 = heads ? __ffs(heads) - 1 : nv;
+                const int pq = __shfl_sync(kFull, myp, q0);
+                if (pq != cur_p) {
+                    flush();
+                    cur_p = pq;
+                    acc = 0.f;
+                }
+                for (int q = q0; q < q1; ++q) acc = fmaf(X.pf[q * 9 + z], X.rf[q * 5 + aa], acc);
             }
             __syncwarp();
-            const int z = lane & 7, aa = lane >> 3;
-            for (int q = 0; q < nv; ++q) accA[pp[q] + lane] += pf[q * 8 + z] * rf[q * 4 + aa];
-            __syncwarp();
-            it.advance(32);
         }
+        flush();
+        for (; next_p < kNPairs; ++next_p) put_g(out, out_lo, kRadLen + 32 * next_p + lane, 0.f);
     }
-    __syncwarp();
-    const int si = species_of(hi_i);
-    const int rw = row_base(a.ctr->species, si) + a.rank[i];
-    if constexpr (sizeof(OutT) == 4) {
-        float* out = reinterpret_cast<float*>(G) + (size_t)rw * kAevLd;
-        for (int c = lane; c < kAevLd; c += 32) out[c] = row_value(acc, c);
-    } else {
-        store_row_bf16(reinterpret_cast<__nv_bfloat16*>(G) + (size_t)rw * kAevLd,
-                       G_lo ? reinterpret_cast<__nv_bfloat16*>(G_lo) + (size_t)rw * kAevLd : nullptr, acc, lane);
-    }
+    // radial block (two halves) and the zero padding of the row
+    for (int c = lane; c < kRadLen; c += 32) put_g(out, out_lo, c, X.accR[c] + X.accR[kRadLen + c]);
+    if (lane < kAevLd - kAevLen) put_g(out, out_lo, kAevLen + lane, 0.f);
     if (lane == 0) row_atom[rw] = i;
 }
 
