@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -39,21 +40,32 @@ inline int64_t now_ns() {
 }
 inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
+// One heap block per request: header, inputs (xyz, species) and the result
+// area (forces), written by the server thread before the request is marked
+// done under the lock.
 struct Request {
     mlp_ticket id;
     int n;
-    std::vector<int8_t> species;
-    std::vector<double> xyz;
+    int status;
+    bool done;
     int64_t t_submit;
+    double E;
+    double* xyz() { return reinterpret_cast<double*>(this + 1); }
+    float* F() { return reinterpret_cast<float*>(xyz() + 3 * (size_t)n); }
+    int8_t* species() { return reinterpret_cast<int8_t*>(F() + 3 * (size_t)n); }
+    static Request* make(int n) {
+        void* p = std::malloc(sizeof(Request) + 24 * (size_t)n + 12 * (size_t)n + (size_t)n);
+        if (!p) return nullptr;
+        Request* r = static_cast<Request*>(p);
+        r->n = n;
+        r->status = MLP_OK;
+        r->done = false;
+        r->E = 0.0;
+        return r;
+    }
+    static void release(Request* r) { std::free(r); }
 };
-
-struct Result {
-    bool done = false;
-    int status = MLP_OK;
-    int n = 0;
-    double E = 0.0;
-    std::vector<float> F;
-};
+static_assert(sizeof(Request) % 8 == 0, "request header keeps the coordinates 8-byte aligned");
 
 struct Slot {
     Workspace ws;
@@ -83,10 +95,11 @@ struct mlp_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
-    std::unordered_map<mlp_ticket, Result> results;
+    std::unordered_map<mlp_ticket, Request*> results;   // submitted and not yet taken
     std::vector<int64_t> latencies;
-    bool stop = false;
-    bool sleeping = false;   // the server thread waits for new requests (submit must wake it)
+    std::atomic<bool> stop{false};
+    bool sleeping = false;              // the server thread waits for new requests (submit must wake it)
+    std::atomic<int64_t> queued{0};     // requests in `queue` (read without the lock by the server loop)
     std::thread th;
     mlp_ticket next_id = 1;
     int64_t inflight_bytes = 0;
@@ -151,8 +164,8 @@ int launch_slot(mlp_server* S, Slot& s) {
     s.h_mol_start[0] = 0;
     for (size_t m = 0; m < s.reqs.size(); ++m) {
         Request* r = s.reqs[m];
-        std::memcpy(s.h_species + off, r->species.data(), r->n);
-        std::memcpy(s.h_xyz + 3 * (size_t)off, r->xyz.data(), 24 * (size_t)r->n);
+        std::memcpy(s.h_species + off, r->species(), r->n);
+        std::memcpy(s.h_xyz + 3 * (size_t)off, r->xyz(), 24 * (size_t)r->n);
         off += r->n;
         s.h_mol_start[m + 1] = off;
     }
@@ -183,28 +196,22 @@ int launch_slot(mlp_server* S, Slot& s) {
 void finish_slot(mlp_server* S, Slot& s, int status) {
     if (status == MLP_OK) status = check_counters(s.ws);
     const int64_t t = now_ns();
-    // results are assembled without the lock; only the hand-over is locked
-    std::vector<std::pair<mlp_ticket, Result>> done;
+    // results go into the requests without the lock (nobody reads a request
+    // before it is marked done); only the done flags are published under it
     std::vector<int64_t> lat;
-    done.reserve(s.reqs.size());
     lat.reserve(s.reqs.size());
     int off = 0;
     for (size_t m = 0; m < s.reqs.size(); ++m) {
         Request* r = s.reqs[m];
-        Result res;
-        res.status = status;
-        res.n = r->n;
-        res.E = s.h_E[m];
-        res.F.assign(s.h_F + 3 * (size_t)off, s.h_F + 3 * (size_t)(off + r->n));
-        res.done = true;
+        r->status = status;
+        r->E = s.h_E[m];
+        std::memcpy(r->F(), s.h_F + 3 * (size_t)off, 12 * (size_t)r->n);
         off += r->n;
         lat.push_back(t - r->t_submit);
-        done.emplace_back(r->id, std::move(res));
-        delete r;
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (auto& d : done) S->results[d.first] = std::move(d.second);
+        for (Request* r : s.reqs) r->done = true;
         S->latencies.insert(S->latencies.end(), lat.begin(), lat.end());
         if (S->latencies.size() > (1u << 22))
             S->latencies.erase(S->latencies.begin(), S->latencies.begin() + (1 << 20));
@@ -212,38 +219,41 @@ void finish_slot(mlp_server* S, Slot& s, int status) {
         S->st.batches += 1;
         S->st.atoms += s.n_atoms;
         S->inflight_bytes -= (int64_t)s.footprint;
-        s.reqs.clear();
-        s.busy = false;
     }
+    s.reqs.clear();
+    s.busy = false;
     S->cv_done.notify_all();
 }
 
+// The loop takes the lock only to move requests from the queue into a batch
+// (and to publish completions): completions are polled and the queue length
+// is read (an atomic) without it, so submitters rarely meet a held lock.
 void server_loop(mlp_server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> batch;
+    int idle = 0;
     for (;;) {
-        // completions
-        for (Slot& s : S->slots) {
-            if (!s.busy) continue;
-            cudaError_t q = cudaEventQuery(s.done);
-            if (q == cudaErrorNotReady) continue;
-            finish_slot(S, s, q == cudaSuccess ? MLP_OK : cuda_error(q, "batch"));
-        }
+        bool progressed = false, any_busy = false;
         Slot* free_slot = nullptr;
-        bool any_busy = false;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            for (Slot& s : S->slots) {
-                if (s.busy)
-                    any_busy = true;
-                else if (!free_slot)
-                    free_slot = &s;
+        for (Slot& s : S->slots) {
+            if (s.busy) {
+                cudaError_t q = cudaEventQuery(s.done);
+                if (q != cudaErrorNotReady) {
+                    finish_slot(S, s, q == cudaSuccess ? MLP_OK : cuda_error(q, "batch"));
+                    progressed = true;
+                }
             }
-            if (S->stop && S->queue.empty() && !any_busy) return;
-            if (free_slot && !S->queue.empty()) {
+            if (s.busy)
+                any_busy = true;
+            else if (!free_slot)
+                free_slot = &s;
+        }
+        if (free_slot && S->queued.load(std::memory_order_acquire) > 0) {
+            int atoms = 0;
+            batch.clear();
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
                 // admission: oldest first, within the slot's limits and the HBM budget
-                int atoms = 0;
-                batch.clear();
                 while (!S->queue.empty()) {
                     Request* r = S->queue.front();
                     if (atoms + r->n > S->o.max_batch_atoms || (int)batch.size() >= S->o.max_batch_mols) break;
@@ -254,35 +264,45 @@ void server_loop(mlp_server* S) {
                     atoms += r->n;
                     S->queue.pop_front();
                 }
+                S->queued.store((int64_t)S->queue.size(), std::memory_order_release);
                 if (!batch.empty()) {
-                    free_slot->reqs = batch;
                     free_slot->footprint = S->bytes_per_atom * (size_t)atoms;
-                    free_slot->busy = true;
                     S->inflight_bytes += (int64_t)free_slot->footprint;
                     S->st.peak_inflight_bytes = std::max(S->st.peak_inflight_bytes, S->inflight_bytes);
-                } else {
-                    free_slot = nullptr;
                 }
-            } else {
-                free_slot = nullptr;
             }
-            if (!free_slot) {
-                if (any_busy) {
-                    // poll the in-flight batches again shortly; new requests need no wake-up
-                    S->cv_work.wait_for(lk, std::chrono::microseconds(20));
-                } else if (S->queue.empty() && !S->stop) {
-                    S->sleeping = true;
-                    S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-                    S->sleeping = false;
+            if (!batch.empty()) {
+                free_slot->reqs = batch;
+                free_slot->busy = true;
+                progressed = true;
+                int rc = launch_slot(S, *free_slot);
+                if (rc) {
+                    cudaStreamSynchronize(free_slot->stream);
+                    finish_slot(S, *free_slot, rc);
                 }
                 continue;
             }
         }
-        int rc = launch_slot(S, *free_slot);
-        if (rc) {
-            cudaStreamSynchronize(free_slot->stream);
-            finish_slot(S, *free_slot, rc);
+        if (progressed) {
+            idle = 0;
+            continue;
         }
+        if (any_busy) {
+            // batches in flight: poll again soon (yield first, then short sleeps)
+            if (++idle < 64)
+                std::this_thread::yield();
+            else
+                std::this_thread::sleep_for(std::chrono::microseconds(5));
+            continue;
+        }
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->stop.load() && S->queue.empty()) return;
+        if (S->queue.empty()) {
+            S->sleeping = true;
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            S->sleeping = false;
+        }
+        idle = 0;
     }
 }
 
@@ -332,6 +352,7 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     S->w = w;
     cudaGetDevice(&S->device);
     S->bytes_per_atom = (sb + o.max_batch_atoms - 1) / o.max_batch_atoms;
+    S->results.reserve(2 * (size_t)o.queue_capacity);
     S->slots.resize(o.streams);
     for (Slot& s : S->slots) {
         int rc = slot_create(s, o);
@@ -356,12 +377,12 @@ void mlp_server_destroy(mlp_server* S) {
     if (!S) return;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->stop = true;
+        S->stop.store(true);
     }
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
-    for (Request* r : S->queue) delete r;
     for (Slot& s : S->slots) slot_destroy(s);
+    for (auto& kv : S->results) Request::release(kv.second);   // queued, in flight or not taken
     delete S;
 }
 
@@ -374,22 +395,22 @@ int mlp_submit(mlp_server* S, int32_t n, const int8_t* species, const double* co
         if (species[i] < 0 || species[i] >= kNSpecies) return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
     for (int q = 0; q < 3 * n; ++q)
         if (!std::isfinite(coords[q])) return set_error(MLP_EINVAL, "non-finite coordinate");
-    Request* r = new (std::nothrow) Request();
+    Request* r = Request::make(n);
     if (!r) return set_error(MLP_ENOMEM, "host allocation failed");
-    r->n = n;
-    r->species.assign(species, species + n);
-    r->xyz.assign(coords, coords + 3 * (size_t)n);
+    std::memcpy(r->species(), species, n);
+    std::memcpy(r->xyz(), coords, 24 * (size_t)n);
     r->t_submit = now_ns();
     bool wake;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if ((int)S->queue.size() >= S->o.queue_capacity) {
-            delete r;
+            Request::release(r);
             return set_error(MLP_EAGAIN, "server queue full (%d requests)", S->o.queue_capacity);
         }
         r->id = S->next_id++;
-        S->results[r->id] = Result();
+        S->results.emplace(r->id, r);
         S->queue.push_back(r);
+        S->queued.store((int64_t)S->queue.size(), std::memory_order_release);
         S->st.submitted += 1;
         *out = r->id;
         wake = S->sleeping;
@@ -398,15 +419,16 @@ int mlp_submit(mlp_server* S, int32_t n, const int8_t* species, const double* co
     return MLP_OK;
 }
 
-static int take_result(mlp_server* S, std::unordered_map<mlp_ticket, Result>::iterator it, double* energy,
+static int take_result(mlp_server* S, std::unordered_map<mlp_ticket, Request*>::iterator it, double* energy,
                        float* forces) {
-    Result& r = it->second;
-    int status = r.status;
+    Request* r = it->second;
+    const int status = r->status;
     if (status == MLP_OK) {
-        if (energy) *energy = r.E;
-        if (forces) std::memcpy(forces, r.F.data(), 12 * (size_t)r.n);
+        if (energy) *energy = r->E;
+        if (forces) std::memcpy(forces, r->F(), 12 * (size_t)r->n);
     }
     S->results.erase(it);
+    Request::release(r);
     return status;
 }
 
@@ -416,7 +438,7 @@ int mlp_poll(mlp_server* S, mlp_ticket t, double* energy, float* forces) {
     std::lock_guard<std::mutex> lk(S->mu);
     auto it = S->results.find(t);
     if (it == S->results.end()) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
-    if (!it->second.done) return MLP_PENDING;
+    if (!it->second->done) return MLP_PENDING;
     int rc = take_result(S, it, energy, forces);
     if (rc) set_error(rc, "request failed");
     return rc;
@@ -430,14 +452,14 @@ int mlp_wait(mlp_server* S, mlp_ticket t, int64_t timeout_ns, double* energy, fl
     for (;;) {
         auto it = S->results.find(t);
         if (it == S->results.end()) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
-        if (it->second.done) {
+        if (it->second->done) {
             int rc = take_result(S, it, energy, forces);
             if (rc) set_error(rc, "request failed");
             return rc;
         }
         if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
             auto it2 = S->results.find(t);
-            if (it2 != S->results.end() && it2->second.done) continue;
+            if (it2 != S->results.end() && it2->second->done) continue;
             return set_error(MLP_ETIMEDOUT, "ticket %llu not done within %lld ns", (unsigned long long)t,
                              (long long)timeout_ns);
         }
