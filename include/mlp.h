@@ -187,7 +187,7 @@ typedef struct {
     int32_t max_batch_mols;     /* molecules per batch (default 4096)                    */
     int32_t max_atoms_per_mol;  /* largest admissible molecule (default 256)             */
     int32_t streams;            /* batches in flight on the device (default 2)           */
-    int32_t queue_capacity;     /* pending requests before MLP_EAGAIN (default 65536)    */
+    int32_t queue_capacity;     /* requests outstanding (submitted, not yet collected) before MLP_EAGAIN (default 65536) */
     int64_t budget_bytes;       /* device bytes the in-flight batches may hold (40e9)    */
 } mlp_server_opts;
 
@@ -238,6 +238,15 @@ MLP_API int mlp_server_latencies(mlp_server *s, int64_t *out, int cap);
 MLP_API int mlp_server_replay(mlp_server *s, int32_t n_req, const int64_t *arrival_ns, const int32_t *mol_start,
                       const int8_t *species, const double *coords, double *energies, float *forces,
                       int64_t *wall_ns);
+
+/* The same with `clients` native client threads (1..64): client c submits
+ * requests c, c + clients, ... at their arrival times and then collects
+ * their results, as independent clients of one serving process would.
+ * MLP_EINVAL for clients outside [1, 64]; a failed request or submission
+ * (other than MLP_EAGAIN, which is retried) ends the replay with its code. */
+MLP_API int mlp_server_replay_clients(mlp_server *s, int32_t n_req, const int64_t *arrival_ns,
+                                      const int32_t *mol_start, const int8_t *species, const double *coords,
+                                      double *energies, float *forces, int32_t clients, int64_t *wall_ns);
 
 /* ------------------------------------------------------------------ allocation-free neighbor list */
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "mlp_server_get_stats": (ip, [vp, ctypes.POINTER(ServerStats)]),
     "mlp_server_latencies": (ip, [vp, i64p, ip]),
     "mlp_server_replay": (ip, [vp, i32, i64p, i32p, i8p, dp, dp, fp, i64p]),
+    "mlp_server_replay_clients": (ip, [vp, i32, i64p, i32p, i8p, dp, dp, fp, i32, i64p]),
     "mlp_neighbors_static": (ip, [vp, i32, dp, ctypes.c_double, vp, vp, i32, vp]),
     "mlp_set_allocator": (None, [vp, vp, vp]),
     "mlp_debug_fail_alloc": (None, [ctypes.c_longlong]),

@@ -262,20 +262,34 @@ class Server:
         k = check(load().mlp_server_latencies(self.handle, _ptr(out, ctypes.c_int64), cap), "mlp_server_latencies")
         return out[:k]
 
-    def replay(self, arrival_ns, mol_start, species, coords, forces=True):
-        """Open-loop arrivals (mlp_server_replay); returns (E, F, wall_s)."""
+    def replay(self, arrival_ns, mol_start, species, coords, forces=True, out=None, clients=1):
+        """Open-loop arrivals (mlp_server_replay_clients with `clients` native
+        client threads); returns (E, F, wall_s).
+
+        out = (E float64 [n_req], F float32 [n_atoms, 3] or None): result
+        arrays to reuse (a serving process keeps its output buffers).
+        """
         arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
         ms = np.ascontiguousarray(mol_start, dtype=np.int32)
         sp = np.ascontiguousarray(species, dtype=np.int8)
         n = int(ms[-1])
         x = _f64(coords, (n, 3))
-        E = np.zeros(arr.shape[0])
-        F = np.zeros((n, 3), dtype=np.float32) if forces else None
+        if out is not None:
+            E, F = out
+            if E.dtype != np.float64 or E.shape != (arr.shape[0],) or not E.flags.c_contiguous:
+                raise ValueError("out[0] must be a contiguous float64 array of one energy per request")
+            if F is not None and (F.dtype != np.float32 or F.shape != (n, 3) or not F.flags.c_contiguous):
+                raise ValueError("out[1] must be a contiguous float32 [n_atoms, 3] array")
+        else:
+            E = np.zeros(arr.shape[0])
+            F = np.zeros((n, 3), dtype=np.float32) if forces else None
         wall = ctypes.c_int64()
-        check(load().mlp_server_replay(self.handle, arr.shape[0], _ptr(arr, ctypes.c_int64), _ptr(ms, ctypes.c_int32),
-                                       _ptr(sp, ctypes.c_int8), _ptr(x, ctypes.c_double), _ptr(E, ctypes.c_double),
-                                       None if F is None else _ptr(F, ctypes.c_float), ctypes.byref(wall)),
-              "mlp_server_replay")
+        check(load().mlp_server_replay_clients(self.handle, arr.shape[0], _ptr(arr, ctypes.c_int64),
+                                               _ptr(ms, ctypes.c_int32), _ptr(sp, ctypes.c_int8),
+                                               _ptr(x, ctypes.c_double), _ptr(E, ctypes.c_double),
+                                               None if F is None else _ptr(F, ctypes.c_float), int(clients),
+                                               ctypes.byref(wall)),
+              "mlp_server_replay_clients")
         return E, F, wall.value * 1e-9
 
     def close(self):

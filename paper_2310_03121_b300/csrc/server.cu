@@ -1,17 +1,22 @@
 // Serving loop: continuous batching of energy+force requests for independent
 // open-boundary molecules.
 //
-// Clients queue molecules with mlp_submit (never blocks). One server thread
-// owns `streams` slots; each slot is a reserved device workspace with its own
+// Clients queue molecules with mlp_submit (never blocks, takes no lock):
+// the request (one pooled heap block holding its inputs and its result
+// area) gets a ticket from an atomic counter, is published in a ticket ring
+// (the lookup table of mlp_poll / mlp_wait) and pushed on an intrusive
+// multi-producer queue. One server thread drains that queue and owns
+// `streams` slots; each slot is a reserved device workspace with its own
 // CUDA stream and pinned staging. Whenever a slot is free and requests are
-// queued, the thread packs the oldest requests (up to the slot's atom and
+// waiting, the thread packs the oldest ones (up to the slot's atom and
 // molecule limits, and while the bytes held by in-flight batches stay within
 // the HBM budget) into one batch, copies it to the device and enqueues the
 // evaluation; batches on different slots overlap on the GPU while the next
 // one is being packed. Completion is detected with CUDA events; results are
-// scattered to their tickets and waiters are woken. Energies are reduced per
-// molecule in a fixed order, so a molecule's energy does not depend on the
-// batch it was packed into (forces agree to FP64 atomic rounding).
+// written into their requests, which are then marked done and waiters woken.
+// Energies are reduced per molecule in a fixed order, so a molecule's energy
+// does not depend on the batch it was packed into (forces agree to FP64
+// atomic rounding).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -20,10 +25,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/mlp.h"
@@ -41,31 +46,113 @@ inline int64_t now_ns() {
 inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 // One heap block per request: header, inputs (xyz, species) and the result
-// area (forces), written by the server thread before the request is marked
-// done under the lock.
+// area (forces). Blocks come in power-of-two atom capacities (2^cls).
 struct Request {
+    std::atomic<Request*> next;   // link of the submission queue
     mlp_ticket id;
     int n;
+    int cls;
     int status;
-    bool done;
+    std::atomic<bool> done;       // results written (release) / readable (acquire)
     int64_t t_submit;
     double E;
     double* xyz() { return reinterpret_cast<double*>(this + 1); }
-    float* F() { return reinterpret_cast<float*>(xyz() + 3 * (size_t)n); }
-    int8_t* species() { return reinterpret_cast<int8_t*>(F() + 3 * (size_t)n); }
-    static Request* make(int n) {
-        void* p = std::malloc(sizeof(Request) + 24 * (size_t)n + 12 * (size_t)n + (size_t)n);
-        if (!p) return nullptr;
-        Request* r = static_cast<Request*>(p);
+    float* F() { return reinterpret_cast<float*>(xyz() + 3 * ((size_t)1 << cls)); }
+    int8_t* species() { return reinterpret_cast<int8_t*>(F() + 3 * ((size_t)1 << cls)); }
+    static size_t bytes(int cls) { return sizeof(Request) + 37 * ((size_t)1 << cls); }
+};
+static_assert(sizeof(Request) % 8 == 0, "request header keeps the coordinates 8-byte aligned");
+
+// Free blocks per capacity class, in 8 shards picked by the calling thread,
+// so that concurrent clients rarely share a lock; blocks are never returned
+// to the system while the server lives (a serving process in steady state
+// allocates and page-faults no new memory).
+struct RequestPool {
+    static constexpr int kShards = 8;
+    struct alignas(64) Shard {
+        std::mutex mu;
+        std::vector<Request*> free_[32];
+    };
+    Shard shards[kShards];
+    static int shard_of_thread() {
+        static thread_local int s = (int)(std::hash<std::thread::id>()(std::this_thread::get_id()) % kShards);
+        return s;
+    }
+    Request* get(int n) {
+        int cls = 3;
+        while (((int64_t)1 << cls) < n) ++cls;
+        Request* r = nullptr;
+        Shard& sh = shards[shard_of_thread()];
+        {
+            std::lock_guard<std::mutex> lk(sh.mu);
+            if (!sh.free_[cls].empty()) {
+                r = sh.free_[cls].back();
+                sh.free_[cls].pop_back();
+            }
+        }
+        if (!r) {
+            void* p = std::malloc(Request::bytes(cls));
+            if (!p) return nullptr;
+            r = new (p) Request();
+        }
         r->n = n;
+        r->cls = cls;
         r->status = MLP_OK;
-        r->done = false;
+        r->done.store(false, std::memory_order_relaxed);
         r->E = 0.0;
         return r;
     }
-    static void release(Request* r) { std::free(r); }
+    void put(Request* r) {
+        Shard& sh = shards[shard_of_thread()];
+        std::lock_guard<std::mutex> lk(sh.mu);
+        sh.free_[r->cls].push_back(r);
+    }
+    ~RequestPool() {
+        for (Shard& sh : shards)
+            for (auto& v : sh.free_)
+                for (Request* r : v) {
+                    r->~Request();
+                    std::free(r);
+                }
+    }
 };
-static_assert(sizeof(Request) % 8 == 0, "request header keeps the coordinates 8-byte aligned");
+
+// Intrusive multi-producer / single-consumer FIFO (a stub node and an
+// exchanged tail): push is wait-free for any number of clients, pop is run
+// by the server thread only.
+struct SubmitQueue {
+    Request stub_;
+    std::atomic<Request*> tail{&stub_};
+    Request* head = &stub_;
+    SubmitQueue() { stub_.next.store(nullptr, std::memory_order_relaxed); }
+    void push(Request* r) {
+        r->next.store(nullptr, std::memory_order_relaxed);
+        Request* prev = tail.exchange(r, std::memory_order_acq_rel);
+        prev->next.store(r, std::memory_order_release);
+    }
+    Request* pop() {
+        Request* h = head;
+        Request* nx = h->next.load(std::memory_order_acquire);
+        if (h == &stub_) {
+            if (!nx) return nullptr;
+            head = nx;
+            h = nx;
+            nx = nx->next.load(std::memory_order_acquire);
+        }
+        if (nx) {
+            head = nx;
+            return h;
+        }
+        if (h != tail.load(std::memory_order_acquire)) return nullptr;   // a push is half done: later
+        push(&stub_);
+        nx = h->next.load(std::memory_order_acquire);
+        if (nx) {
+            head = nx;
+            return h;
+        }
+        return nullptr;
+    }
+};
 
 struct Slot {
     Workspace ws;
@@ -92,18 +179,43 @@ struct mlp_server {
     int device = 0;
     std::vector<Slot> slots;
     size_t bytes_per_atom = 0;
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request*> queue;
-    std::unordered_map<mlp_ticket, Request*> results;   // submitted and not yet taken
-    std::vector<int64_t> latencies;
+    // ticket ring: ticket t lives in entry t & ring_mask until taken; a
+    // submit whose entry is still held by an uncollected request is refused
+    std::vector<std::atomic<Request*>> ring;
+    uint64_t ring_mask = 0;
+    RequestPool pool;
+    SubmitQueue sq;
+    std::deque<Request*> pending;   // drained from sq, not yet batched (server thread only)
+    alignas(64) std::atomic<uint64_t> next_id{1};
+    alignas(64) std::atomic<int64_t> queued{0};   // pushed on sq and not yet drained
+    alignas(64) std::atomic<bool> sleeping{false};
     std::atomic<bool> stop{false};
-    bool sleeping = false;              // the server thread waits for new requests (submit must wake it)
-    std::atomic<int64_t> queued{0};     // requests in `queue` (read without the lock by the server loop)
-    std::thread th;
-    mlp_ticket next_id = 1;
+    std::atomic<int64_t> submitted{0};
+    // guarded by mu: statistics, latencies, in-flight bytes; cv_done waiters
+    alignas(64) std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::vector<int64_t> latencies;
     int64_t inflight_bytes = 0;
     mlp_server_stats st{};
+    std::thread th;
+
+    bool init_tables() {
+        size_t r = 8;
+        while (r < (size_t)o.queue_capacity) r <<= 1;
+        try {
+            ring = std::vector<std::atomic<Request*>>(r);
+        } catch (...) {
+            return false;
+        }
+        for (auto& e : ring) e.store(nullptr, std::memory_order_relaxed);
+        ring_mask = r - 1;
+        return true;
+    }
+    Request* lookup(mlp_ticket t) {
+        if (t == 0) return nullptr;
+        Request* r = ring[t & ring_mask].load(std::memory_order_acquire);
+        return (r && r->id == t) ? r : nullptr;
+    }
 };
 
 struct mlp_weights;   // defined in api.cu; the server only passes it through
@@ -196,8 +308,7 @@ int launch_slot(mlp_server* S, Slot& s) {
 void finish_slot(mlp_server* S, Slot& s, int status) {
     if (status == MLP_OK) status = check_counters(s.ws);
     const int64_t t = now_ns();
-    // results go into the requests without the lock (nobody reads a request
-    // before it is marked done); only the done flags are published under it
+    // results go into the requests; a request is readable once marked done
     std::vector<int64_t> lat;
     lat.reserve(s.reqs.size());
     int off = 0;
@@ -208,10 +319,10 @@ void finish_slot(mlp_server* S, Slot& s, int status) {
         std::memcpy(r->F(), s.h_F + 3 * (size_t)off, 12 * (size_t)r->n);
         off += r->n;
         lat.push_back(t - r->t_submit);
+        r->done.store(true, std::memory_order_release);
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (Request* r : s.reqs) r->done = true;
         S->latencies.insert(S->latencies.end(), lat.begin(), lat.end());
         if (S->latencies.size() > (1u << 22))
             S->latencies.erase(S->latencies.begin(), S->latencies.begin() + (1 << 20));
@@ -225,15 +336,20 @@ void finish_slot(mlp_server* S, Slot& s, int status) {
     S->cv_done.notify_all();
 }
 
-// The loop takes the lock only to move requests from the queue into a batch
-// (and to publish completions): completions are polled and the queue length
-// is read (an atomic) without it, so submitters rarely meet a held lock.
+// The serving thread: drains the submission queue, polls completions and
+// forms batches; it takes the lock only for statistics and for sleeping.
 void server_loop(mlp_server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> batch;
     int idle = 0;
     for (;;) {
         bool progressed = false, any_busy = false;
+        int64_t drained = 0;
+        while (Request* r = S->sq.pop()) {
+            S->pending.push_back(r);
+            ++drained;
+        }
+        if (drained) S->queued.fetch_sub(drained);
         Slot* free_slot = nullptr;
         for (Slot& s : S->slots) {
             if (s.busy) {
@@ -248,46 +364,48 @@ void server_loop(mlp_server* S) {
             else if (!free_slot)
                 free_slot = &s;
         }
-        if (free_slot && S->queued.load(std::memory_order_acquire) > 0) {
+        if (free_slot && !S->pending.empty()) {
+            // admission: oldest first, within the slot's limits and the HBM budget
             int atoms = 0;
             batch.clear();
+            int64_t inflight;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                // admission: oldest first, within the slot's limits and the HBM budget
-                while (!S->queue.empty()) {
-                    Request* r = S->queue.front();
-                    if (atoms + r->n > S->o.max_batch_atoms || (int)batch.size() >= S->o.max_batch_mols) break;
-                    int64_t fp = (int64_t)S->bytes_per_atom * (atoms + r->n);
-                    if (S->inflight_bytes + fp > S->o.budget_bytes && !batch.empty()) break;
-                    if (S->inflight_bytes + fp > S->o.budget_bytes && any_busy) break;   // wait for memory
-                    batch.push_back(r);
-                    atoms += r->n;
-                    S->queue.pop_front();
-                }
-                S->queued.store((int64_t)S->queue.size(), std::memory_order_release);
-                if (!batch.empty()) {
-                    free_slot->footprint = S->bytes_per_atom * (size_t)atoms;
+                inflight = S->inflight_bytes;
+            }
+            while (!S->pending.empty()) {
+                Request* r = S->pending.front();
+                if (atoms + r->n > S->o.max_batch_atoms || (int)batch.size() >= S->o.max_batch_mols) break;
+                int64_t fp = (int64_t)S->bytes_per_atom * (atoms + r->n);
+                if (inflight + fp > S->o.budget_bytes && !batch.empty()) break;
+                if (inflight + fp > S->o.budget_bytes && any_busy) break;   // wait for memory
+                batch.push_back(r);
+                atoms += r->n;
+                S->pending.pop_front();
+            }
+            if (!batch.empty()) {
+                free_slot->footprint = S->bytes_per_atom * (size_t)atoms;
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
                     S->inflight_bytes += (int64_t)free_slot->footprint;
                     S->st.peak_inflight_bytes = std::max(S->st.peak_inflight_bytes, S->inflight_bytes);
                 }
-            }
-            if (!batch.empty()) {
                 free_slot->reqs = batch;
                 free_slot->busy = true;
-                progressed = true;
                 int rc = launch_slot(S, *free_slot);
                 if (rc) {
                     cudaStreamSynchronize(free_slot->stream);
                     finish_slot(S, *free_slot, rc);
                 }
+                idle = 0;
                 continue;
             }
         }
-        if (progressed) {
+        if (progressed || drained) {
             idle = 0;
             continue;
         }
-        if (any_busy) {
+        if (any_busy || !S->pending.empty()) {
             // batches in flight: poll again soon (yield first, then short sleeps)
             if (++idle < 64)
                 std::this_thread::yield();
@@ -295,12 +413,12 @@ void server_loop(mlp_server* S) {
                 std::this_thread::sleep_for(std::chrono::microseconds(5));
             continue;
         }
-        std::unique_lock<std::mutex> lk(S->mu);
-        if (S->stop.load() && S->queue.empty()) return;
-        if (S->queue.empty()) {
-            S->sleeping = true;
-            S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            S->sleeping = false;
+        if (S->stop.load() && S->queued.load() == 0) return;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->sleeping.store(true);
+            if (S->queued.load() == 0 && !S->stop.load()) S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            S->sleeping.store(false);
         }
         idle = 0;
     }
@@ -352,7 +470,10 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     S->w = w;
     cudaGetDevice(&S->device);
     S->bytes_per_atom = (sb + o.max_batch_atoms - 1) / o.max_batch_atoms;
-    S->results.reserve(2 * (size_t)o.queue_capacity);
+    if (!S->init_tables()) {
+        delete S;
+        return set_error(MLP_ENOMEM, "host allocation failed");
+    }
     S->slots.resize(o.streams);
     for (Slot& s : S->slots) {
         int rc = slot_create(s, o);
@@ -382,7 +503,10 @@ void mlp_server_destroy(mlp_server* S) {
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     for (Slot& s : S->slots) slot_destroy(s);
-    for (auto& kv : S->results) Request::release(kv.second);   // queued, in flight or not taken
+    for (auto& e : S->ring) {   // queued, in flight or not collected
+        Request* r = e.load();
+        if (r) S->pool.put(r);
+    }
     delete S;
 }
 
@@ -391,78 +515,88 @@ int mlp_submit(mlp_server* S, int32_t n, const int8_t* species, const double* co
     if (!S || !species || !coords || !out) return set_error(MLP_EINVAL, "NULL argument");
     if (n <= 0 || n > S->o.max_atoms_per_mol)
         return set_error(MLP_EINVAL, "molecule of %d atoms outside [1, %d]", n, S->o.max_atoms_per_mol);
-    for (int i = 0; i < n; ++i)
-        if (species[i] < 0 || species[i] >= kNSpecies) return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
-    for (int q = 0; q < 3 * n; ++q)
-        if (!std::isfinite(coords[q])) return set_error(MLP_EINVAL, "non-finite coordinate");
-    Request* r = Request::make(n);
+    // branch-free scans (vectorizable); the failing index is looked up only on error
+    int bad = 0;
+    for (int i = 0; i < n; ++i) bad |= (species[i] < 0) | (species[i] >= kNSpecies);
+    if (bad)
+        for (int i = 0; i < n; ++i)
+            if (species[i] < 0 || species[i] >= kNSpecies)
+                return set_error(MLP_EINVAL, "species[%d] = %d", i, species[i]);
+    uint64_t nonfinite = 0;
+    for (int q = 0; q < 3 * n; ++q) {
+        uint64_t b;
+        std::memcpy(&b, coords + q, 8);
+        nonfinite |= (uint64_t)((b & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+    }
+    if (nonfinite) return set_error(MLP_EINVAL, "non-finite coordinate");
+    Request* r = S->pool.get(n);
     if (!r) return set_error(MLP_ENOMEM, "host allocation failed");
     std::memcpy(r->species(), species, n);
     std::memcpy(r->xyz(), coords, 24 * (size_t)n);
     r->t_submit = now_ns();
-    bool wake;
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        if ((int)S->queue.size() >= S->o.queue_capacity) {
-            Request::release(r);
-            return set_error(MLP_EAGAIN, "server queue full (%d requests)", S->o.queue_capacity);
-        }
-        r->id = S->next_id++;
-        S->results.emplace(r->id, r);
-        S->queue.push_back(r);
-        S->queued.store((int64_t)S->queue.size(), std::memory_order_release);
-        S->st.submitted += 1;
-        *out = r->id;
-        wake = S->sleeping;
+    const mlp_ticket t = S->next_id.fetch_add(1);
+    r->id = t;
+    Request* expected = nullptr;
+    if (!S->ring[t & S->ring_mask].compare_exchange_strong(expected, r, std::memory_order_acq_rel)) {
+        S->pool.put(r);
+        return set_error(MLP_EAGAIN, "server full: %d requests outstanding", S->o.queue_capacity);
     }
-    if (wake) S->cv_work.notify_one();
+    S->submitted.fetch_add(1, std::memory_order_relaxed);
+    S->sq.push(r);
+    S->queued.fetch_add(1);
+    if (S->sleeping.load()) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->cv_work.notify_one();
+    }
+    *out = t;
     return MLP_OK;
 }
 
-static int take_result(mlp_server* S, std::unordered_map<mlp_ticket, Request*>::iterator it, double* energy,
-                       float* forces) {
-    Request* r = it->second;
+// Takes a done request out of the ring (only one caller can); MLP_ENOTFOUND
+// if another caller took the ticket first.
+static int take_result(mlp_server* S, mlp_ticket t, Request* r, double* energy, float* forces) {
+    Request* expected = r;
+    if (!S->ring[t & S->ring_mask].compare_exchange_strong(expected, nullptr, std::memory_order_acq_rel))
+        return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
+    if (r->id != t) {   // the block was recycled under another ticket: not ours
+        S->ring[t & S->ring_mask].store(r, std::memory_order_release);
+        return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
+    }
     const int status = r->status;
     if (status == MLP_OK) {
         if (energy) *energy = r->E;
         if (forces) std::memcpy(forces, r->F(), 12 * (size_t)r->n);
     }
-    S->results.erase(it);
-    Request::release(r);
+    S->pool.put(r);
+    if (status) set_error(status, "request failed");
     return status;
 }
 
 int mlp_poll(mlp_server* S, mlp_ticket t, double* energy, float* forces) {
     clear_error();
     if (!S) return set_error(MLP_EINVAL, "NULL server");
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->results.find(t);
-    if (it == S->results.end()) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
-    if (!it->second->done) return MLP_PENDING;
-    int rc = take_result(S, it, energy, forces);
-    if (rc) set_error(rc, "request failed");
-    return rc;
+    Request* r = S->lookup(t);
+    if (!r) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
+    if (!r->done.load(std::memory_order_acquire)) return MLP_PENDING;
+    return take_result(S, t, r, energy, forces);
 }
 
 int mlp_wait(mlp_server* S, mlp_ticket t, int64_t timeout_ns, double* energy, float* forces) {
     clear_error();
     if (!S) return set_error(MLP_EINVAL, "NULL server");
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto deadline = Clock::now() + std::chrono::nanoseconds(timeout_ns < 0 ? 0 : timeout_ns);
+    const auto deadline = Clock::now() + std::chrono::nanoseconds(timeout_ns < 0 ? 0 : timeout_ns);
+    bool timed_out = false;
     for (;;) {
-        auto it = S->results.find(t);
-        if (it == S->results.end()) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
-        if (it->second->done) {
-            int rc = take_result(S, it, energy, forces);
-            if (rc) set_error(rc, "request failed");
-            return rc;
-        }
-        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
-            auto it2 = S->results.find(t);
-            if (it2 != S->results.end() && it2->second->done) continue;
+        Request* r = S->lookup(t);
+        if (!r) return set_error(MLP_ENOTFOUND, "unknown ticket %llu", (unsigned long long)t);
+        if (r->done.load(std::memory_order_acquire)) return take_result(S, t, r, energy, forces);
+        if (timed_out)
             return set_error(MLP_ETIMEDOUT, "ticket %llu not done within %lld ns", (unsigned long long)t,
                              (long long)timeout_ns);
-        }
+        std::unique_lock<std::mutex> lk(S->mu);
+        // done is set before finish_slot takes the lock to notify: checked again under it
+        if (r->done.load(std::memory_order_acquire) || S->lookup(t) != r) continue;
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) timed_out = true;
     }
 }
 
@@ -471,6 +605,7 @@ int mlp_server_get_stats(mlp_server* S, mlp_server_stats* out) {
     if (!S || !out) return set_error(MLP_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->st;
+    out->submitted = S->submitted.load();
     out->inflight_bytes = S->inflight_bytes;
     out->mean_batch_atoms = S->st.batches ? (double)S->st.atoms / (double)S->st.batches : 0.0;
     out->slot_bytes = (int64_t)slot_bytes(S->o);
@@ -488,17 +623,20 @@ int mlp_server_latencies(mlp_server* S, int64_t* out, int cap) {
     return k;
 }
 
-int mlp_server_replay(mlp_server* S, int32_t n_req, const int64_t* arrival_ns, const int32_t* mol_start,
-                      const int8_t* species, const double* coords, double* energies, float* forces,
-                      int64_t* wall_ns) {
+int mlp_server_replay_clients(mlp_server* S, int32_t n_req, const int64_t* arrival_ns, const int32_t* mol_start,
+                              const int8_t* species, const double* coords, double* energies, float* forces,
+                              int32_t clients, int64_t* wall_ns) {
     clear_error();
-    if (!S || !arrival_ns || !mol_start || !species || !coords || !energies || n_req <= 0)
+    if (!S || !arrival_ns || !mol_start || !species || !coords || !energies || n_req <= 0 || clients < 1 ||
+        clients > 64)
         return set_error(MLP_EINVAL, "bad replay arguments");
     std::vector<mlp_ticket> tickets(n_req);
-    int status = MLP_OK;
+    std::atomic<int> status{MLP_OK};
     const int64_t t0 = now_ns();
-    std::thread gen([&]() {
-        for (int r = 0; r < n_req; ++r) {
+    // client c submits requests c, c + clients, ... at their arrival times,
+    // then collects the results of its own requests
+    auto client = [&](int c) {
+        for (int r = c; r < n_req && status.load() == MLP_OK; r += clients) {
             const int64_t due = t0 + arrival_ns[r];
             for (;;) {
                 int64_t now = now_ns();
@@ -513,23 +651,35 @@ int mlp_server_replay(mlp_server* S, int32_t n_req, const int64_t* arrival_ns, c
                 int rc = mlp_submit(S, b - a, species + a, coords + 3 * (size_t)a, &tickets[r]);
                 if (rc == MLP_OK) break;
                 if (rc != MLP_EAGAIN) {
-                    status = rc;
-                    tickets[r] = 0;
-                    break;
+                    status.store(rc);
+                    return;
                 }
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
         }
-    });
-    gen.join();
-    if (status != MLP_OK) return set_error(status, "replay submit failed");
-    for (int r = 0; r < n_req; ++r) {
-        const int a = mol_start[r];
-        int rc = mlp_wait(S, tickets[r], 600LL * 1000000000LL, &energies[r], forces ? forces + 3 * (size_t)a : nullptr);
-        if (rc) return rc;
+        for (int r = c; r < n_req && status.load() == MLP_OK; r += clients) {
+            const int a = mol_start[r];
+            int rc = mlp_wait(S, tickets[r], 600LL * 1000000000LL, &energies[r], forces ? forces + 3 * (size_t)a : nullptr);
+            if (rc) status.store(rc);
+        }
+    };
+    std::vector<std::thread> th;
+    try {
+        for (int c = 1; c < clients; ++c) th.emplace_back(client, c);
+    } catch (...) {
+        status.store(MLP_ENOMEM);
     }
+    client(0);
+    for (auto& t : th) t.join();
+    if (status.load() != MLP_OK) return set_error(status.load(), "replay: a request failed or could not be submitted");
     if (wall_ns) *wall_ns = now_ns() - t0;
     return MLP_OK;
+}
+
+int mlp_server_replay(mlp_server* S, int32_t n_req, const int64_t* arrival_ns, const int32_t* mol_start,
+                      const int8_t* species, const double* coords, double* energies, float* forces,
+                      int64_t* wall_ns) {
+    return mlp_server_replay_clients(S, n_req, arrival_ns, mol_start, species, coords, energies, forces, 1, wall_ns);
 }
 
 }  // extern "C"

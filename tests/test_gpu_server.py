@@ -174,3 +174,25 @@ def test_replay_open_loop(P, W, stream):
     assert lat.shape[0] == n and (lat > 0).all()
     assert wall >= arr[-1] * 1e-9
     srv.close()
+
+
+def test_replay_several_clients(P, W, stream):
+    """Three client threads: every request answered, results equal to the
+    batch path bit for bit (energies) and to FP64-atomic rounding (forces)."""
+    st = stream
+    srv = P.Server(W, precision="bf16", max_batch_atoms=16384, max_batch_mols=256, streams=2)
+    n = 400
+    arr = np.zeros(n, dtype=np.int64)
+    ms = st.mol_start[: n + 1]
+    E, F, wall = srv.replay(arr, ms, st.species[: ms[-1]], st.coords[: ms[-1]], clients=3)
+    b = P.Batch(W, precision="bf16", max_atoms=int(ms[-1]), max_mols=n)
+    Eb, Fb = b.run(ms, st.species[: ms[-1]], st.coords[: ms[-1]])
+    np.testing.assert_array_equal(E, Eb)
+    assert np.abs(F - Fb).max() <= 1e-6 * max(1.0, np.abs(Fb).max())
+    assert srv.stats()["completed"] == n and wall > 0
+    from paper_2310_03121_b300 import _lib
+
+    with pytest.raises(P.MLPError) as ei:
+        srv.replay(arr, ms, st.species[: ms[-1]], st.coords[: ms[-1]], clients=65)
+    assert ei.value.code == _lib.MLP_EINVAL
+    srv.close()
