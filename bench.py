@@ -24,6 +24,7 @@ host cores (cpu_baseline).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -382,6 +383,30 @@ def term_counts(stream):
     return nr / n, npairs / n
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per atom of one
+# launch, taken by ncu on a 131,056-atom launch of the served stream with the
+# kernel source whose SHA-1 is given; reported as `traffic` only while the
+# source is unchanged (otherwise null: the counters no longer describe it).
+MEASURED_TRAFFIC = {
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "a7ec9b769ac00b5f640729099c15318b01970572",
+               "bytes_per_atom": (603.203584e6 + 236.504832e6) / 131056},
+}
+
+
+def measured_traffic(name, atoms_per_launch):
+    m = MEASURED_TRAFFIC.get(name)
+    if not m:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2310_03121_b300", "csrc", m["file"])
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != m["sha1"]:
+                return None
+    except OSError:
+        return None
+    return m["bytes_per_atom"] * atoms_per_launch
+
+
 def roofline(prof, n_atoms, steps, prec, terms):
     peaks, src = measured_peaks()
     if not prof:
@@ -393,7 +418,8 @@ def roofline(prof, n_atoms, steps, prec, terms):
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
     nrad, npair = terms
-    base = {"kernel": name, "launch_ms": avg_ms, "units_per_launch": atoms_per_launch, "traffic": None}
+    base = {"kernel": name, "launch_ms": avg_ms, "units_per_launch": atoms_per_launch,
+            "traffic": measured_traffic(name, atoms_per_launch)}
     if name.startswith("mlp_tc"):
         per_atom = (3 * MLP_FLOP_FWD if prec == "bf16" else MLP_FLOP_FWD) + MLP_FLOP_BWD
         ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
