@@ -76,23 +76,42 @@ struct M<false> {   // accurate FP32 library functions (FP32 path)
     static __device__ __forceinline__ float rcp(float x) { return 1.f / x; }
 };
 template <>
-struct M<true> {    // hardware approximations (BF16-network path)
+struct M<true> {    // hardware approximations with subnormals flushed (BF16-network path)
     static __device__ __forceinline__ float ex2(float x) {
         float y;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
-    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
-    static __device__ __forceinline__ float pw(float b, float e) { return ex2(e * __log2f(b)); }
-    static __device__ __forceinline__ float cpi(float x) { return __cosf(3.14159265358979f * x); }
-    static __device__ __forceinline__ float spi(float x) { return __sinf(3.14159265358979f * x); }
-    static __device__ __forceinline__ float sq(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
-    static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float lg2(float x) {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     static __device__ __forceinline__ float rcp(float x) {
         float y;
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
+    static __device__ __forceinline__ float rsq(float x) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    // exp(x) = 2^(x log2 e); b^e = 2^(e log2 b)
+    static __device__ __forceinline__ float ex(float x) { return ex2(x * 1.4426950408889634f); }
+    static __device__ __forceinline__ float pw(float b, float e) { return ex2(e * lg2(b)); }
+    static __device__ __forceinline__ float cpi(float x) {
+        float y;
+        asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(3.14159265358979f * x));
+        return y;
+    }
+    static __device__ __forceinline__ float spi(float x) {
+        float y;
+        asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(3.14159265358979f * x));
+        return y;
+    }
+    static __device__ __forceinline__ float sq(float x) { return x * rsq(fmaxf(x, 1e-30f)); }
+    static __device__ __forceinline__ float dv(float a, float b) { return a * rcp(b); }
 };
 
 // Angular sub-list of one atom (neighbors within 3.5 A).
@@ -144,6 +163,7 @@ struct NbrLane {
     bool inR, inA;
 };
 
+template <bool FAST>
 __device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* row, int q, int cnt,
                                                  const float4& hi_i, const float4& lo_i) {
     NbrLane nl;
@@ -156,7 +176,8 @@ __device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* ro
         nl.j = row[q];
         const float4 hj = a.hi[nl.j], lj = a.lo[nl.j];
         nl.d = displacement(hi_i, lo_i, hj, lj, a.box);
-        nl.r = sqrtf(nl.d.x * nl.d.x + nl.d.y * nl.d.y + nl.d.z * nl.d.z);
+        const float r2 = nl.d.x * nl.d.x + nl.d.y * nl.d.y + nl.d.z * nl.d.z;
+        nl.r = FAST ? M<true>::sq(r2) : sqrtf(r2);
         nl.inR = nl.r < kRcRad;
         nl.inA = nl.r < kRcAng;
         nl.sp = species_of(hj);
@@ -250,7 +271,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
     for (int base = 0; base < cnt; base += 32) {
-        const NbrLane nl = load_neighbor(a, row, base + lane, cnt, hi_i, lo_i);
+        const NbrLane nl = load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
         const float fcr = nl.inR ? 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcRad)) + 0.5f : 0.f;
         const int nq = min(32, cnt - base);
         for (int q = 0; q < nq; q += 2) {
@@ -420,20 +441,20 @@ __device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, 
     // C = exp(-2 eta D^2), d_k = r - R_k, D the shift spacing.
     const float R0 = c_aev.shf_r[0];
     const float D = c_aev.shf_r[1] - c_aev.shf_r[0];
-    const float C = __expf(-2.f * kEtaRad * D * D);
+    const float C = M<true>::ex(-2.f * kEtaRad * D * D);
     int kc = __float2int_rn((r - R0) * (1.f / D));
     kc = min(max(kc, 0), kRadShifts - 1);
     const float dc = r - c_aev.shf_r[kc];
-    const float Gc = __expf(-kEtaRad * dc * dc);
+    const float Gc = M<true>::ex(-kEtaRad * dc * dc);
     s = g[kc] * Gc * (-2.f * kEtaRad * dc * fc + dfc);
-    float gu = Gc, mu = __expf(2.f * kEtaRad * D * dc - kEtaRad * D * D), du = dc;
+    float gu = Gc, mu = M<true>::ex(2.f * kEtaRad * D * dc - kEtaRad * D * D), du = dc;
     for (int kk = kc + 1; kk < kRadShifts; ++kk) {
         gu *= mu;
         mu *= C;
         du -= D;
         s += g[kk] * gu * (-2.f * kEtaRad * du * fc + dfc);
     }
-    float gd = Gc, nd = __expf(-2.f * kEtaRad * D * dc - kEtaRad * D * D), dd = dc;
+    float gd = Gc, nd = M<true>::ex(-2.f * kEtaRad * D * dc - kEtaRad * D * D), dd = dc;
     for (int kk = kc - 1; kk >= 0; --kk) {
         gd *= nd;
         nd *= C;
@@ -493,7 +514,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
     // to its (still private) shared-memory slot, which the angular terms add
     // to and which is flushed once; other neighbors go straight to the FP64 sums.
     for (int base = 0; base < cnt; base += 32) {
-        const NbrLane nl = load_neighbor(a, row, base + lane, cnt, hi_i, lo_i);
+        const NbrLane nl = load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
         int pA;
         mA = stage_angular<FAST>(nl, mA, s, a, &pA);
         if (nl.inR) {
