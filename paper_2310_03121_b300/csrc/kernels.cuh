@@ -94,6 +94,22 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
                      const __nv_bfloat16* G, const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e,
                      __nv_bfloat16* dG, bool backward, int* err_flag);
 
+// ---- serving batches (kernels_misc.cu): one molecule per request, its inputs
+// and result area in page-locked host memory that kernels address directly
+// (unified addressing), so that no host thread copies request data.
+struct MolRef {
+    const double* xyz;     // [n][3]
+    const int8_t* species; // [n]
+    float* F;              // [n][3] result
+    double* E;             // result
+};
+// Gathers the molecules' inputs into d_xyz / d_species at mol_start offsets.
+void launch_gather_batch(cudaStream_t st, int n_mols, const MolRef* refs, const int* mol_start, double* d_xyz,
+                         int8_t* d_species);
+// Scatters energies and forces back into the molecules' result areas.
+void launch_scatter_results(cudaStream_t st, int n_mols, const MolRef* refs, const int* mol_start, const double* d_E,
+                            const float* d_F);
+
 // ---- finalize (kernels_misc.cu)
 // Also ORs this evaluation's error flags (1 neighbor overflow, 2 AEV staging
 // overflow, 4 bad element code, 8 network kernel error) into *sticky when

@@ -47,7 +47,39 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
     for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) F[q] = (float)(scale * grad[q]);
 }
 
+// One block per molecule: contiguous copies between the molecule's host
+// block (read / written through its unified address) and the batch arrays.
+__global__ void k_gather_batch(const MolRef* __restrict__ refs, const int* __restrict__ mol_start,
+                               double* __restrict__ xyz, int8_t* __restrict__ species) {
+    const int m = blockIdx.x;
+    const MolRef r = refs[m];
+    const int a = mol_start[m], n = mol_start[m + 1] - a;
+    for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) xyz[3 * (size_t)a + q] = r.xyz[q];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) species[a + q] = r.species[q];
+}
+
+__global__ void k_scatter_results(const MolRef* __restrict__ refs, const int* __restrict__ mol_start,
+                                  const double* __restrict__ E, const float* __restrict__ F) {
+    const int m = blockIdx.x;
+    const MolRef r = refs[m];
+    const int a = mol_start[m], n = mol_start[m + 1] - a;
+    for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) r.F[q] = F[3 * (size_t)a + q];
+    if (threadIdx.x == 0) *r.E = E[m];
+}
+
 }  // namespace
+
+void launch_gather_batch(cudaStream_t st, int n_mols, const MolRef* refs, const int* mol_start, double* d_xyz,
+                         int8_t* d_species) {
+    if (n_mols <= 0) return;
+    MLP_LAUNCH("gather", st, k_gather_batch<<<n_mols, 128, 0, st>>>(refs, mol_start, d_xyz, d_species));
+}
+
+void launch_scatter_results(cudaStream_t st, int n_mols, const MolRef* refs, const int* mol_start, const double* d_E,
+                            const float* d_F) {
+    if (n_mols <= 0) return;
+    MLP_LAUNCH("scatter", st, k_scatter_results<<<n_mols, 128, 0, st>>>(refs, mol_start, d_E, d_F));
+}
 
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,

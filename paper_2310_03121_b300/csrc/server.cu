@@ -63,17 +63,49 @@ struct Request {
 };
 static_assert(sizeof(Request) % 8 == 0, "request header keeps the coordinates 8-byte aligned");
 
-// Free blocks per capacity class, in 8 shards picked by the calling thread,
-// so that concurrent clients rarely share a lock; blocks are never returned
-// to the system while the server lives (a serving process in steady state
-// allocates and page-faults no new memory).
+// Request blocks live in page-locked host slabs (the serving kernels read a
+// request's inputs and write its results through their unified addresses,
+// so no host thread copies request data). Free blocks are kept per capacity
+// class in 8 shards picked by the calling thread, so that concurrent clients
+// rarely share a lock; slabs are returned only when the server is destroyed
+// (a serving process in steady state allocates and page-faults no memory).
 struct RequestPool {
     static constexpr int kShards = 8;
+    static constexpr size_t kSlab = 8u << 20;
     struct alignas(64) Shard {
         std::mutex mu;
         std::vector<Request*> free_[32];
     };
     Shard shards[kShards];
+    std::mutex slab_mu;
+    std::vector<void*> slabs;
+    int device = 0;   // the server's device, current while a slab is allocated
+    char* cur = nullptr;
+    size_t left = 0;
+    void* carve(size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        std::lock_guard<std::mutex> lk(slab_mu);
+        if (bytes > left) {
+            const size_t sz = bytes > kSlab ? bytes : kSlab;
+            void* p = nullptr;
+            int prev = 0;
+            cudaGetDevice(&prev);
+            if (prev != device) cudaSetDevice(device);
+            const cudaError_t e = cudaHostAlloc(&p, sz, cudaHostAllocPortable);
+            if (prev != device) cudaSetDevice(prev);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            slabs.push_back(p);
+            cur = static_cast<char*>(p);
+            left = sz;
+        }
+        void* p = cur;
+        cur += bytes;
+        left -= bytes;
+        return p;
+    }
     static int shard_of_thread() {
         static thread_local int s = (int)(std::hash<std::thread::id>()(std::this_thread::get_id()) % kShards);
         return s;
@@ -91,7 +123,7 @@ struct RequestPool {
             }
         }
         if (!r) {
-            void* p = std::malloc(Request::bytes(cls));
+            void* p = carve(Request::bytes(cls));
             if (!p) return nullptr;
             r = new (p) Request();
         }
@@ -108,12 +140,7 @@ struct RequestPool {
         sh.free_[r->cls].push_back(r);
     }
     ~RequestPool() {
-        for (Shard& sh : shards)
-            for (auto& v : sh.free_)
-                for (Request* r : v) {
-                    r->~Request();
-                    std::free(r);
-                }
+        for (void* p : slabs) cudaFreeHost(p);
     }
 };
 
@@ -161,10 +188,11 @@ struct Slot {
     void* dev_block = nullptr;
     void* host_block = nullptr;
     int *d_mol_start = nullptr, *h_mol_start = nullptr;
-    int8_t *d_species = nullptr, *h_species = nullptr;
-    double *d_xyz = nullptr, *h_xyz = nullptr;
-    double *d_E = nullptr, *h_E = nullptr;
-    float *d_F = nullptr, *h_F = nullptr;
+    MolRef *d_refs = nullptr, *h_refs = nullptr;   // per molecule: its request's input and result areas
+    int8_t* d_species = nullptr;
+    double* d_xyz = nullptr;
+    double* d_E = nullptr;
+    float* d_F = nullptr;
     bool busy = false;
     size_t footprint = 0;
     int n_atoms = 0, n_mols = 0;
@@ -239,45 +267,51 @@ int slot_create(Slot& s, const mlp_server_opts& o) {
     int rc = workspace_create(s.ws, o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0);
     if (rc) return rc;
     const size_t A = o.max_batch_atoms, M = o.max_batch_mols;
-    const size_t io = al256(4 * (M + 1)) + al256(A) + al256(24 * A) + al256(8 * M) + al256(12 * A);
-    s.dev_block = dev_alloc(io);
+    const size_t dev = al256(4 * (M + 1)) + al256(sizeof(MolRef) * M) + al256(A) + al256(24 * A) + al256(8 * M) +
+                       al256(12 * A);
+    s.dev_block = dev_alloc(dev);
     if (!s.dev_block) return set_error(MLP_ENOMEM, "device allocation of a serving slot failed");
     cudaError_t e;
-    if ((e = cudaMallocHost(&s.host_block, io)) != cudaSuccess) return cuda_error(e, "cudaMallocHost(slot)");
+    const size_t host = al256(4 * (M + 1)) + al256(sizeof(MolRef) * M);
+    if ((e = cudaMallocHost(&s.host_block, host)) != cudaSuccess) return cuda_error(e, "cudaMallocHost(slot)");
     if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_error(e, "cudaStreamCreate");
     if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_error(e, "cudaEventCreate");
     char* d = static_cast<char*>(s.dev_block);
     char* h = static_cast<char*>(s.host_block);
-    auto carve = [&](size_t bytes, void** dp, void** hp) {
-        *dp = d;
-        *hp = h;
-        d += al256(bytes);
-        h += al256(bytes);
-    };
-    carve(4 * (M + 1), (void**)&s.d_mol_start, (void**)&s.h_mol_start);
-    carve(A, (void**)&s.d_species, (void**)&s.h_species);
-    carve(24 * A, (void**)&s.d_xyz, (void**)&s.h_xyz);
-    carve(8 * M, (void**)&s.d_E, (void**)&s.h_E);
-    carve(12 * A, (void**)&s.d_F, (void**)&s.h_F);
+    s.d_mol_start = reinterpret_cast<int*>(d);
+    s.h_mol_start = reinterpret_cast<int*>(h);
+    d += al256(4 * (M + 1));
+    h += al256(4 * (M + 1));
+    s.d_refs = reinterpret_cast<MolRef*>(d);
+    s.h_refs = reinterpret_cast<MolRef*>(h);
+    d += al256(sizeof(MolRef) * M);
+    s.d_species = reinterpret_cast<int8_t*>(d);
+    d += al256(A);
+    s.d_xyz = reinterpret_cast<double*>(d);
+    d += al256(24 * A);
+    s.d_E = reinterpret_cast<double*>(d);
+    d += al256(8 * M);
+    s.d_F = reinterpret_cast<float*>(d);
     return MLP_OK;
 }
 
 size_t slot_bytes(const mlp_server_opts& o) {
     const size_t A = o.max_batch_atoms, M = o.max_batch_mols;
     return workspace_bytes(o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0) +
-           al256(4 * (M + 1)) + al256(A) + al256(24 * A) + al256(8 * M) + al256(12 * A);
+           al256(4 * (M + 1)) + al256(sizeof(MolRef) * M) + al256(A) + al256(24 * A) + al256(8 * M) + al256(12 * A);
 }
 
-// Packs slot.reqs into the slot's staging and enqueues copies + evaluation.
+// Enqueues one batch: a table of the molecules' host blocks and offsets goes
+// to the device; a gather kernel reads the inputs from the blocks, the
+// evaluation runs, a scatter kernel writes energies and forces back.
 int launch_slot(mlp_server* S, Slot& s) {
     int off = 0;
     s.h_mol_start[0] = 0;
     for (size_t m = 0; m < s.reqs.size(); ++m) {
         Request* r = s.reqs[m];
-        std::memcpy(s.h_species + off, r->species(), r->n);
-        std::memcpy(s.h_xyz + 3 * (size_t)off, r->xyz(), 24 * (size_t)r->n);
+        s.h_refs[m] = MolRef{r->xyz(), r->species(), r->F(), &r->E};
         off += r->n;
         s.h_mol_start[m + 1] = off;
     }
@@ -285,8 +319,8 @@ int launch_slot(mlp_server* S, Slot& s) {
     s.n_mols = (int)s.reqs.size();
     cudaStream_t st = s.stream;
     cudaMemcpyAsync(s.d_mol_start, s.h_mol_start, 4 * (size_t)(s.n_mols + 1), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s.d_species, s.h_species, s.n_atoms, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s.d_xyz, s.h_xyz, 24 * (size_t)s.n_atoms, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s.d_refs, s.h_refs, sizeof(MolRef) * (size_t)s.n_mols, cudaMemcpyHostToDevice, st);
+    launch_gather_batch(st, s.n_mols, s.d_refs, s.d_mol_start, s.d_xyz, s.d_species);
     EvalSpec sp;
     sp.n_atoms = s.n_atoms;
     sp.n_mols = s.n_mols;
@@ -298,9 +332,10 @@ int launch_slot(mlp_server* S, Slot& s) {
     sp.d_F = s.d_F;
     int rc = enqueue_eval(s.ws, weights_of(S->w), sp, st);
     if (rc) return rc;
-    cudaMemcpyAsync(s.h_E, s.d_E, 8 * (size_t)s.n_mols, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(s.h_F, s.d_F, 12 * (size_t)s.n_atoms, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaEventRecord(s.done, st);
+    launch_scatter_results(st, s.n_mols, s.d_refs, s.d_mol_start, s.d_E, s.d_F);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "serving kernels");
+    e = cudaEventRecord(s.done, st);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     return MLP_OK;
 }
@@ -308,16 +343,11 @@ int launch_slot(mlp_server* S, Slot& s) {
 void finish_slot(mlp_server* S, Slot& s, int status) {
     if (status == MLP_OK) status = check_counters(s.ws);
     const int64_t t = now_ns();
-    // results go into the requests; a request is readable once marked done
+    // energies and forces are already in the requests (scatter kernel)
     std::vector<int64_t> lat;
     lat.reserve(s.reqs.size());
-    int off = 0;
-    for (size_t m = 0; m < s.reqs.size(); ++m) {
-        Request* r = s.reqs[m];
+    for (Request* r : s.reqs) {
         r->status = status;
-        r->E = s.h_E[m];
-        std::memcpy(r->F(), s.h_F + 3 * (size_t)off, 12 * (size_t)r->n);
-        off += r->n;
         lat.push_back(t - r->t_submit);
         r->done.store(true, std::memory_order_release);
     }
@@ -469,6 +499,7 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     S->o = o;
     S->w = w;
     cudaGetDevice(&S->device);
+    S->pool.device = S->device;
     S->bytes_per_atom = (sb + o.max_batch_atoms - 1) / o.max_batch_atoms;
     if (!S->init_tables()) {
         delete S;
