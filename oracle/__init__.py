@@ -14,7 +14,8 @@ Parity status per function (what pins it, from tests/test_oracle.py):
   oracle_pair_index ................. enumeration of the 28 unordered pairs
   oracle_neighbors .................. scipy.spatial.cKDTree on periodic/open boxes
   oracle_aev ........................ 2- and 3-atom special cases, invariances
-  oracle_atom_energy ................ torch Linear+CELU chain, single-path network
+  oracle_atom_energy ................ torch Linear+CELU chain, single-path network;
+                                      ensemble: K copies of one net, net-by-net means
   oracle_energy_forces .............. central finite differences, zero net force/torque
   oracle_forces_subset / local energy  equality with the full evaluation
 """
@@ -43,7 +44,8 @@ def build(force=False):
 
 
 class _Weights(ctypes.Structure):
-    _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")]
+    _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")] + \
+        [("nets", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -118,12 +120,24 @@ def _cell(cell):
 
 
 class Weights:
-    """FP64 weights for the oracle (dict from gen.make_weights, single net)."""
+    """FP64 weights for the oracle (dict from gen.make_weights).
+
+    A single net has W1[7,256,1008] ...; an ensemble of K nets carries a
+    leading [K] axis on every array, and the model is the mean of the K nets
+    (energy and dE/dG alike)."""
 
     def __init__(self, w):
         self.arrays = {k: _f64(w[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")}
-        assert self.arrays["W1"].shape == (7, 256, AEV_LEN)
-        self.struct = _Weights(*[_d(self.arrays[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")])
+        shp = self.arrays["W1"].shape
+        if shp == (7, 256, AEV_LEN):
+            self.nets = 1
+        else:
+            assert len(shp) == 4 and shp[1:] == (7, 256, AEV_LEN), shp
+            self.nets = shp[0]
+        for k, v in self.arrays.items():
+            assert v.shape[0] == self.nets or self.nets == 1, (k, v.shape)
+        self.struct = _Weights(*[_d(self.arrays[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")],
+                               self.nets)
 
     def ref(self):
         return ctypes.byref(self.struct)

@@ -27,6 +27,8 @@
  *             species pair (s_j, s_k) in the row-major upper triangle.
  *   network   e_i = w4 . celu(W3 celu(W2 celu(W1 G_i + b1) + b2) + b3) + b4
  *             with the weights of atom i's element, celu alpha = 0.1.
+ *   ensemble  with K nets per element (ANI-2x has eight), e_i is the mean of
+ *             the K nets' outputs (section "Performance of MLPs").
  *   energy    E = sum_i e_i;  forces F = -dE/dr (chain rule written out).
  *
  * Hyper-parameters: Rc_R = 5.1 A, 16 radial shifts R_k = linspace(0.8, 4.9),
@@ -71,6 +73,7 @@ static const double CELU_ALPHA = 0.1;
  * W3[7][160][192] b3[7][160] W4[7][160] b4[7]   (row = output unit) */
 typedef struct {
     const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;
+    int nets; /* ensemble size K; each array holds K nets back to back (0 reads as 1) */
 } oracle_weights;
 
 /* ------------------------------------------------------------ AEV pieces */
@@ -225,14 +228,16 @@ void oracle_aev(int n, const int *species, const double *xyz, const double *cell
 
 /* ------------------------------------------------------------ network */
 
-/* Energy of one atom of element s from its AEV; if dEdG != NULL, also the
- * gradient dE/dG (backpropagation through the four layers). */
-double oracle_atom_energy(int s, const double *G, const oracle_weights *w, double *dEdG)
+/* Energy of one atom of element s from its AEV under net k of the ensemble;
+ * if dEdG != NULL, also the gradient dE/dG (backpropagation through the four
+ * layers). */
+static double net_atom_energy(int s, const double *G, const oracle_weights *w, int k, double *dEdG)
 {
-    const double *W1 = w->W1 + (size_t)s * H1 * AEV_LEN, *b1 = w->b1 + s * H1;
-    const double *W2 = w->W2 + (size_t)s * H2 * H1, *b2 = w->b2 + s * H2;
-    const double *W3 = w->W3 + (size_t)s * H3 * H2, *b3 = w->b3 + s * H3;
-    const double *W4 = w->W4 + (size_t)s * H3, b4 = w->b4[s];
+    const size_t ks = (size_t)k * NSP + (size_t)s; /* (net, element) index */
+    const double *W1 = w->W1 + ks * H1 * AEV_LEN, *b1 = w->b1 + ks * H1;
+    const double *W2 = w->W2 + ks * H2 * H1, *b2 = w->b2 + ks * H2;
+    const double *W3 = w->W3 + ks * H3 * H2, *b3 = w->b3 + ks * H3;
+    const double *W4 = w->W4 + ks * H3, b4 = w->b4[ks];
     double z1[H1], h1[H1], z2[H2], h2[H2], z3[H3], h3[H3];
     for (int o = 0; o < H1; ++o) {
         double acc = b1[o];
@@ -274,6 +279,28 @@ double oracle_atom_energy(int s, const double *G, const oracle_weights *w, doubl
         }
     }
     return e;
+}
+
+/* Energy of one atom of element s from its AEV, and optionally dE/dG. With an
+ * ensemble of K independently trained nets the model is their average
+ * (section "Performance of MLPs", the ANI-2x ensemble of eight, Table 3): e is
+ * the mean of the K nets' energies and dE/dG the mean of their gradients, so
+ * the forces are the mean of the K nets' forces. K = 1 is the single model. */
+double oracle_atom_energy(int s, const double *G, const oracle_weights *w, double *dEdG)
+{
+    const int K = w->nets > 0 ? w->nets : 1;
+    if (K == 1) return net_atom_energy(s, G, w, 0, dEdG);
+    double gk[AEV_LEN];
+    double e = 0.0;
+    if (dEdG) memset(dEdG, 0, sizeof(double) * AEV_LEN);
+    for (int k = 0; k < K; ++k) {
+        e += net_atom_energy(s, G, w, k, dEdG ? gk : NULL);
+        if (dEdG)
+            for (int c = 0; c < AEV_LEN; ++c) dEdG[c] += gk[c];
+    }
+    if (dEdG)
+        for (int c = 0; c < AEV_LEN; ++c) dEdG[c] /= K;
+    return e / K;
 }
 
 /* ------------------------------------------------------------ forces */

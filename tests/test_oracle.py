@@ -218,6 +218,60 @@ def test_single_path_network_by_hand():
     assert oracle.atom_energy(0, G, Wz) == 0.0
 
 
+def _torch_net(w, k, s):
+    """Net k (of an ensemble dict with a leading [nets] axis), element s, as torch layers."""
+    net = torch.nn.Sequential(
+        torch.nn.Linear(1008, 256), torch.nn.CELU(0.1), torch.nn.Linear(256, 192), torch.nn.CELU(0.1),
+        torch.nn.Linear(192, 160), torch.nn.CELU(0.1), torch.nn.Linear(160, 1)).double()
+    with torch.no_grad():
+        for li, lay in enumerate([0, 2, 4, 6]):
+            Wt = w[f"W{li + 1}"][k, s]
+            net[lay].weight.copy_(torch.from_numpy(Wt if li < 3 else Wt[None, :]))
+            net[lay].bias.copy_(torch.from_numpy(np.atleast_1d(w[f"b{li + 1}"][k, s])))
+    return net
+
+
+@pytest.mark.parametrize("nets", [2, 8])
+def test_ensemble_is_mean_of_torch_nets(nets):
+    """Section "Performance of MLPs": the ANI-2x ensemble averages eight
+    independently trained models; energy and dE/dG are the means over nets."""
+    w = gen.make_weights(nets=nets)
+    We = oracle.Weights(w)
+    assert We.nets == nets
+    rng = np.random.default_rng(70 + nets)
+    for s in (0, 3, 6):
+        G = rng.uniform(0, 1.5, size=1008) * (rng.uniform(size=1008) < 0.3)
+        Gt = torch.tensor(G, requires_grad=True)
+        et = sum(_torch_net(w, k, s)(Gt)[0] for k in range(nets)) / nets
+        et.backward()
+        e, g = oracle.atom_energy(s, G, We, grad=True)
+        assert e == pytest.approx(et.item(), rel=1e-13, abs=1e-14)
+        np.testing.assert_allclose(g, Gt.grad.numpy(), rtol=0, atol=1e-8 * np.abs(g).max())
+
+
+def test_ensemble_single_path_by_hand():
+    """Two nets, each with one live path through element 2: e is the mean of
+    the two hand-computed outputs and so is dE/dG."""
+    z = {k: np.zeros_like(v) for k, v in gen.make_weights(nets=2).items()}
+    z["W1"][0, 2, 0, 5] = 2.0
+    z["W2"][0, 2, 0, 0] = 3.0
+    z["W3"][0, 2, 0, 0] = 0.5
+    z["W4"][0, 2, 0] = 1.5
+    z["b4"][0, 2] = 0.25        # net 0: 1.5 * (0.5 * 3 * 2 * 0.4) + 0.25 = 2.05
+    z["W1"][1, 2, 7, 9] = 1.0
+    z["W2"][1, 2, 4, 7] = 1.0
+    z["W3"][1, 2, 9, 4] = 1.0
+    z["W4"][1, 2, 9] = -2.0
+    z["b4"][1, 2] = 1.0         # net 1: -2 * 0.7 + 1 = -0.4
+    G = np.zeros(1008)
+    G[5], G[9] = 0.4, 0.7
+    e, g = oracle.atom_energy(2, G, oracle.Weights(z), grad=True)
+    assert e == pytest.approx((2.05 - 0.4) / 2, abs=1e-14)
+    assert g[5] == pytest.approx(1.5 * 0.5 * 3.0 * 2.0 / 2, abs=1e-13)
+    assert g[9] == pytest.approx(-2.0 / 2, abs=1e-13)
+    assert np.count_nonzero(g) == 2
+
+
 # ------------------------------------------------------------------ forces
 def _fd_forces(c, W, atoms, h):
     out = np.zeros((len(atoms), 3))
@@ -247,6 +301,16 @@ def test_forces_match_central_differences(W, n):
     assert np.abs(f4 - f5).max() <= 1e-6 * scale
     assert np.abs(F[atoms] - f4).max() <= 1e-6 * scale
     assert np.abs(F[atoms] - f5).max() <= 1e-6 * scale
+
+
+def test_ensemble_forces_match_central_differences():
+    We = oracle.Weights(gen.make_weights(nets=3))
+    c = gen.random_molecule(9, seed=5, density=0.3)
+    E, F = oracle.energy_forces(c.species, c.coords, c.cell, We)
+    atoms = [0, 4, 8]
+    fd = _fd_forces(c, We, atoms, 1e-4)
+    assert np.abs(F[atoms] - fd).max() <= 1e-6 * max(np.abs(F).max(), 1e-3)
+    assert np.abs(F.sum(0)).max() <= 1e-10 * max(np.abs(F).max(), 1.0)
 
 
 def test_forces_fd_periodic(W):
