@@ -47,6 +47,7 @@ WORKLOAD = ("served stream: 20,000 open-boundary molecules, N log-uniform in [8,
 # Algorithmic work per atom of each kernel (measurement section).
 MLP_FLOP_FWD = 2 * (1008 * 256 + 256 * 192 + 192 * 160 + 160)          # 676,160
 MLP_FLOP_BWD = 2 * (160 * 192 + 192 * 256 + 256 * 1008)                 # 675,840
+MLP_FLOP_B1 = 2 * 256 * 1008                                             # 516,096 (dE/dG = g1 W1)
 
 
 def _dist():
@@ -167,7 +168,7 @@ def run_reference(args):
     import gen
 
     stream = gen.served_stream(args.count)
-    wts = gen.make_weights()
+    wts = gen.make_weights(nets=args.nets)
     budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
     vals = []
     base = None
@@ -180,7 +181,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "bounded per-step sample, see cpu_baseline"},
+            "config": {"workload": WORKLOAD, "nets": args.nets, "sample": "bounded per-step sample, see cpu_baseline"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -188,28 +189,16 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure_device(P, W, stream, args, prec, dev, ws, local, steps, warmup, profile_steps):
+    """Device-resident served-stream steps: (ms per step, per-kernel profile,
+    launches in the timed steps, clocks, d_E, d_F). Every step packs the
+    stream into batches of at most max_batch_atoms atoms, run alternately on
+    two streams; L2 is flushed between timed steps."""
     import torch
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    import gen
-    import paper_2310_03121_b300 as P
-
-    prec = args.precision
-    stream = gen.served_stream(args.count)
-    wts = gen.make_weights()
-    W = P.Weights(wts)
     n_atoms = stream.n_atoms
     max_atoms, max_mols = args.max_batch_atoms, args.max_batch_mols
     chunks = pack_chunks(stream.mol_start, max_atoms, max_mols)
-
-    # device-resident inputs and outputs
     d_xyz = torch.from_numpy(stream.coords).to(dev)
     d_sp = torch.from_numpy(stream.species).to(dev)
     d_E = torch.zeros(stream.count, dtype=torch.float64, device=dev)
@@ -253,7 +242,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
         for b in batches:
             b.sync()
@@ -262,7 +251,7 @@ def run_ours(args):
     clk = Clocks(local)
     clk.start()
     times = []
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()                      # L2 flush between timed steps (outside the events)
         torch.cuda.synchronize()
         s_ev, e_ev = step()
@@ -277,7 +266,7 @@ def run_ours(args):
     # brackets exactly one kernel), CUDA events around every launch
     P.profile_reset()
     P.profile_enable(True)
-    for _ in range(args.profile_steps):
+    for _ in range(profile_steps):
         flush.zero_()
         torch.cuda.synchronize()
         step(one_stream=True)
@@ -293,6 +282,32 @@ def run_ours(args):
         t = torch.tensor([ms_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
+    return {"ms_step": ms_step, "prof": prof, "launches": launches, "clocks": clocks, "chunks": len(chunks),
+            "d_E": d_E, "d_F": d_F}
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import gen
+    import paper_2310_03121_b300 as P
+
+    prec = args.precision
+    stream = gen.served_stream(args.count)
+    wts = gen.make_weights(nets=args.nets)
+    W = P.Weights(wts)
+    n_atoms = stream.n_atoms
+    max_atoms, max_mols = args.max_batch_atoms, args.max_batch_mols
+    m = measure_device(P, W, stream, args, prec, dev, ws, local, args.steps, args.warmup, args.profile_steps)
+    ms_step, prof, launches, clocks = m["ms_step"], m["prof"], m["launches"], m["clocks"]
+    d_E, d_F = m["d_E"], m["d_F"]
     value = ws * n_atoms / (ms_step * 1e-3)
 
     # sanity: outputs finite
@@ -302,15 +317,31 @@ def run_ours(args):
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "bf16" if prec == "bf16" else "f32", "data": "synthetic",
               "config": {"workload": WORKLOAD, "precision": prec, "molecules": stream.count, "atoms": n_atoms,
-                         "batch_atoms": max_atoms, "batches_per_step": len(chunks), "streams": 2,
+                         "nets": args.nets, "batch_atoms": max_atoms, "batches_per_step": m["chunks"], "streams": 2,
                          "l2": "flushed between timed steps (256 MB write)",
                          "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
               "clocks": clocks, "gpu_launches": int(round(launches / max(1, args.steps)))}
     result["gpu_launches_timed_total"] = int(launches)
-    result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec, term_counts(stream))
+    terms = term_counts(stream)
+    result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec, terms, args.nets)
     result["kernels_ms_per_step"] = {k: v[0] / max(1, args.profile_steps) for k, v in sorted(prof.items())}
     result["kernels_timing"] = ("CUDA events around every launch, on the launching stream, in "
                                 f"{args.profile_steps} extra steps run on one stream after the timed steps")
+
+    # ---------------- the 8-net ensemble on the same stream (device-resident)
+    if args.ensemble_nets > 1 and args.nets == 1:
+        We = P.Weights(gen.make_weights(nets=args.ensemble_nets))
+        me = measure_device(P, We, stream, args, prec, dev, ws, local, args.steps, args.warmup, args.profile_steps)
+        assert torch.isfinite(me["d_E"]).all() and torch.isfinite(me["d_F"]).all()
+        result["ensemble"] = {
+            "nets": args.ensemble_nets, "value": ws * n_atoms / (me["ms_step"] * 1e-3), "unit": UNIT,
+            "ms_per_step": me["ms_step"], "clocks": me["clocks"],
+            "gpu_launches": int(round(me["launches"] / max(1, args.steps))),
+            "roofline": roofline(me["prof"], n_atoms, args.profile_steps, prec, terms, args.ensemble_nets),
+            "kernels_ms_per_step": {k: v[0] / max(1, args.profile_steps) for k, v in sorted(me["prof"].items())},
+            "what": "energy = mean of the nets' energies, forces = mean gradient; one AEV and one force pass, "
+                    "every net on each 128-row tile inside one network kernel"}
+        We.close()
 
     # ---------------- e2e through the server (host buffers), saturating arrivals
     if not args.no_e2e:
@@ -328,7 +359,7 @@ def run_ours(args):
                 walls.append(wall)
                 lat = lt
         wall = statistics.median(walls)
-        h2d = 24 * n_atoms + n_atoms + 4 * (stream.count + len(chunks))
+        h2d = 24 * n_atoms + n_atoms + 4 * (stream.count + m["chunks"])
         d2h = 12 * n_atoms + 8 * stream.count
         result["e2e"] = {"value": ws * n_atoms / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h, "wall_s": wall,
@@ -393,8 +424,8 @@ MEASURED_TRAFFIC = {
 }
 
 
-def measured_traffic(name, atoms_per_launch):
-    m = MEASURED_TRAFFIC.get(name)
+def measured_traffic(name, atoms_per_launch, nets=1):
+    m = MEASURED_TRAFFIC.get(name if nets == 1 else f"{name}@{nets}")
     if not m:
         return None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2310_03121_b300", "csrc", m["file"])
@@ -407,7 +438,7 @@ def measured_traffic(name, atoms_per_launch):
     return m["bytes_per_atom"] * atoms_per_launch
 
 
-def roofline(prof, n_atoms, steps, prec, terms):
+def roofline(prof, n_atoms, steps, prec, terms, nets=1):
     peaks, src = measured_peaks()
     if not prof:
         return None
@@ -419,11 +450,30 @@ def roofline(prof, n_atoms, steps, prec, terms):
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
     nrad, npair = terms
     base = {"kernel": name, "launch_ms": avg_ms, "units_per_launch": atoms_per_launch,
-            "traffic": measured_traffic(name, atoms_per_launch)}
+            "traffic": measured_traffic(name, atoms_per_launch, nets)}
     if name.startswith("mlp_tc"):
-        per_atom = (3 * MLP_FLOP_FWD if prec == "bf16" else MLP_FLOP_FWD) + MLP_FLOP_BWD
-        ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
+        fwd = 3 * MLP_FLOP_FWD if prec == "bf16" else MLP_FLOP_FWD
+        per_atom = nets * (fwd + MLP_FLOP_BWD)
+        if "mlp_tc_b1_ens" in prof:
+            # ensemble: the network kernel stops at g1, the last backward layer
+            # of every net is one GEMM in mlp_tc_b1_ens; the pair is the network
+            b_ms, b_cnt = prof["mlp_tc_b1_ens"]
+            b_avg = b_ms / max(1, b_cnt)
+            tc_atom = nets * (fwd + MLP_FLOP_BWD - MLP_FLOP_B1)
+            b1_atom = nets * MLP_FLOP_B1
+            ach = per_atom * atoms_per_launch / ((avg_ms + b_avg) * 1e-3) / 1e12
+            base.update({"kernel": "mlp_tc + mlp_tc_b1_ens", "launch_ms": avg_ms + b_avg,
+                         "traffic": (None if base["traffic"] is None or measured_traffic("mlp_tc_b1_ens", 1, nets)
+                                     is None else base["traffic"] +
+                                     measured_traffic("mlp_tc_b1_ens", atoms_per_launch, nets)),
+                         "parts": {
+                             "mlp_tc": {"launch_ms": avg_ms, "work": f"{tc_atom} FLOP per atom",
+                                        "frac": tc_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12 / peak},
+                             "mlp_tc_b1_ens": {"launch_ms": b_avg, "work": f"{b1_atom} FLOP per atom",
+                                               "frac": b1_atom * atoms_per_launch / (b_avg * 1e-3) / 1e12 / peak}}})
+        else:
+            ach = per_atom * atoms_per_launch / (avg_ms * 1e-3) / 1e12
         base.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                      "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside a long step",
                      "work": f"{per_atom} FLOP per atom"})
@@ -431,7 +481,7 @@ def roofline(prof, n_atoms, steps, prec, terms):
     if name.startswith("mlp_f32"):
         layer_flop = {"mlp_f32_l1": 2 * 1008 * 256, "mlp_f32_l2": 2 * 256 * 192, "mlp_f32_l3": 2 * 192 * 160,
                       "mlp_f32_b3": 2 * 160 * 192, "mlp_f32_b2": 2 * 192 * 256, "mlp_f32_b1": 2 * 256 * 1008}
-        per_atom = layer_flop.get(name, 0)
+        per_atom = nets * layer_flop.get(name, 0)
     elif name == "forces":
         per_atom = FLOP_FORCE_PER_NEIGHBOR * nrad + FLOP_FORCE_PER_PAIR * npair
     elif name == "aev":
@@ -502,6 +552,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nets", type=int, default=1, help="ensemble size of the headline measurement")
+    ap.add_argument("--ensemble-nets", type=int, default=8,
+                    help="also time an ensemble of this many nets on the same stream (<= 1: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -108,8 +108,12 @@ typedef struct {
 /* ------------------------------------------------------------------ weights */
 
 /* Uploads the weights to the current device in FP32 and BF16 with the
- * transposed copies the backward needs. n_nets in [1, 8]. Returns
- * MLP_EINVAL on NULL arrays or n_nets out of range, MLP_ENOMEM, MLP_ECUDA. */
+ * transposed copies the backward needs. n_nets in [1, 8]. With n_nets = K > 1
+ * every evaluation made with these weights is the ensemble model: each atom's
+ * energy is the mean of the K nets' outputs and dE/dG the mean of their
+ * gradients, so energies and forces are the means over the K nets (one AEV,
+ * K network passes). Returns MLP_EINVAL on NULL arrays, a non-finite W1 entry
+ * or n_nets out of range, MLP_ENOMEM, MLP_ECUDA. */
 MLP_API int mlp_weights_create(const mlp_weights_host *w, int n_nets, mlp_weights **out);
 MLP_API void mlp_weights_destroy(mlp_weights *w);
 

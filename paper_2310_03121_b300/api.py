@@ -50,13 +50,20 @@ class Weights:
     """Per-element network weights on the device (mlp_weights_create).
 
     `w` is a dict of arrays W1[7,256,1008] b1[7,256] W2[7,192,256] b2[7,192]
-    W3[7,160,192] b3[7,160] W4[7,160] b4[7] (a leading [nets] axis for an
-    ensemble with n_nets > 1)."""
+    W3[7,160,192] b3[7,160] W4[7,160] b4[7], or with a leading [K] axis an
+    ensemble of K <= 8 nets whose mean is the model (n_nets is taken from
+    the arrays when not given)."""
 
-    def __init__(self, w, n_nets=1):
+    def __init__(self, w, n_nets=None):
         L = load()
         self._arrays = {k: np.ascontiguousarray(w[k], dtype=np.float32) for k in
                         ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")}
+        shp = self._arrays["W1"].shape
+        inferred = shp[0] if len(shp) == 4 else 1
+        if n_nets is None:
+            n_nets = inferred
+        if n_nets != inferred or shp[-3:] != (7, 256, 1008):
+            raise ValueError(f"W1 of shape {shp} does not hold {n_nets} net(s) of [7, 256, 1008]")
         host = _lib.WeightsHost(*[_ptr(self._arrays[k], ctypes.c_float) for k in
                                   ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")])
         h = ctypes.c_void_p()

@@ -124,7 +124,7 @@ int sys_make_workspace(mlp_system* s, int nbr_cap) {
     // open systems: at most ~2 cells per atom plus slack
     int max_cells = s->periodic ? make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin)).ncell
                                 : (s->n * 2 + 64);
-    int rc = workspace_create(s->ws, s->n, 1, s->precision, true, nbr_cap, max_cells);
+    int rc = workspace_create(s->ws, s->n, 1, s->precision, true, nbr_cap, max_cells, s->w->dw.n_nets);
     if (rc) return rc;
     if (s->periodic) {
         Grid g = make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin));
@@ -198,150 +198,135 @@ int mlp_weights_create(const mlp_weights_host* w, int n_nets, mlp_weights** out)
     int rc = check_cuda_device();
     if (rc) return rc;
     const int S = kNSpecies;
-    // per-net sizes (floats)
+    const size_t K = (size_t)n_nets;
+    // per-net sizes (elements)
     const size_t nW1 = (size_t)S * kH1 * kAevLen, nb1 = S * kH1, nW2 = (size_t)S * kH2 * kH1, nb2 = S * kH2,
                  nW3 = (size_t)S * kH3 * kH2, nb3 = S * kH3, nW4 = S * kH3, nb4 = S;
-    // FP32 block: W1 b1 W2 b2 W3 b3 W4 b4 W1t W2t W3t per net
-    size_t f32_per_net = al256(nW1 * 4) + al256(nb1 * 4) + al256(nW2 * 4) + al256(nb2 * 4) + al256(nW3 * 4) +
-                         al256(nb3 * 4) + al256(nW4 * 4) + al256(nb4 * 4) + al256(nW1 * 4) + al256(nW2 * 4) +
-                         al256(nW3 * 4);
     const size_t nW1p = (size_t)S * kH1 * kAevLd;   // padded K for the BF16 operands
-    size_t bf_per_net = 2 * (al256(nW1p * 2) + al256(nW2 * 2) + al256(nW3 * 2)) + al256(nW1p * 2) +
-                        al256(nW2 * 2) + al256(nW3 * 2);
+    for (size_t q = 0; q < nW1 * K; ++q)
+        if (!std::isfinite(w->W1[q])) return set_error(MLP_EINVAL, "non-finite weight in W1");
+    // Every array holds the K nets back to back ("net-major"), so that net k
+    // of element s is block k * 7 + s of one matrix: one TMA map per weight
+    // matrix covers the whole ensemble.
+    // FP32 block: W1 b1 W2 b2 W3 b3 W4 b4 W1t W2t W3t
+    const size_t f32_cnt[11] = {nW1, nb1, nW2, nb2, nW3, nb3, nW4, nb4, nW1, nW2, nW3};
+    size_t f32_off[11], f32_bytes = 0;
+    for (int q = 0; q < 11; ++q) {
+        f32_off[q] = f32_bytes;
+        f32_bytes += al256(f32_cnt[q] * K * 4);
+    }
+    // BF16 block: W1 W2 W3 W1t W2t W3t W1lo W2lo W3lo (W1 K padded to 1024, W1t rows >= 1008 zero)
+    const size_t bf_cnt[9] = {nW1p, nW2, nW3, nW1p, nW2, nW3, nW1p, nW2, nW3};
+    size_t bf_off[9], bf_bytes = 0;
+    for (int q = 0; q < 9; ++q) {
+        bf_off[q] = bf_bytes;
+        bf_bytes += al256(bf_cnt[q] * K * 2);
+    }
     mlp_weights* mw = new (std::nothrow) mlp_weights();
     if (!mw) return set_error(MLP_ENOMEM, "host allocation failed");
     mw->dw.n_nets = n_nets;
     cudaGetDevice(&mw->dw.device);
-    mw->dw.blk_f32 = dev_alloc(f32_per_net * n_nets);
-    mw->dw.blk_bf16 = dev_alloc(bf_per_net * n_nets);
+    mw->dw.blk_f32 = dev_alloc(f32_bytes);
+    mw->dw.blk_bf16 = dev_alloc(bf_bytes);
     if (!mw->dw.blk_f32 || !mw->dw.blk_bf16) {
         mlp_weights_destroy(mw);
         return set_error(MLP_ENOMEM, "device allocation of the weights failed");
     }
-    std::vector<char> hf(f32_per_net), hb(bf_per_net);
-    for (int net = 0; net < n_nets; ++net) {
+    std::vector<char> hf(f32_bytes, 0), hb(bf_bytes, 0);
+    auto F = [&](int q, size_t net) { return reinterpret_cast<float*>(hf.data() + f32_off[q]) + net * f32_cnt[q]; };
+    auto B = [&](int q, size_t net) {
+        return reinterpret_cast<__nv_bfloat16*>(hb.data() + bf_off[q]) + net * bf_cnt[q];
+    };
+    // remainder after BF16 rounding, itself rounded to BF16
+    auto lo_of = [](float x) { return to_bf16(x - __bfloat162float(to_bf16(x))); };
+    for (size_t net = 0; net < K; ++net) {
         const float* W1 = w->W1 + net * nW1;
-        const float* b1 = w->b1 + net * nb1;
         const float* W2 = w->W2 + net * nW2;
-        const float* b2 = w->b2 + net * nb2;
         const float* W3 = w->W3 + net * nW3;
-        const float* b3 = w->b3 + net * nb3;
-        const float* W4 = w->W4 + net * nW4;
-        const float* b4 = w->b4 + net * nb4;
-        for (size_t q = 0; q < nW1; ++q)
-            if (!std::isfinite(W1[q])) {
-                mlp_weights_destroy(mw);
-                return set_error(MLP_EINVAL, "non-finite weight in W1");
-            }
-        // FP32 layout
-        std::memset(hf.data(), 0, hf.size());
-        size_t off = 0;
-        auto put = [&](const float* src, size_t cnt) {
-            float* dst = reinterpret_cast<float*>(hf.data() + off);
-            if (src) std::memcpy(dst, src, cnt * 4);
-            size_t o = off;
-            off += al256(cnt * 4);
-            return o;
-        };
-        size_t oW1 = put(W1, nW1), ob1 = put(b1, nb1), oW2 = put(W2, nW2), ob2 = put(b2, nb2), oW3 = put(W3, nW3),
-               ob3 = put(b3, nb3), oW4 = put(W4, nW4), ob4 = put(b4, nb4);
-        size_t oW1t = put(nullptr, nW1), oW2t = put(nullptr, nW2), oW3t = put(nullptr, nW3);
-        float* W1t = reinterpret_cast<float*>(hf.data() + oW1t);
-        float* W2t = reinterpret_cast<float*>(hf.data() + oW2t);
-        float* W3t = reinterpret_cast<float*>(hf.data() + oW3t);
-        for (int s = 0; s < S; ++s) {
-            for (int o = 0; o < kH1; ++o)
-                for (int c = 0; c < kAevLen; ++c)
-                    W1t[(size_t)s * kAevLen * kH1 + (size_t)c * kH1 + o] = W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c];
-            for (int o = 0; o < kH2; ++o)
-                for (int c = 0; c < kH1; ++c) W2t[(size_t)s * kH1 * kH2 + c * kH2 + o] = W2[(size_t)s * kH2 * kH1 + o * kH1 + c];
-            for (int o = 0; o < kH3; ++o)
-                for (int c = 0; c < kH2; ++c) W3t[(size_t)s * kH2 * kH3 + c * kH3 + o] = W3[(size_t)s * kH3 * kH2 + o * kH2 + c];
-        }
-        char* dbase = static_cast<char*>(mw->dw.blk_f32) + net * f32_per_net;
-        cudaError_t e = cudaMemcpy(dbase, hf.data(), f32_per_net, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            mlp_weights_destroy(mw);
-            return cuda_error(e, "cudaMemcpy(weights)");
-        }
-        NetF32& nf = mw->dw.f32[net];
-        nf.W1 = reinterpret_cast<const float*>(dbase + oW1);
-        nf.b1 = reinterpret_cast<const float*>(dbase + ob1);
-        nf.W2 = reinterpret_cast<const float*>(dbase + oW2);
-        nf.b2 = reinterpret_cast<const float*>(dbase + ob2);
-        nf.W3 = reinterpret_cast<const float*>(dbase + oW3);
-        nf.b3 = reinterpret_cast<const float*>(dbase + ob3);
-        nf.W4 = reinterpret_cast<const float*>(dbase + oW4);
-        nf.b4 = reinterpret_cast<const float*>(dbase + ob4);
-        nf.W1t = reinterpret_cast<const float*>(dbase + oW1t);
-        nf.W2t = reinterpret_cast<const float*>(dbase + oW2t);
-        nf.W3t = reinterpret_cast<const float*>(dbase + oW3t);
-        // BF16 layout: W1 [7][256][1024] (K padded with zeros), W2, W3, and the
-        // transposes W1t [7][1024][256] (rows >= 1008 zero), W2t, W3t
-        std::memset(hb.data(), 0, hb.size());
-        size_t boff = 0;
-        auto bput = [&](size_t cnt) {
-            size_t o = boff;
-            boff += al256(cnt * 2);
-            return o;
-        };
-        size_t bW1 = bput(nW1p), bW2 = bput(nW2), bW3 = bput(nW3), bW1t = bput(nW1p), bW2t = bput(nW2),
-               bW3t = bput(nW3);
-        size_t bW1lo = bput(nW1p), bW2lo = bput(nW2), bW3lo = bput(nW3);
-        // remainder after BF16 rounding, itself rounded to BF16
-        auto lo_of = [](float x) { return to_bf16(x - __bfloat162float(to_bf16(x))); };
-        auto B = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(hb.data() + o); };
+        std::memcpy(F(0, net), W1, nW1 * 4);
+        std::memcpy(F(1, net), w->b1 + net * nb1, nb1 * 4);
+        std::memcpy(F(2, net), W2, nW2 * 4);
+        std::memcpy(F(3, net), w->b2 + net * nb2, nb2 * 4);
+        std::memcpy(F(4, net), W3, nW3 * 4);
+        std::memcpy(F(5, net), w->b3 + net * nb3, nb3 * 4);
+        std::memcpy(F(6, net), w->W4 + net * nW4, nW4 * 4);
+        std::memcpy(F(7, net), w->b4 + net * nb4, nb4 * 4);
+        float *W1t = F(8, net), *W2t = F(9, net), *W3t = F(10, net);
+        __nv_bfloat16 *bW1 = B(0, net), *bW2 = B(1, net), *bW3 = B(2, net), *bW1t = B(3, net), *bW2t = B(4, net),
+                      *bW3t = B(5, net), *bW1lo = B(6, net), *bW2lo = B(7, net), *bW3lo = B(8, net);
         for (int s = 0; s < S; ++s) {
             for (int o = 0; o < kH1; ++o)
                 for (int c = 0; c < kAevLen; ++c) {
                     const float x = W1[(size_t)s * kH1 * kAevLen + (size_t)o * kAevLen + c];
-                    __nv_bfloat16 v = to_bf16(x);
-                    B(bW1)[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = v;
-                    B(bW1lo)[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = lo_of(x);
-                    B(bW1t)[(size_t)s * kAevLd * kH1 + (size_t)c * kH1 + o] = v;
+                    const __nv_bfloat16 v = to_bf16(x);
+                    W1t[(size_t)s * kAevLen * kH1 + (size_t)c * kH1 + o] = x;
+                    bW1[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = v;
+                    bW1lo[(size_t)s * kH1 * kAevLd + (size_t)o * kAevLd + c] = lo_of(x);
+                    bW1t[(size_t)s * kAevLd * kH1 + (size_t)c * kH1 + o] = v;
                 }
             for (int o = 0; o < kH2; ++o)
                 for (int c = 0; c < kH1; ++c) {
                     const float x = W2[(size_t)s * kH2 * kH1 + o * kH1 + c];
-                    __nv_bfloat16 v = to_bf16(x);
-                    B(bW2)[(size_t)s * kH2 * kH1 + o * kH1 + c] = v;
-                    B(bW2lo)[(size_t)s * kH2 * kH1 + o * kH1 + c] = lo_of(x);
-                    B(bW2t)[(size_t)s * kH1 * kH2 + c * kH2 + o] = v;
+                    const __nv_bfloat16 v = to_bf16(x);
+                    W2t[(size_t)s * kH1 * kH2 + c * kH2 + o] = x;
+                    bW2[(size_t)s * kH2 * kH1 + o * kH1 + c] = v;
+                    bW2lo[(size_t)s * kH2 * kH1 + o * kH1 + c] = lo_of(x);
+                    bW2t[(size_t)s * kH1 * kH2 + c * kH2 + o] = v;
                 }
             for (int o = 0; o < kH3; ++o)
                 for (int c = 0; c < kH2; ++c) {
                     const float x = W3[(size_t)s * kH3 * kH2 + o * kH2 + c];
-                    __nv_bfloat16 v = to_bf16(x);
-                    B(bW3)[(size_t)s * kH3 * kH2 + o * kH2 + c] = v;
-                    B(bW3lo)[(size_t)s * kH3 * kH2 + o * kH2 + c] = lo_of(x);
-                    B(bW3t)[(size_t)s * kH2 * kH3 + c * kH3 + o] = v;
+                    const __nv_bfloat16 v = to_bf16(x);
+                    W3t[(size_t)s * kH2 * kH3 + c * kH3 + o] = x;
+                    bW3[(size_t)s * kH3 * kH2 + o * kH2 + c] = v;
+                    bW3lo[(size_t)s * kH3 * kH2 + o * kH2 + c] = lo_of(x);
+                    bW3t[(size_t)s * kH2 * kH3 + c * kH3 + o] = v;
                 }
         }
-        char* bbase = static_cast<char*>(mw->dw.blk_bf16) + net * bf_per_net;
-        e = cudaMemcpy(bbase, hb.data(), bf_per_net, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            mlp_weights_destroy(mw);
-            return cuda_error(e, "cudaMemcpy(weights bf16)");
-        }
-        NetBF16& nb = mw->dw.bf16[net];
-        nb.W1 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1);
-        nb.W2 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2);
-        nb.W3 = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3);
-        nb.W1t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1t);
-        nb.W2t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2t);
-        nb.W3t = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3t);
-        nb.W1lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW1lo);
-        nb.W2lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW2lo);
-        nb.W3lo = reinterpret_cast<const __nv_bfloat16*>(bbase + bW3lo);
-        nb.b1 = nf.b1;
-        nb.b2 = nf.b2;
-        nb.b3 = nf.b3;
-        nb.W4 = nf.W4;
-        nb.b4 = nf.b4;
-        if (!make_weight_maps(nb)) {
-            mlp_weights_destroy(mw);
-            return set_error(MLP_ECUDA, "TMA tensor map creation for the weights failed");
-        }
+    }
+    cudaError_t e = cudaMemcpy(mw->dw.blk_f32, hf.data(), f32_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(mw->dw.blk_bf16, hb.data(), bf_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mlp_weights_destroy(mw);
+        return cuda_error(e, "cudaMemcpy(weights)");
+    }
+    const char* df = static_cast<const char*>(mw->dw.blk_f32);
+    const char* db = static_cast<const char*>(mw->dw.blk_bf16);
+    auto DF = [&](int q, size_t net) { return reinterpret_cast<const float*>(df + f32_off[q]) + net * f32_cnt[q]; };
+    auto DB = [&](int q) { return reinterpret_cast<const __nv_bfloat16*>(db + bf_off[q]); };
+    for (size_t net = 0; net < K; ++net) {
+        NetF32& nf = mw->dw.f32[net];
+        nf.W1 = DF(0, net);
+        nf.b1 = DF(1, net);
+        nf.W2 = DF(2, net);
+        nf.b2 = DF(3, net);
+        nf.W3 = DF(4, net);
+        nf.b3 = DF(5, net);
+        nf.W4 = DF(6, net);
+        nf.b4 = DF(7, net);
+        nf.W1t = DF(8, net);
+        nf.W2t = DF(9, net);
+        nf.W3t = DF(10, net);
+    }
+    NetBF16& nb = mw->dw.bf16;
+    nb.n_nets = n_nets;
+    nb.W1 = DB(0);
+    nb.W2 = DB(1);
+    nb.W3 = DB(2);
+    nb.W1t = DB(3);
+    nb.W2t = DB(4);
+    nb.W3t = DB(5);
+    nb.W1lo = DB(6);
+    nb.W2lo = DB(7);
+    nb.W3lo = DB(8);
+    nb.b1 = DF(1, 0);
+    nb.b2 = DF(3, 0);
+    nb.b3 = DF(5, 0);
+    nb.W4 = DF(6, 0);
+    nb.b4 = DF(7, 0);
+    if (!make_weight_maps(nb)) {
+        mlp_weights_destroy(mw);
+        return set_error(MLP_ECUDA, "TMA tensor map creation for the weights failed");
     }
     *out = mw;
     return MLP_OK;
@@ -550,7 +535,7 @@ int mlp_batch_create(const mlp_weights* w, int precision, int32_t max_atoms, int
     b->precision = precision;
     b->max_atoms_per_mol = max_atoms_per_mol;
     b->w = w;
-    rc = workspace_create(b->ws, max_atoms, max_mols, precision, false, kDefaultNbrCap, 0);
+    rc = workspace_create(b->ws, max_atoms, max_mols, precision, false, kDefaultNbrCap, 0, w->dw.n_nets);
     if (rc) {
         mlp_batch_destroy(b);
         return rc;
@@ -789,7 +774,7 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
     int rc = check_cuda_device();
     if (rc) return rc;
     Workspace ws;
-    rc = workspace_create(ws, n, 1, precision, false, 1, 0);
+    rc = workspace_create(ws, n, 1, precision, false, 1, 0, w->dw.n_nets);
     if (rc) return rc;
     // element-grouped rows: stable order inside each element
     Counters c;
@@ -820,7 +805,9 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         std::vector<float> all(R * kAevLd, 0.f);
         for (int i = 0; i < n; ++i) std::memcpy(&all[(size_t)rows[i] * kAevLd], G + (size_t)i * kAevLen, 4 * kAevLen);
         cudaMemcpy(ws.G32, all.data(), 4 * all.size(), cudaMemcpyHostToDevice);
-        launch_mlp_f32(nullptr, ws.rows_cap, ws.ctr, w->dw.f32[0], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG, true);
+        for (int k = 0; k < w->dw.n_nets; ++k)
+            launch_mlp_f32(nullptr, ws.rows_cap, ws.ctr, w->dw.f32[k], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG, true,
+                           k, w->dw.n_nets);
     } else {
         std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f)), all_lo(R * kAevLd, to_bf16(0.f));
         for (int i = 0; i < n; ++i)
@@ -831,8 +818,8 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
             }
         cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
         if (ws.G16lo) cudaMemcpy(ws.G16lo, all_lo.data(), 2 * all_lo.size(), cudaMemcpyHostToDevice);
-        if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16[0], ws.G16, ws.G16lo, precision == MLP_BF16,
-                             ws.row_atom, ws.e, ws.dG16, true, ws.tc_err)) {
+        if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16, ws.G16, ws.G16lo, precision == MLP_BF16,
+                             ws.row_atom, ws.e, ws.dG16, ws.g1ens, true, ws.tc_err)) {
             workspace_destroy(ws);
             return MLP_ECUDA;
         }

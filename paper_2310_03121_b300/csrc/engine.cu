@@ -74,10 +74,12 @@ void plan_workspace(Plan& P, Workspace& ws) {
     P.add(&ws.ctr, 1);
     P.add(&ws.grad, 3 * n);
     P.add(&ws.e, n);
-    if (ws.precision == 0)
+    if (ws.precision == 0) {
         P.add(&ws.dG, R * kAevLd);
-    else
+    } else {
         P.add(&ws.dG16, R * kAevLd);
+        if (ws.nets > 1) P.add(&ws.g1ens, R * (size_t)ws.nets * kH1);
+    }
     P.add(&ws.tc_err, 4);
     P.add(&ws.err_sticky, 4);
     if (ws.precision == 0) {
@@ -105,8 +107,10 @@ void plan_workspace(Plan& P, Workspace& ws) {
 }
 }  // namespace
 
-size_t workspace_bytes(int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap, int max_cells) {
+size_t workspace_bytes(int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap, int max_cells,
+                       int nets) {
     Workspace ws;
+    ws.nets = nets;
     ws.cap_atoms = cap_atoms;
     ws.cap_mols = cap_mols;
     ws.rows_cap = rows_capacity(cap_atoms);
@@ -120,8 +124,9 @@ size_t workspace_bytes(int cap_atoms, int cap_mols, int precision, bool cell_pat
 }
 
 int workspace_create(Workspace& ws, int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap,
-                     int max_cells) {
+                     int max_cells, int nets) {
     ws = Workspace();
+    ws.nets = nets;
     ws.cap_atoms = cap_atoms;
     ws.cap_mols = cap_mols;
     ws.rows_cap = rows_capacity(cap_atoms);
@@ -208,13 +213,17 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
             launch_aev_bf16(st, aa, ws.G16, ws.G16lo, ws.row_atom, fast);
     }
 
+    if (w.n_nets != ws.nets)
+        return set_error(-1, "weights hold %d nets, the workspace was sized for %d", w.n_nets, ws.nets);
     if (ws.precision == 0) {
-        launch_mlp_f32(st, ws.rows_cap, ws.ctr, w.f32[0], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG,
-                       sp.network_backward);
+        // ensemble: one pass per net, each adding its share of the mean
+        for (int k = 0; k < w.n_nets; ++k)
+            launch_mlp_f32(st, ws.rows_cap, ws.ctr, w.f32[k], ws.G32, ws.row_atom, ws.fb, ws.e, ws.dG,
+                           sp.network_backward, k, w.n_nets);
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
-        if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16[0], ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
-                             ws.e, ws.dG16, sp.network_backward, &ws.ctr->net_error))
+        if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16, ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
+                             ws.e, ws.dG16, ws.g1ens, sp.network_backward, &ws.ctr->net_error))
             return -5;
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.dG16, ws.grad, fast);

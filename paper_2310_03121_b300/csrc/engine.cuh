@@ -40,8 +40,8 @@ struct DevWeights {
     int device = 0;
     void* blk_f32 = nullptr;
     void* blk_bf16 = nullptr;
-    NetF32 f32[kMaxNets];
-    NetBF16 bf16[kMaxNets];
+    NetF32 f32[kMaxNets];   // net k
+    NetBF16 bf16;           // all nets
 };
 
 // precision: 0 = FP32 network, 1 = BF16 tensor cores with split-precision
@@ -49,6 +49,7 @@ struct DevWeights {
 struct Workspace {
     int cap_atoms = 0, cap_mols = 0, rows_cap = 0, nbr_cap = 0, max_cells = 0;
     int precision = 0;
+    int nets = 1;   // ensemble size of the weights it serves
     bool cell_path = false;
     size_t bytes = 0;
     std::vector<void*> owned;
@@ -62,6 +63,7 @@ struct Workspace {
     __nv_bfloat16* G16lo = nullptr;   // split-precision network only
     float* dG = nullptr;              // FP32 network
     __nv_bfloat16* dG16 = nullptr;    // BF16 networks
+    __nv_bfloat16* g1ens = nullptr;   // BF16 ensemble: every net's g1, [rows][nets * 256]
     MlpF32Bufs fb{};
     float* e = nullptr;
     Grid* grid = nullptr;
@@ -73,9 +75,10 @@ struct Workspace {
 };
 
 // Bytes a workspace of these dimensions occupies on the device.
-size_t workspace_bytes(int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap, int max_cells);
+size_t workspace_bytes(int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap, int max_cells,
+                       int nets);
 int workspace_create(Workspace& ws, int cap_atoms, int cap_mols, int precision, bool cell_path, int nbr_cap,
-                     int max_cells);
+                     int max_cells, int nets);
 void workspace_destroy(Workspace& ws);
 
 struct EvalSpec {

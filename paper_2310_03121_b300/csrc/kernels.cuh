@@ -73,15 +73,22 @@ struct NetF32 {   // device pointers, element-major, one net
 struct MlpF32Bufs {
     float *Z1, *H1, *Z2, *H2, *H3, *G3, *G2, *G1;   // [rows][256|192|160]
 };
+// Net `net` of an ensemble of `nets`: writes e and dE/dG scaled by 1 / nets
+// when net == 0 and adds them (scaled) otherwise, so that after nets
+// launches e and dE/dG hold the ensemble means.
 void launch_mlp_f32(cudaStream_t st, int rows_cap, const Counters* ctr, const NetF32& w, const float* G,
-                    const int* row_atom, MlpF32Bufs& b, float* e, float* dG, bool backward);
+                    const int* row_atom, MlpF32Bufs& b, float* e, float* dG, bool backward, int net = 0,
+                    int nets = 1);
 
 // ---- network, BF16 tcgen05 path (kernels_mlp_tc.cu)
+// All nets of the ensemble: every array holds the nets back to back, so
+// that block k * 7 + s of a matrix (or bias vector) is net k, element s.
 struct NetBF16 {
-    const __nv_bfloat16 *W1, *W2, *W3;       // [7][256][1024], [7][192][256], [7][160][192]
+    int n_nets;
+    const __nv_bfloat16 *W1, *W2, *W3;       // [K][7][256][1024], [K][7][192][256], [K][7][160][192]
     const __nv_bfloat16 *W1lo, *W2lo, *W3lo; // BF16 remainders W - W_hi of the forward weights
-    const __nv_bfloat16 *W1t, *W2t, *W3t;    // [7][1024][256], [7][256][192], [7][192][160]
-    const float *b1, *b2, *b3, *W4, *b4;
+    const __nv_bfloat16 *W1t, *W2t, *W3t;    // [K][7][1024][256], [K][7][256][192], [K][7][192][160]
+    const float *b1, *b2, *b3, *W4, *b4;     // FP32 [K][7][...]
     // TMA descriptors of the weight matrices (built once per weight set)
     CUtensorMap tmW1, tmW2, tmW3, tmW1lo, tmW2lo, tmW3lo, tmW1t, tmW2t, tmW3t;
     bool maps_ok;
@@ -89,10 +96,14 @@ struct NetBF16 {
 bool mlp_tc_available();
 bool make_weight_maps(NetBF16& w);
 // split = true: forward GEMMs from hi/lo BF16 pairs of both operands (G_lo
-// required); false: single BF16 pass everywhere.
+// required); false: single BF16 pass everywhere. dE/dG goes to dG (BF16). An
+// ensemble (w.n_nets > 1) leaves the mean energy in e and the mean dE/dG in
+// dG; with backward it also needs g1, BF16 [rows_cap][n_nets * 256] scratch
+// for every net's last hidden-layer gradient (two launches: the network
+// kernel, then the mean dE/dG GEMM).
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
                      const __nv_bfloat16* G, const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e,
-                     __nv_bfloat16* dG, bool backward, int* err_flag);
+                     __nv_bfloat16* dG, __nv_bfloat16* g1, bool backward, int* err_flag);
 
 // ---- serving batches (kernels_misc.cu): one molecule per request, its inputs
 // and result area in page-locked host memory that kernels address directly

@@ -8,6 +8,9 @@
 //             e = w4 . h3 + b4 (separate row reduction, fixed order)
 //   backward  g2 = (g3 W3) * celu'(z2); g1 = (g2 W2) * celu'(z1); dE/dG = g1 W1
 // (paper, section "PyTorch Model Support": forces by backpropagation).
+// An ensemble of K nets (section "Performance of MLPs") runs these launches
+// once per net; e and dE/dG take each net's output scaled by 1 / K, written
+// by net 0 and added by the others in net order, which leaves the means.
 // SIMT tiling: 128 x 64 output tile per block of 256 threads, 8 x 4 outputs
 // per thread, K in steps of 16 through double-buffered shared memory.
 #include "common.cuh"
@@ -24,7 +27,8 @@ template <int EPI>
 __global__ void __launch_bounds__(256) k_gemm(const Counters* __restrict__ ctr, const float* __restrict__ A, int lda,
                                               const float* __restrict__ B, int ldb, size_t b_elem_stride, int N,
                                               int K, const float* __restrict__ bias, const float* __restrict__ aux,
-                                              int ldaux, float* __restrict__ C0, float* __restrict__ C1, int ldc) {
+                                              int ldaux, float* __restrict__ C0, float* __restrict__ C1, int ldc,
+                                              float oscale, int oacc) {
     int s, row0, nvalid;
     if (!tile_info(ctr->species, blockIdx.y, s, row0, nvalid)) return;
     const int n0 = blockIdx.x * BN;
@@ -110,8 +114,9 @@ __global__ void __launch_bounds__(256) k_gemm(const Counters* __restrict__ ctr, 
                 C1[row * ldc + n] = aux[s * N + n] * celu_deriv(z);
             } else if (EPI == EPI_DSIG) {
                 C0[row * ldc + n] = v * celu_deriv(aux[row * ldaux + n]);
-            } else {
-                C0[row * ldc + n] = v;
+            } else {   // plain output: net 0 of K writes v / K, the others add theirs
+                const float o = v * oscale;
+                C0[row * ldc + n] = oacc ? C0[row * ldc + n] + o : o;
             }
         }
     }
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(256) k_gemm(const Counters* __restrict__ ctr, 
 // e[atom] = w4 . h3 + b4 for every valid row (one warp per row, fixed order).
 __global__ void k_energy_rows(const Counters* __restrict__ ctr, const float* __restrict__ H3,
                               const float* __restrict__ W4, const float* __restrict__ b4,
-                              const int* __restrict__ row_atom, float* __restrict__ e) {
+                              const int* __restrict__ row_atom, float* __restrict__ e, float oscale, int oacc) {
     int s, row0, nvalid;
     if (!tile_info(ctr->species, blockIdx.x, s, row0, nvalid)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -130,37 +135,43 @@ __global__ void k_energy_rows(const Counters* __restrict__ ctr, const float* __r
         for (int c = lane; c < kH3; c += 32) acc = fmaf(W4[s * kH3 + c], h[c], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) e[row_atom[row0 + r]] = acc + b4[s];
+        if (lane == 0) {
+            const int a = row_atom[row0 + r];
+            const float o = (acc + b4[s]) * oscale;
+            e[a] = oacc ? e[a] + o : o;
+        }
     }
 }
 
 }  // namespace
 
 void launch_mlp_f32(cudaStream_t st, int rows_cap, const Counters* ctr, const NetF32& w, const float* G,
-                    const int* row_atom, MlpF32Bufs& b, float* e, float* dG, bool backward) {
+                    const int* row_atom, MlpF32Bufs& b, float* e, float* dG, bool backward, int net, int nets) {
     const int tiles = rows_cap / kTileRows;
+    const float osc = nets > 1 ? 1.f / (float)nets : 1.f;
+    const int oacc = net > 0 ? 1 : 0;
     auto grid = [&](int N) { return dim3((N + BN - 1) / BN, tiles); };
     MLP_LAUNCH("mlp_f32_l1", st,
                k_gemm<EPI_BIAS_CELU><<<grid(kH1), 256, 0, st>>>(ctr, G, kAevLd, w.W1, kAevLen, (size_t)kH1 * kAevLen,
-                                                                kH1, kAevLen, w.b1, nullptr, 0, b.Z1, b.H1, kH1));
+                                                                kH1, kAevLen, w.b1, nullptr, 0, b.Z1, b.H1, kH1, 1.f, 0));
     MLP_LAUNCH("mlp_f32_l2", st,
                k_gemm<EPI_BIAS_CELU><<<grid(kH2), 256, 0, st>>>(ctr, b.H1, kH1, w.W2, kH1, (size_t)kH2 * kH1, kH2,
-                                                                kH1, w.b2, nullptr, 0, b.Z2, b.H2, kH2));
+                                                                kH1, w.b2, nullptr, 0, b.Z2, b.H2, kH2, 1.f, 0));
     MLP_LAUNCH("mlp_f32_l3", st,
                k_gemm<EPI_G3><<<grid(kH3), 256, 0, st>>>(ctr, b.H2, kH2, w.W3, kH2, (size_t)kH3 * kH2, kH3, kH2,
-                                                         w.b3, w.W4, 0, b.H3, b.G3, kH3));
-    MLP_LAUNCH("mlp_f32_energy", st, k_energy_rows<<<tiles, 256, 0, st>>>(ctr, b.H3, w.W4, w.b4, row_atom, e));
+                                                         w.b3, w.W4, 0, b.H3, b.G3, kH3, 1.f, 0));
+    MLP_LAUNCH("mlp_f32_energy", st, k_energy_rows<<<tiles, 256, 0, st>>>(ctr, b.H3, w.W4, w.b4, row_atom, e, osc, oacc));
     if (!backward) return;
     MLP_LAUNCH("mlp_f32_b3", st,
                k_gemm<EPI_DSIG><<<grid(kH2), 256, 0, st>>>(ctr, b.G3, kH3, w.W3t, kH3, (size_t)kH2 * kH3, kH2, kH3,
-                                                           nullptr, b.Z2, kH2, b.G2, nullptr, kH2));
+                                                           nullptr, b.Z2, kH2, b.G2, nullptr, kH2, 1.f, 0));
     MLP_LAUNCH("mlp_f32_b2", st,
                k_gemm<EPI_DSIG><<<grid(kH1), 256, 0, st>>>(ctr, b.G2, kH2, w.W2t, kH2, (size_t)kH1 * kH2, kH1, kH2,
-                                                           nullptr, b.Z1, kH1, b.G1, nullptr, kH1));
+                                                           nullptr, b.Z1, kH1, b.G1, nullptr, kH1, 1.f, 0));
     MLP_LAUNCH("mlp_f32_b1", st,
                k_gemm<EPI_PLAIN><<<grid(kAevLen), 256, 0, st>>>(ctr, b.G1, kH1, w.W1t, kH1, (size_t)kAevLen * kH1,
                                                                 kAevLen, kH1, nullptr, nullptr, 0, dG, nullptr,
-                                                                kAevLd));
+                                                                kAevLd, osc, oacc));
 }
 
 }  // namespace mlp

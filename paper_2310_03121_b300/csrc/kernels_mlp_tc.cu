@@ -20,6 +20,15 @@
 // rounding of the remainder, as A_hi B_hi + A_lo B_hi + A_hi B_lo (three MMAs
 // per K step, FP32 accumulation), so the energy carries ~16 bits of operand
 // precision; the backward (forces) uses the single BF16 terms.
+// Ensemble (section "Performance of MLPs": ANI-2x averages eight nets): each
+// tile runs F1..B2 once per net k (weights block k * 7 + s of the net-major
+// matrices), G coming back from L2 for every net. The energy of a row is
+// summed over the nets in registers and written once, times 1 / K. Instead of
+// B1, every net's g1 (BF16, the B1 A operand) is written out by TMA, and a
+// second kernel (k_mlp_b1_ens) forms the mean dE/dG as one GEMM with the nets
+// stacked along the contraction, dE/dG = (1/K) [g1_0 .. g1_K-1] [W1_0; ..;
+// W1_K-1], accumulated in tensor memory: one dE/dG epilogue per tile instead
+// of K, and no partial sums through L2.
 //
 // Warp roles (14 warps, at most 4 per SM sub-partition so that the epilogue
 // warps get up to 128 registers):
@@ -91,20 +100,24 @@ enum {
     kBarStage = 21,     // 1: a tile's epilogues are done with shared memory; one arrival per epilogue warp
     kBarEPart = 22,     // 1: E3 partial sums written; one arrival per epilogue warp
     kBarDrain = 23,     // 1: teardown MMA drain
-    kNBars = 24
+    kBarG1 = 24,        // 1: ensemble, g1 written to shared memory; one arrival per epilogue warp
+    kNBars = 25
 };
 
 struct TcArgs {
     const Counters* ctr;
     const int* row_atom;
-    const float *b1, *b2, *b3, *W4, *b4;
+    const float *b1, *b2, *b3, *W4, *b4;   // net-major: block k * 7 + s
     float* e;
     int backward;
+    int nets;         // ensemble size K (1: single net)
+    float inv_nets;   // 1 / K
     int* err;
 };
 
 struct TcMaps {
     CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t, dG;
+    CUtensorMap G1;   // ensemble: g1 of every net, BF16 [rows][K * 256]
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -174,15 +187,8 @@ __device__ __noinline__ bool mbar_wait_plain(uint32_t bar, uint32_t parity) {
         if (globaltimer() - t0 > kWaitNs) return false;
     }
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-// Same with an L2 eviction-priority policy (createpolicy): the weights stay
-// in L2 while G and dE/dG stream through it.
+// TMA tile load with an L2 eviction-priority policy (createpolicy): the
+// weights stay in L2 while G and dE/dG stream through it.
 __device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
                                                  uint64_t policy) {
     asm volatile(
@@ -407,64 +413,69 @@ __device__ void prefetch_g(const TcMaps& M, int row0, bool split) {
 
 template <bool SPLIT>
 __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t bar0, volatile int* abrt,
-                         bool backward, ProdState& P) {
+                         bool backward, bool b1, int nets, ProdState& P) {
     constexpr int nst = SPLIT ? 2 : 4;
     constexpr uint32_t stage = SPLIT ? 98304u : 49152u;   // A (+A_lo) 16 KB each, B (+B_lo) 32 KB each
     const CUtensorMap* maps[12] = {&M.G, &M.Glo, &M.W1, &M.W1lo, &M.W2, &M.W2lo, &M.W3, &M.W3lo, &M.W3t, &M.W2t,
                                    &M.W1t, &M.dG};
     for (int q = 0; q < 12; ++q) prefetch_map(maps[q]);
-    const uint64_t keep = policy_evict_last();
+    const uint64_t keep = policy_evict_last(), evict = policy_evict_first();
     auto job = [&](int k, int s) -> bool { return prod_job(P, make_job<SPLIT>(M, k, s), sbase, bar0, abrt, keep); };
-    int tile_no = 0;
-    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
+    int tile_no = 0;   // (tile, net) units started
+    for (int t = blockIdx.x;; t += gridDim.x) {
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
-        if (tile_no == 0) prefetch_g(M, row0, SPLIT);
-        // F1 stages cover every region: the previous tile's epilogues and MMAs must be done with them
-        if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
-        if (!prod_drain(P, bar0, 0xf0u, abrt)) break;
-        bool ok = true;
-        for (int c = 0; c < kAevLd / 64 && ok; ++c) {
-            const int st = (int)P.f1pos;
-            P.f1pos = (P.f1pos + 1u) & (uint32_t)(nst - 1);
-            if (!prod_free(P, bar0, st, abrt)) {
-                ok = false;
-                break;
-            }
-            const uint32_t full = bar0 + 8u * (kBarF1Full + st), dst = sbase + (uint32_t)st * stage;
-            mbar_expect_tx(full, stage);
-            tma_load_2d(dst, &M.G, c * 64, row0, full);
-            if (SPLIT) {
-                tma_load_2d(dst + 16384u, &M.Glo, c * 64, row0, full);
-                tma_load_2d_hint(dst + 32768u, &M.W1, c * 64, s * kH1, full, keep);
-                tma_load_2d_hint(dst + 65536u, &M.W1lo, c * 64, s * kH1, full, keep);
-            } else {
-                tma_load_2d_hint(dst + 16384u, &M.W1, c * 64, s * kH1, full, keep);
-            }
-            P.pend |= 1u << st;
-            P.lpar ^= 1u << st;
-            if (c == 0) MLP_TC_MARK(27);
-        }
-        if (!ok) break;
-        MLP_TC_MARK(28);
-        // the F2 ring overlays the F1 stages
-        if (!prod_drain(P, bar0, 0x0fu, abrt)) break;
-        if (!job(kJobF2, s)) break;
-        MLP_TC_MARK(29);
-        if (!job(kJobF3, s)) break;
         int sn, rown, nvn;
         const bool has_next = tile_info(counts, t + (int)gridDim.x, sn, rown, nvn);
-        if (!backward) {
-            if (has_next) prefetch_g(M, rown, SPLIT);
-            continue;
+        bool ok = true;
+        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+            const int es = net * kNSpecies + s;   // weight block of (net, element)
+            ok = false;
+            if (tile_no == 0) prefetch_g(M, row0, SPLIT);
+            // F1 stages cover every region: the previous unit's epilogues and MMAs must be done with them
+            if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
+            if (!prod_drain(P, bar0, 0xf0u, abrt)) break;
+            bool f1 = true;
+            for (int c = 0; c < kAevLd / 64; ++c) {
+                const int st = (int)P.f1pos;
+                P.f1pos = (P.f1pos + 1u) & (uint32_t)(nst - 1);
+                if (!prod_free(P, bar0, st, abrt)) {
+                    f1 = false;
+                    break;
+                }
+                const uint32_t full = bar0 + 8u * (kBarF1Full + st), dst = sbase + (uint32_t)st * stage;
+                // G stays in L2 while later nets of this tile still need it
+                const uint64_t gpol = net < nets - 1 ? keep : evict;
+                mbar_expect_tx(full, stage);
+                tma_load_2d_hint(dst, &M.G, c * 64, row0, full, gpol);
+                if (SPLIT) {
+                    tma_load_2d_hint(dst + 16384u, &M.Glo, c * 64, row0, full, gpol);
+                    tma_load_2d_hint(dst + 32768u, &M.W1, c * 64, es * kH1, full, keep);
+                    tma_load_2d_hint(dst + 65536u, &M.W1lo, c * 64, es * kH1, full, keep);
+                } else {
+                    tma_load_2d_hint(dst + 16384u, &M.W1, c * 64, es * kH1, full, keep);
+                }
+                P.pend |= 1u << st;
+                P.lpar ^= 1u << st;
+                if (c == 0) MLP_TC_MARK(27);
+            }
+            if (!f1) break;
+            MLP_TC_MARK(28);
+            // the F2 ring overlays the F1 stages
+            if (!prod_drain(P, bar0, 0x0fu, abrt)) break;
+            if (!job(kJobF2, es)) break;
+            MLP_TC_MARK(29);
+            if (!job(kJobF3, es)) break;
+            if (backward && (!job(kJobB3, es) || !job(kJobB2, es))) break;
+            if (b1 && (!job(kJobB1 + 0, es) || !job(kJobB1 + 1, es) || !job(kJobB1 + 2, es) || !job(kJobB1 + 3, es)))
+                break;
+            // the next tile's G: requested after this tile's last weight load, so
+            // that the weight loads never queue behind it
+            if (net == nets - 1 && has_next) prefetch_g(M, rown, SPLIT);
+            MLP_TC_MARK(30);
+            ok = true;
         }
-        if (!job(kJobB3, s) || !job(kJobB2, s) || !job(kJobB1 + 0, s) || !job(kJobB1 + 1, s) ||
-            !job(kJobB1 + 2, s) || !job(kJobB1 + 3, s))
-            break;
-        // the next tile's G: requested after this tile's last weight load, so
-        // that the weight loads never queue behind it
-        if (has_next) prefetch_g(M, rown, SPLIT);
-        MLP_TC_MARK(30);
+        if (!ok) break;
     }
 }
 
@@ -515,7 +526,7 @@ __device__ __forceinline__ bool mma_job(MmaState& S, const Job& J, uint32_t sbas
 
 template <bool SPLIT>
 __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t tmem, uint32_t bar0,
-                           volatile int* abrt, bool backward, MmaState& S) {
+                           volatile int* abrt, bool backward, bool b1, int nets, MmaState& S) {
     constexpr int nst = SPLIT ? 2 : 4;
     constexpr uint32_t stage = SPLIT ? 98304u : 49152u;
     const uint32_t idesc1 = idesc_bf16(128, kH1);
@@ -537,58 +548,69 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
         mma_commit(bar0 + 8u * (kBarAcc + half));
         return true;
     };
-    int tile_no = 0;
-    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
+    int tile_no = 0;   // (tile, net) units started
+    for (int t = blockIdx.x;; t += gridDim.x) {
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
-        // F1 writes accumulator half 0: the previous tile's last reader of it must be done
-        if (tile_no > 0 && !(backward ? wait_b1(0) : wait_op())) break;
-        MLP_TC_MARK(20);
         bool ok = true;
-        for (int c = 0; c < kAevLd / 64; ++c) {
-            const int st = (int)S.f1pos;
-            S.f1pos = (S.f1pos + 1u) & (uint32_t)(nst - 1);
-            if (!mbar_wait(full_bar(bar0, st), (S.fpar >> st) & 1u, abrt)) {
-                ok = false;
-                break;
-            }
-            S.fpar ^= 1u << st;
-            tc_fence_after();
-            const uint32_t base = sbase + (uint32_t)st * stage;
-            const uint64_t ah = sdesc(base), al = sdesc(base + 16384u);
-            const uint64_t bh = sdesc(base + (SPLIT ? 32768u : 16384u)), bl = sdesc(base + 65536u);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-                if (SPLIT) {
-                    mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
-                    mma_bf16(tmem, al + 2u * k, bh + 2u * k, idesc1, 1u);
-                    mma_bf16(tmem, ah + 2u * k, bl + 2u * k, idesc1, 1u);
-                } else {
-                    mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
+        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+            const int es = net * kNSpecies + s;
+            ok = false;
+            // F1 writes accumulator half 0: the previous unit's last reader of it
+            // (EB1 block 2, else E3 or EB2, which arrive on the operand barrier) must be done
+            if (tile_no > 0 && !(b1 ? wait_b1(0) : wait_op())) break;
+            MLP_TC_MARK(20);
+            bool f1 = true;
+            for (int c = 0; c < kAevLd / 64; ++c) {
+                const int st = (int)S.f1pos;
+                S.f1pos = (S.f1pos + 1u) & (uint32_t)(nst - 1);
+                if (!mbar_wait(full_bar(bar0, st), (S.fpar >> st) & 1u, abrt)) {
+                    f1 = false;
+                    break;
                 }
+                S.fpar ^= 1u << st;
+                tc_fence_after();
+                const uint32_t base = sbase + (uint32_t)st * stage;
+                const uint64_t ah = sdesc(base), al = sdesc(base + 16384u);
+                const uint64_t bh = sdesc(base + (SPLIT ? 32768u : 16384u)), bl = sdesc(base + 65536u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    if (SPLIT) {
+                        mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
+                        mma_bf16(tmem, al + 2u * k, bh + 2u * k, idesc1, 1u);
+                        mma_bf16(tmem, ah + 2u * k, bl + 2u * k, idesc1, 1u);
+                    } else {
+                        mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
+                    }
+                }
+                mma_commit(empty_bar(bar0, st));
             }
-            mma_commit(empty_bar(bar0, st));
+            if (!f1) break;
+            mma_commit(bar0 + 8u * kBarAcc);
+            MLP_TC_MARK(21);
+            // F2 writes half 1: the previous unit's last B1 block must have been read
+            if (b1 && tile_no > 0 && !wait_b1(1)) break;
+            if (!wait_op() || !job(kJobF2, es, 1)) break;   // after E1
+            MLP_TC_MARK(22);
+            if (!wait_op() || !job(kJobF3, es, 0)) break;   // after E2
+            MLP_TC_MARK(23);
+            if (backward) {
+                if (!wait_op() || !job(kJobB3, es, 1)) break;   // after E3
+                MLP_TC_MARK(24);
+                if (!wait_op() || !job(kJobB2, es, 0)) break;   // after EB3
+                MLP_TC_MARK(25);
+            }
+            if (b1) {
+                if (!wait_op() || !job(kJobB1 + 0, es, 0)) break;   // after EB2
+                if (!job(kJobB1 + 1, es, 1)) break;
+                if (!wait_b1(0) || !job(kJobB1 + 2, es, 0)) break;
+                if (!wait_b1(1) || !job(kJobB1 + 3, es, 1)) break;
+                MLP_TC_MARK(26);
+            }
+            ok = true;
         }
         if (!ok) break;
-        mma_commit(bar0 + 8u * kBarAcc);
-        MLP_TC_MARK(21);
-        // F2 writes half 1: the previous tile's last B1 block must have been read
-        if (backward && tile_no > 0 && !wait_b1(1)) break;
-        if (!wait_op() || !job(kJobF2, s, 1)) break;   // after E1
-        MLP_TC_MARK(22);
-        if (!wait_op() || !job(kJobF3, s, 0)) break;   // after E2
-        MLP_TC_MARK(23);
-        if (!backward) continue;
-        if (!wait_op() || !job(kJobB3, s, 1)) break;   // after E3
-        MLP_TC_MARK(24);
-        if (!wait_op() || !job(kJobB2, s, 0)) break;   // after EB3
-        MLP_TC_MARK(25);
-        if (!wait_op() || !job(kJobB1 + 0, s, 0)) break;   // after EB2
-        if (!job(kJobB1 + 1, s, 1)) break;
-        if (!wait_b1(0) || !job(kJobB1 + 2, s, 0)) break;
-        if (!wait_b1(1) || !job(kJobB1 + 3, s, 1)) break;
-        MLP_TC_MARK(26);
     }
 }
 
@@ -663,197 +685,234 @@ __device__ __forceinline__ void epi_arrive(EpiCtx& X, uint32_t bar) {
 // Epilogue loops take one 16-column chunk per iteration, chunks c0 = 16
 // (part + kParts k) < N, and are kept rolled: the code of every phase stays
 // small, so the epilogue warps keep hitting in the instruction cache.
-template <bool SPLIT>
+template <bool SPLIT, bool ENS>
 __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, EpiCtx& X, int warp) {
     const uint32_t sbase = X.sbase, bar0 = X.bar0;
     const uint32_t op_bar = bar0 + 8u * kBarOp;
     const int r = X.r, part = X.part;
     const uint32_t stage_box = sbase + kOffStage + (uint32_t)(warp - 2) * 4096u;
     const uint64_t stream_out = policy_evict_first();
+    const int nets = ENS ? p.nets : 1;
     uint32_t n_epart = 0;
-    int tile_no = 0;
+    int tile_no = 0;   // (tile, net) units
+    float e_sum = 0.f; // ensemble: this row's energy summed over the nets so far (part 0)
     (void)warp;
-    for (int t = blockIdx.x;; t += gridDim.x, ++tile_no) {
+    for (int t = blockIdx.x;; t += gridDim.x) {
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
-        if (warp == 2) MLP_TC_MARK(0);
-        const float* b1 = p.b1 + s * kH1;
-        const float* b2 = p.b2 + s * kH2;
-        const float* b3 = p.b3 + s * kH3;
-        const float* w4 = p.W4 + s * kH3;
+        bool ok = true;
+        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+            const int es = net * kNSpecies + s;
+            ok = false;
+            if (warp == 2) MLP_TC_MARK(0);
+            const float* b1 = p.b1 + es * kH1;
+            const float* b2 = p.b2 + es * kH2;
+            const float* b3 = p.b3 + es * kH3;
+            const float* w4 = p.W4 + es * kH3;
 
-        // ---- E1: h1 = celu(D + b1)
-        if (!epi_acc(X, 0)) break;
-        if (warp == 2) MLP_TC_MARK(1);
+            // ---- E1: h1 = celu(D + b1)
+            if (!epi_acc(X, 0)) break;
+            if (warp == 2) MLP_TC_MARK(1);
 #pragma unroll 1
-        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
-            uint32_t d[16];
-            tmem_ld16(X.tl + (uint32_t)c0, d);
-            tmem_wait_ld();
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b1 + c0 + q));
-            store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
-        }
-        epi_arrive(X, op_bar);
-        if (warp == 2) MLP_TC_MARK(2);
-
-        // ---- E2: h2 = celu(D + b2)
-        if (!epi_acc(X, 1)) break;
-        if (warp == 2) MLP_TC_MARK(3);
-#pragma unroll 1
-        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
-            uint32_t d[16];
-            tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
-            tmem_wait_ld();
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b2 + c0 + q));
-            store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
-        }
-        epi_arrive(X, op_bar);
-        if (warp == 2) MLP_TC_MARK(4);
-
-        // ---- E3: energy (four column-part partial sums per row, added in
-        // fixed order by part 0) and g3 = w4 * celu'(z3)
-        if (!epi_acc(X, 0)) break;
-        if (warp == 2) MLP_TC_MARK(5);
-        {
-            float es = 0.f;
-#pragma unroll 1
-            for (int c0 = 16 * part; c0 < kH3; c0 += 16 * kParts) {
+            for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
                 uint32_t d[16];
                 tmem_ld16(X.tl + (uint32_t)c0, d);
                 tmem_wait_ld();
-                uint32_t pk[8];
+                float v[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    // one exponential per element: exp(min(z, 0) / alpha) gives celu and celu'
-                    const float z0 = __uint_as_float(d[2 * q]) + __ldg(b3 + c0 + 2 * q);
-                    const float z1 = __uint_as_float(d[2 * q + 1]) + __ldg(b3 + c0 + 2 * q + 1);
-                    const float w0 = __ldg(w4 + c0 + 2 * q), w1 = __ldg(w4 + c0 + 2 * q + 1);
-                    const float x0 = __expf(fminf(z0, 0.f) * (1.f / kCeluAlpha));
-                    const float x1 = __expf(fminf(z1, 0.f) * (1.f / kCeluAlpha));
-                    es = fmaf(w0, z0 > 0.f ? z0 : kCeluAlpha * (x0 - 1.f), es);
-                    es = fmaf(w1, z1 > 0.f ? z1 : kCeluAlpha * (x1 - 1.f), es);
-                    pk[q] = pack_bf16(z0 > 0.f ? w0 : w0 * x0, z1 > 0.f ? w1 : w1 * x1);
-                }
-                if (p.backward) {
-                    st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
-                    st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
-                }
+                for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b1 + c0 + q));
+                store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
             }
-            const uint32_t ep = sbase + kOffEPart + (uint32_t)r * 128u + (uint32_t)((4 ^ (r & 7)) << 4);
-            asm volatile("st.shared.f32 [%0], %1;" ::"r"(ep + 4u * (uint32_t)part), "f"(es) : "memory");
-            __syncwarp();
-            if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarEPart);
-            if (part == 0) {
-                if (!epi_wait(X, bar0 + 8u * kBarEPart, n_epart & 1u)) break;
-                if (r < nvalid) {
-                    const uint4 v = ld_shared_v4(ep);
-                    float e = __ldg(p.b4 + s);
-                    e += __uint_as_float(v.x);
-                    e += __uint_as_float(v.y);
-                    e += __uint_as_float(v.z);
-                    p.e[p.row_atom[row0 + r]] = e;
-                }
-            }
-            ++n_epart;
-        }
-        epi_arrive(X, op_bar);
-        if (warp == 2) MLP_TC_MARK(6);
-        if (!p.backward) {
-            __syncwarp();
-            if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
-            continue;
-        }
+            epi_arrive(X, op_bar);
+            if (warp == 2) MLP_TC_MARK(2);
 
-        // ---- EB3: g2 = D * celu'(z2) over h2
-        if (!epi_acc(X, 1)) break;
-        if (warp == 2) MLP_TC_MARK(7);
+            // ---- E2: h2 = celu(D + b2)
+            if (!epi_acc(X, 1)) break;
+            if (warp == 2) MLP_TC_MARK(3);
 #pragma unroll 1
-        for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
-            uint32_t d[16];
-            tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
-            tmem_wait_ld();
-            store_grad(sbase, kOffH2, r, c0, d);
-        }
-        epi_arrive(X, op_bar);
-        if (warp == 2) MLP_TC_MARK(8);
-
-        // ---- EB2: g1 = D * celu'(z1) over h1
-        if (!epi_acc(X, 0)) break;
-        if (warp == 2) MLP_TC_MARK(9);
-#pragma unroll 1
-        for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
-            uint32_t d[16];
-            tmem_ld16(X.tl + (uint32_t)c0, d);
-            tmem_wait_ld();
-            store_grad(sbase, kOffH1, r, c0, d);
-        }
-        epi_arrive(X, op_bar);
-        if (warp == 2) MLP_TC_MARK(10);
-
-        // ---- EB1: four 256-column blocks of dE/dG, 16 boxes of 64 columns
-        // per tile; box g = 4 j + b goes to part g % 3. A warp converts its
-        // boxes (its 32 rows) to BF16 in its 4 KB swizzled staging box and
-        // writes each with one TMA store.
-        bool ok = true;
-        for (int j = 0; j < 4; ++j) {
-            const int h = j & 1;
-            if (!epi_acc(X, h)) {
-                ok = false;
-                break;
-            }
-            if (warp == 2) MLP_TC_MARK(11 + 2 * j);
-            int nb = 0;
-#pragma unroll 1
-            for (int b = 0; b < 4; ++b) {
-                if ((4 * j + b) % kParts != part) continue;
-                uint32_t d[4][16];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    tmem_ld16(X.tl + 256u * (uint32_t)h + (uint32_t)(64 * b + 16 * k), d[k]);
+            for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
+                uint32_t d[16];
+                tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
                 tmem_wait_ld();
-                ++nb;
-                if (X.lane == 0) bulk_wait_read0();   // the previous store has read the staging box
-                __syncwarp();
-                const uint32_t rowb = stage_box + (uint32_t)X.lane * 128u;
+                float v[16];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b2 + c0 + q));
+                store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
+            }
+            epi_arrive(X, op_bar);
+            if (warp == 2) MLP_TC_MARK(4);
+
+            // ---- E3: energy (column-part partial sums per row, added in
+            // fixed order by part 0) and g3 = w4 * celu'(z3)
+            if (!epi_acc(X, 0)) break;
+            if (warp == 2) MLP_TC_MARK(5);
+            {
+                float es_part = 0.f;
+#pragma unroll 1
+                for (int c0 = 16 * part; c0 < kH3; c0 += 16 * kParts) {
+                    uint32_t d[16];
+                    tmem_ld16(X.tl + (uint32_t)c0, d);
+                    tmem_wait_ld();
+                    uint32_t pk[8];
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const uint32_t* v = d[k] + 8 * hh;
-                        const uint32_t chunk = (uint32_t)((2 * k + hh) ^ (X.lane & 7));
-                        st_shared_v4(rowb + chunk * 16u, pack_bf16(__uint_as_float(v[0]), __uint_as_float(v[1])),
-                                     pack_bf16(__uint_as_float(v[2]), __uint_as_float(v[3])),
-                                     pack_bf16(__uint_as_float(v[4]), __uint_as_float(v[5])),
-                                     pack_bf16(__uint_as_float(v[6]), __uint_as_float(v[7])));
+                    for (int q = 0; q < 8; ++q) {
+                        // one exponential per element: exp(min(z, 0) / alpha) gives celu and celu'
+                        const float z0 = __uint_as_float(d[2 * q]) + __ldg(b3 + c0 + 2 * q);
+                        const float z1 = __uint_as_float(d[2 * q + 1]) + __ldg(b3 + c0 + 2 * q + 1);
+                        const float w0 = __ldg(w4 + c0 + 2 * q), w1 = __ldg(w4 + c0 + 2 * q + 1);
+                        const float x0 = __expf(fminf(z0, 0.f) * (1.f / kCeluAlpha));
+                        const float x1 = __expf(fminf(z1, 0.f) * (1.f / kCeluAlpha));
+                        es_part = fmaf(w0, z0 > 0.f ? z0 : kCeluAlpha * (x0 - 1.f), es_part);
+                        es_part = fmaf(w1, z1 > 0.f ? z1 : kCeluAlpha * (x1 - 1.f), es_part);
+                        pk[q] = pack_bf16(z0 > 0.f ? w0 : w0 * x0, z1 > 0.f ? w1 : w1 * x1);
+                    }
+                    if (p.backward) {
+                        st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
+                        st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
                     }
                 }
-                fence_proxy_async();
+                const uint32_t ep = sbase + kOffEPart + (uint32_t)r * 128u + (uint32_t)((4 ^ (r & 7)) << 4);
+                asm volatile("st.shared.f32 [%0], %1;" ::"r"(ep + 4u * (uint32_t)part), "f"(es_part) : "memory");
                 __syncwarp();
-                if (X.lane == 0) tma_store_2d(&M.dG, 256 * j + 64 * b, row0 + 32 * (warp & 3), stage_box, stream_out);
+                if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarEPart);
+                if (part == 0) {
+                    if (!epi_wait(X, bar0 + 8u * kBarEPart, n_epart & 1u)) break;
+                    if (r < nvalid) {
+                        const uint4 v = ld_shared_v4(ep);
+                        float e = __ldg(p.b4 + es);
+                        e += __uint_as_float(v.x);
+                        e += __uint_as_float(v.y);
+                        e += __uint_as_float(v.z);
+                        if (ENS) {
+                            e_sum = net == 0 ? e : e_sum + e;
+                            if (net == nets - 1) p.e[p.row_atom[row0 + r]] = e_sum * p.inv_nets;
+                        } else {
+                            p.e[p.row_atom[row0 + r]] = e;
+                        }
+                    }
+                }
+                ++n_epart;
             }
-            (void)nb;
-            // this warp is done reading accumulator half h
-            tc_fence_before();
+            epi_arrive(X, op_bar);
+            if (warp == 2) MLP_TC_MARK(6);
+            if (!p.backward) {
+                __syncwarp();
+                if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
+                ok = true;
+                continue;
+            }
+
+            // ---- EB3: g2 = D * celu'(z2) over h2
+            if (!epi_acc(X, 1)) break;
+            if (warp == 2) MLP_TC_MARK(7);
+#pragma unroll 1
+            for (int c0 = 16 * part; c0 < kH2; c0 += 16 * kParts) {
+                uint32_t d[16];
+                tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
+                tmem_wait_ld();
+                store_grad(sbase, kOffH2, r, c0, d);
+            }
+            epi_arrive(X, op_bar);
+            if (warp == 2) MLP_TC_MARK(8);
+
+            // ---- EB2: g1 = D * celu'(z1) over h1
+            if (!epi_acc(X, 0)) break;
+            if (warp == 2) MLP_TC_MARK(9);
+#pragma unroll 1
+            for (int c0 = 16 * part; c0 < kH1; c0 += 16 * kParts) {
+                uint32_t d[16];
+                tmem_ld16(X.tl + (uint32_t)c0, d);
+                tmem_wait_ld();
+                store_grad(sbase, kOffH1, r, c0, d);
+            }
+            epi_arrive(X, op_bar);
+            if (warp == 2) MLP_TC_MARK(10);
+
+            if (ENS) {
+                // ---- ensemble: g1 of this net -> global (four 128 x 64 boxes,
+                // straight from the operand region) once every warp has written its part
+                if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarG1);
+                if (warp == 2) {
+                    int gok = 1;
+                    if (X.lane == 0) {
+                        gok = mbar_wait(bar0 + 8u * kBarG1, (uint32_t)tile_no & 1u, X.abrt) ? 1 : 0;
+                        if (gok) {
+                            for (int c = 0; c < kH1 / 64; ++c)
+                                tma_store_2d(&M.G1, kH1 * net + 64 * c, row0, sbase + kOffH1 + (uint32_t)c * kAtom,
+                                             stream_out);
+                            bulk_wait_read0();   // read out of shared memory before the next unit's F1
+                        }
+                    }
+                    if (!__shfl_sync(0xffffffffu, gok, 0)) break;
+                }
+                __syncwarp();
+                if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
+                ok = true;
+                continue;
+            }
+
+            // ---- EB1: four 256-column blocks of dE/dG, 16 boxes of 64 columns
+            // per tile; box g = 4 j + b goes to part g % 3. A warp converts its
+            // boxes (its 32 rows) to BF16 in its 4 KB swizzled staging box and
+            // writes each with one TMA store.
+            bool jok = true;
+            for (int j = 0; j < 4; ++j) {
+                const int h = j & 1;
+                if (!epi_acc(X, h)) {
+                    jok = false;
+                    break;
+                }
+                if (warp == 2) MLP_TC_MARK(11 + 2 * j);
+#pragma unroll 1
+                for (int b = 0; b < 4; ++b) {
+                    if ((4 * j + b) % kParts != part) continue;
+                    uint32_t d[4][16];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tmem_ld16(X.tl + 256u * (uint32_t)h + (uint32_t)(64 * b + 16 * k), d[k]);
+                    tmem_wait_ld();
+                    const uint32_t rowb = stage_box + (uint32_t)X.lane * 128u;
+                    const int y = row0 + 32 * (warp & 3);
+                    if (X.lane == 0) bulk_wait_read0();   // the previous store has read the staging box
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const uint32_t* v = d[k] + 8 * hh;
+                            const uint32_t chunk = (uint32_t)((2 * k + hh) ^ (X.lane & 7));
+                            st_shared_v4(rowb + chunk * 16u,
+                                         pack_bf16(__uint_as_float(v[0]), __uint_as_float(v[1])),
+                                         pack_bf16(__uint_as_float(v[2]), __uint_as_float(v[3])),
+                                         pack_bf16(__uint_as_float(v[4]), __uint_as_float(v[5])),
+                                         pack_bf16(__uint_as_float(v[6]), __uint_as_float(v[7])));
+                        }
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (X.lane == 0) tma_store_2d(&M.dG, 256 * j + 64 * b, y, stage_box, stream_out);
+                }
+                // this warp is done reading accumulator half h
+                tc_fence_before();
+                __syncwarp();
+                if (X.lane == 0) mbar_arrive(bar0 + 8u * (kBarB1Free + h));
+                if (warp == 2) MLP_TC_MARK(12 + 2 * j);
+            }
+            if (!jok) break;
+            if (X.lane == 0) {
+                bulk_wait_read0();
+                mbar_arrive(bar0 + 8u * kBarStage);
+            }
             __syncwarp();
-            if (X.lane == 0) mbar_arrive(bar0 + 8u * (kBarB1Free + h));
-            if (warp == 2) MLP_TC_MARK(12 + 2 * j);
+            if (warp == 2) MLP_TC_MARK(19);
+            ok = true;
         }
         if (!ok) break;
-        if (X.lane == 0) {
-            bulk_wait_read0();
-            mbar_arrive(bar0 + 8u * kBarStage);
-        }
-        __syncwarp();
-        if (warp == 2) MLP_TC_MARK(19);
     }
 }
 
 // ------------------------------------------------------------------ kernel
-template <bool SPLIT>
+template <bool SPLIT, bool ENS>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ TcMaps M, TcArgs p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) unsigned long long bars[kNBars];
@@ -869,7 +928,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
 
     if (tid == 0) {
         for (int q = 0; q < kNBars; ++q) {
-            const bool epi = q == kBarOp || q == kBarB1Free || q == kBarB1Free + 1 || q == kBarStage || q == kBarEPart;
+            const bool epi = q == kBarOp || q == kBarB1Free || q == kBarB1Free + 1 || q == kBarStage ||
+                             q == kBarEPart || q == kBarG1;
             mbar_init(bar0 + 8u * q, epi ? (uint32_t)kEpiWarps : 1u);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -886,6 +946,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const bool backward = p.backward != 0;
+    const int nets = ENS ? p.nets : 1;
+    const bool b1 = backward && !ENS;   // the ensemble's B1 is k_mlp_b1_ens
 
     ProdState P;
     MmaState S;
@@ -895,9 +957,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     P.geom = S.geom = 0xffffffffu;
 
     if (warp == 0) {
-        if (lane == 0) producer<SPLIT>(M, counts, sbase, bar0, abrt, backward, P);
+        if (lane == 0) producer<SPLIT>(M, counts, sbase, bar0, abrt, backward, b1, nets, P);
     } else if (warp == 1) {
-        if (lane == 0) mma_issuer<SPLIT>(M, counts, sbase, tmem, bar0, abrt, backward, S);
+        if (lane == 0) mma_issuer<SPLIT>(M, counts, sbase, tmem, bar0, abrt, backward, b1, nets, S);
     } else {
         EpiCtx X;
         X.sbase = sbase;
@@ -908,7 +970,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         X.part = (warp - 2) >> 2;
         X.r = (warp & 3) * 32 + lane;
         X.n_acc[0] = X.n_acc[1] = 0;
-        epilogue<SPLIT>(M, p, counts, X, warp);
+        epilogue<SPLIT, ENS>(M, p, counts, X, warp);
     }
     __syncwarp();
 
@@ -934,6 +996,207 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
         const uint32_t a = (uint32_t)abort_flag;
         const uint32_t code = (a & 0x40000000u) ? 1u | (((a >> 20) & 0x3fu) << 4) | ((((a & 0xfffffu) - bar0) / 8u) << 12) : 1u;
         atomicOr(p.err, (int)code);
+    }
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// ------------------------------------------------------------------ ensemble dE/dG
+// The ensemble's last backward layer as one GEMM per work item (tile t of
+// 128 rows of element s, 256-column block j of dE/dG):
+//   D[128 x 256] = sum over nets k, K chunks c of g1_k[:, 64c..] W1_k^T[256j.., 64c..]^T
+//   dE/dG[rows, 256j ..] = BF16(D / K)
+// A (g1, written by k_mlp_tc for every net) and B (W1^T of net k, element s)
+// stream through a 4-stage ring; two TMEM accumulators of 256 columns let the
+// epilogue of item i overlap the MMAs of item i + 1.
+// Warps: 0 TMA producer, 1 MMA issuer, 2..5 epilogue (TMEM lane quarter
+// warp % 4: 32 rows each, four 64-column boxes stored by TMA).
+constexpr int kEnsStages = 4;
+constexpr uint32_t kEnsStage = 3u * 16384u;                         // A 16 KB + B 32 KB
+constexpr uint32_t kEnsOffStaging = (uint32_t)kEnsStages * kEnsStage;   // 4 x 4 KB, one per epilogue warp
+constexpr uint32_t kEnsSmemAlloc = kEnsOffStaging + 4u * 4096u + 1024u;
+constexpr int kEnsThreads = 32 * 6;
+enum {
+    kEnsFull = 0,       // 4: stage loaded
+    kEnsEmpty = 4,      // 4: stage consumed (MMA commit)
+    kEnsAccFull = 8,    // 2: accumulator complete (MMA commit)
+    kEnsAccEmpty = 10,  // 2: accumulator read; one arrival per epilogue warp
+    kEnsDrain = 12,     // 1: teardown MMA drain
+    kEnsNBars = 13
+};
+
+struct EnsArgs {
+    const Counters* ctr;
+    int nets;
+    float inv_nets;
+    int* err;
+};
+struct EnsMaps {
+    CUtensorMap G1, W1t, dG;
+};
+
+__global__ void __launch_bounds__(kEnsThreads, 1) k_mlp_b1_ens(const __grid_constant__ EnsMaps M, EnsArgs p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) unsigned long long bars[kEnsNBars];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int counts[8];
+    __shared__ uint32_t consumed_par;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    volatile int* abrt = &abort_flag;
+    const int nq = 4 * p.nets;   // K chunks of 64 per item
+
+    if (tid == 0) {
+        for (int q = 0; q < kEnsNBars; ++q)
+            mbar_init(bar0 + 8u * q, (q == kEnsAccEmpty || q == kEnsAccEmpty + 1) ? 4u : 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (tid < 8) counts[tid] = tid < kNSpecies ? p.ctr->species[tid] : 0;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    uint32_t lpar = 0, fpar = 0;   // per stage: loads issued / loads consumed, parity
+
+    if (warp == 0 && lane == 0) {
+        prefetch_map(&M.G1);
+        prefetch_map(&M.W1t);
+        const uint64_t keep = policy_evict_last(), evict = policy_evict_first();
+        uint32_t pend = 0, epar = 0;
+        int pos = 0;
+        bool ok = true;
+        for (int i = blockIdx.x; ok; i += gridDim.x) {
+            int s, row0, nvalid;
+            if (!tile_info(counts, i >> 2, s, row0, nvalid)) break;
+            const int j = i & 3;
+            for (int q = 0; q < nq; ++q) {
+                const int st = pos;
+                pos = (pos + 1) & (kEnsStages - 1);
+                const uint32_t m = 1u << st;
+                if (pend & m) {
+                    if (!mbar_wait(bar0 + 8u * (kEnsEmpty + st), (epar >> st) & 1u, abrt)) {
+                        ok = false;
+                        break;
+                    }
+                    epar ^= m;
+                }
+                const int k = q >> 2, c = q & 3;
+                const uint32_t full = bar0 + 8u * (kEnsFull + st), dst = sbase + (uint32_t)st * kEnsStage;
+                mbar_expect_tx(full, kEnsStage);
+                // g1 tile: read by the four column-block items of the tile, then done
+                tma_load_2d_hint(dst, &M.G1, kH1 * k + 64 * c, row0, full, j == 3 ? evict : keep);
+                tma_load_2d_hint(dst + 16384u, &M.W1t, 64 * c, (k * kNSpecies + s) * kAevLd + 256 * j, full, keep);
+                pend |= m;
+                lpar ^= m;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16(128, 256);
+        int pos = 0, n_item = 0;
+        bool ok = true;
+        for (int i = blockIdx.x; ok; i += gridDim.x, ++n_item) {
+            int s, row0, nvalid;
+            if (!tile_info(counts, i >> 2, s, row0, nvalid)) break;
+            const int h = n_item & 1;
+            // accumulator h was last used by item n_item - 2: its epilogue must be done
+            if (n_item >= 2 && !mbar_wait(bar0 + 8u * (kEnsAccEmpty + h), (uint32_t)((n_item >> 1) + 1) & 1u, abrt))
+                break;
+            tc_fence_after();
+            const uint32_t d = tmem + 256u * (uint32_t)h;
+            for (int q = 0; q < nq; ++q) {
+                const int st = pos;
+                pos = (pos + 1) & (kEnsStages - 1);
+                if (!mbar_wait(bar0 + 8u * (kEnsFull + st), (fpar >> st) & 1u, abrt)) {
+                    ok = false;
+                    break;
+                }
+                fpar ^= 1u << st;
+                tc_fence_after();
+                const uint32_t base = sbase + (uint32_t)st * kEnsStage;
+                const uint64_t ad = sdesc(base), bd = sdesc(base + 16384u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2u * k, bd + 2u * k, idesc, (q > 0 || k > 0) ? 1u : 0u);
+                mma_commit(bar0 + 8u * (kEnsEmpty + st));
+            }
+            if (!ok) break;
+            mma_commit(bar0 + 8u * (kEnsAccFull + h));
+        }
+    } else if (warp >= 2) {
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const uint32_t stage_box = sbase + kEnsOffStaging + (uint32_t)(warp - 2) * 4096u;
+        const uint64_t stream_out = policy_evict_first();
+        const float sc = p.inv_nets;
+        int n_item = 0;
+        for (int i = blockIdx.x;; i += gridDim.x, ++n_item) {
+            int s, row0, nvalid;
+            if (!tile_info(counts, i >> 2, s, row0, nvalid)) break;
+            const int j = i & 3, h = n_item & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(bar0 + 8u * (kEnsAccFull + h), (uint32_t)(n_item >> 1) & 1u, abrt) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            tc_fence_after();
+            const uint32_t rowb = stage_box + (uint32_t)lane * 128u;
+#pragma unroll 1
+            for (int b = 0; b < 4; ++b) {
+                uint32_t d[4][16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tmem_ld16(tl + 256u * (uint32_t)h + (uint32_t)(64 * b + 16 * k), d[k]);
+                tmem_wait_ld();
+                if (lane == 0) bulk_wait_read0();   // the previous store has read the staging box
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint32_t* v = d[k] + 8 * hh;
+                        const uint32_t chunk = (uint32_t)((2 * k + hh) ^ (lane & 7));
+                        st_shared_v4(rowb + chunk * 16u,
+                                     pack_bf16(__uint_as_float(v[0]) * sc, __uint_as_float(v[1]) * sc),
+                                     pack_bf16(__uint_as_float(v[2]) * sc, __uint_as_float(v[3]) * sc),
+                                     pack_bf16(__uint_as_float(v[4]) * sc, __uint_as_float(v[5]) * sc),
+                                     pack_bf16(__uint_as_float(v[6]) * sc, __uint_as_float(v[7]) * sc));
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tma_store_2d(&M.dG, 256 * j + 64 * b, row0 + 32 * (warp & 3), stage_box, stream_out);
+            }
+            // accumulator h read: the MMAs of item n_item + 2 may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar0 + 8u * (kEnsAccEmpty + h));
+        }
+    }
+    __syncwarp();
+
+    // ---- teardown: drain own copies, MMAs and stores (bounded), free tensor memory
+    if (warp == 1 && lane == 0) consumed_par = fpar;
+    __syncthreads();
+    if (warp == 0 && lane == 0 && abort_flag) {
+        const uint32_t out = lpar ^ consumed_par;   // at most one load per stage is ahead of the MMAs
+        for (int b = 0; b < kEnsStages; ++b)
+            if ((out >> b) & 1u) (void)mbar_wait_plain(bar0 + 8u * (kEnsFull + b), (consumed_par >> b) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+        mma_commit(bar0 + 8u * kEnsDrain);
+        (void)mbar_wait_plain(bar0 + 8u * kEnsDrain, 0u);
+    }
+    if (warp >= 2 && lane == 0) bulk_wait0();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && abort_flag) {
+        const uint32_t a = (uint32_t)abort_flag;
+        const uint32_t code = (a & 0x40000000u) ? 1u | (((a >> 20) & 0x3fu) << 4) | ((((a & 0xfffffu) - bar0) / 8u) << 12) : 1u;
+        atomicOr(p.err, (int)(code | 0x100000u));   // bit 20: the ensemble dE/dG kernel
     }
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
@@ -984,31 +1247,37 @@ extern "C" __attribute__((visibility("default"))) int mlp_tc_trace_read(unsigned
 }
 #endif
 
+// One map per weight matrix over all nets: rows of (net, element) block
+// k * 7 + s start at (k * 7 + s) * rows-per-block.
 bool make_weight_maps(NetBF16& w) {
-    bool ok = true;
-    ok &= make_map(&w.tmW1, w.W1, kAevLd, (uint64_t)kNSpecies * kH1, kH1);
-    ok &= make_map(&w.tmW2, w.W2, kH1, (uint64_t)kNSpecies * kH2, kH2);
-    ok &= make_map(&w.tmW3, w.W3, kH2, (uint64_t)kNSpecies * kH3, kH3);
-    ok &= make_map(&w.tmW1lo, w.W1lo, kAevLd, (uint64_t)kNSpecies * kH1, kH1);
-    ok &= make_map(&w.tmW2lo, w.W2lo, kH1, (uint64_t)kNSpecies * kH2, kH2);
-    ok &= make_map(&w.tmW3lo, w.W3lo, kH2, (uint64_t)kNSpecies * kH3, kH3);
-    ok &= make_map(&w.tmW3t, w.W3t, kH3, (uint64_t)kNSpecies * kH2, kH2);
-    ok &= make_map(&w.tmW2t, w.W2t, kH2, (uint64_t)kNSpecies * kH1, kH1);
-    ok &= make_map(&w.tmW1t, w.W1t, kH1, (uint64_t)kNSpecies * kAevLd, 256);
+    const uint64_t blocks = (uint64_t)w.n_nets * kNSpecies;
+    bool ok = w.n_nets >= 1;
+    ok &= make_map(&w.tmW1, w.W1, kAevLd, blocks * kH1, kH1);
+    ok &= make_map(&w.tmW2, w.W2, kH1, blocks * kH2, kH2);
+    ok &= make_map(&w.tmW3, w.W3, kH2, blocks * kH3, kH3);
+    ok &= make_map(&w.tmW1lo, w.W1lo, kAevLd, blocks * kH1, kH1);
+    ok &= make_map(&w.tmW2lo, w.W2lo, kH1, blocks * kH2, kH2);
+    ok &= make_map(&w.tmW3lo, w.W3lo, kH2, blocks * kH3, kH3);
+    ok &= make_map(&w.tmW3t, w.W3t, kH3, blocks * kH2, kH2);
+    ok &= make_map(&w.tmW2t, w.W2t, kH2, blocks * kH1, kH1);
+    ok &= make_map(&w.tmW1t, w.W1t, kH1, blocks * kAevLd, 256);
     w.maps_ok = ok;
     return ok;
 }
 
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w, const __nv_bfloat16* G,
                      const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, __nv_bfloat16* dG,
-                     bool backward, int* err_flag) {
+                     __nv_bfloat16* g1, bool backward, int* err_flag) {
     TcMaps M;
+    const bool ens = w.n_nets > 1;
     if (!w.maps_ok || !make_map(&M.G, G, kAevLd, (uint64_t)rows_cap, 128) ||
         (split && (!G_lo || !make_map(&M.Glo, G_lo, kAevLd, (uint64_t)rows_cap, 128))) ||
-        (backward && (!dG || !make_map(&M.dG, dG, kAevLd, (uint64_t)rows_cap, 32)))) {
+        (backward && (!dG || !make_map(&M.dG, dG, kAevLd, (uint64_t)rows_cap, 32))) ||
+        (backward && ens && (!g1 || !make_map(&M.G1, g1, (uint64_t)kH1 * w.n_nets, (uint64_t)rows_cap, 128)))) {
         set_error(-5, "TMA tensor map creation failed");
         return false;
     }
+    if (!(backward && ens)) M.G1 = M.G;   // not used
     if (!split) M.Glo = M.G;
     if (!backward) M.dG = M.G;   // not used
     M.W1 = w.tmW1;
@@ -1022,8 +1291,11 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
     M.W1t = w.tmW1t;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
-        cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+        cudaFuncSetAttribute(k_mlp_b1_ens, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsSmemAlloc);
         attr = true;
     }
     static int sms = 0;
@@ -1035,11 +1307,30 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
     }
     const int tiles = rows_cap / kTileRows;
     const int grid = tiles < sms ? tiles : sms;
-    TcArgs a{ctr, row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, backward ? 1 : 0, err_flag};
-    if (split)
-        MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
-    else
-        MLP_LAUNCH("mlp_tc", st, k_mlp_tc<false><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+    TcArgs a{ctr,   row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, backward ? 1 : 0, w.n_nets, 1.f / (float)w.n_nets,
+             err_flag};
+    if (ens) {
+        if (split)
+            MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true, true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+        else
+            MLP_LAUNCH("mlp_tc", st, k_mlp_tc<false, true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+        if (backward) {
+            // mean dE/dG over the nets: one work item per (tile, 256-column block)
+            EnsMaps EM;
+            EM.G1 = M.G1;
+            EM.W1t = w.tmW1t;
+            EM.dG = M.dG;
+            EnsArgs ea{ctr, w.n_nets, a.inv_nets, err_flag};
+            const int items = 4 * tiles;
+            const int egrid = items < sms ? items : sms;
+            MLP_LAUNCH("mlp_tc_b1_ens", st, k_mlp_b1_ens<<<egrid, kEnsThreads, kEnsSmemAlloc, st>>>(EM, ea));
+        }
+    } else {
+        if (split)
+            MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true, false><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+        else
+            MLP_LAUNCH("mlp_tc", st, k_mlp_tc<false, false><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
+    }
     return true;
 }
 

@@ -263,8 +263,8 @@ void slot_destroy(Slot& s) {
     s = Slot();
 }
 
-int slot_create(Slot& s, const mlp_server_opts& o) {
-    int rc = workspace_create(s.ws, o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0);
+int slot_create(Slot& s, const mlp_server_opts& o, int nets) {
+    int rc = workspace_create(s.ws, o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0, nets);
     if (rc) return rc;
     const size_t A = o.max_batch_atoms, M = o.max_batch_mols;
     const size_t dev = al256(4 * (M + 1)) + al256(sizeof(MolRef) * M) + al256(A) + al256(24 * A) + al256(8 * M) +
@@ -297,9 +297,9 @@ int slot_create(Slot& s, const mlp_server_opts& o) {
     return MLP_OK;
 }
 
-size_t slot_bytes(const mlp_server_opts& o) {
+size_t slot_bytes(const mlp_server_opts& o, int nets) {
     const size_t A = o.max_batch_atoms, M = o.max_batch_mols;
-    return workspace_bytes(o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0) +
+    return workspace_bytes(o.max_batch_atoms, o.max_batch_mols, o.precision, false, kDefaultNbrCap, 0, nets) +
            al256(4 * (M + 1)) + al256(sizeof(MolRef) * M) + al256(A) + al256(24 * A) + al256(8 * M) + al256(12 * A);
 }
 
@@ -489,7 +489,7 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
         return set_error(MLP_ECUDA, "no usable CUDA device");
     }
     init_constants_for_current_device();
-    const size_t sb = slot_bytes(o);
+    const size_t sb = slot_bytes(o, weights_of(w).n_nets);
     long long fit = o.budget_bytes / (long long)sb;
     if (fit < 1)
         return set_error(MLP_ENOMEM, "budget of %lld bytes holds no slot of %zu bytes", (long long)o.budget_bytes, sb);
@@ -507,7 +507,7 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     }
     S->slots.resize(o.streams);
     for (Slot& s : S->slots) {
-        int rc = slot_create(s, o);
+        int rc = slot_create(s, o, weights_of(w).n_nets);
         if (rc) {
             for (Slot& t : S->slots) slot_destroy(t);
             delete S;
@@ -639,7 +639,7 @@ int mlp_server_get_stats(mlp_server* S, mlp_server_stats* out) {
     out->submitted = S->submitted.load();
     out->inflight_bytes = S->inflight_bytes;
     out->mean_batch_atoms = S->st.batches ? (double)S->st.atoms / (double)S->st.batches : 0.0;
-    out->slot_bytes = (int64_t)slot_bytes(S->o);
+    out->slot_bytes = (int64_t)slot_bytes(S->o, weights_of(S->w).n_nets);
     out->slots = (int32_t)S->slots.size();
     return MLP_OK;
 }

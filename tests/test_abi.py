@@ -65,6 +65,20 @@ def test_bad_weight_count_rejected(L):
     assert L.mlp_weights_create(ctypes.byref(host), 9, ctypes.byref(out)) == _lib.MLP_EINVAL
 
 
+def test_weights_binding_checks_ensemble_shape(L):
+    """The binding takes K from the arrays' leading axis and refuses a
+    count that does not match them, before anything reaches the library."""
+    from paper_2310_03121_b300 import api
+
+    w2 = gen.make_weights(nets=2)
+    with pytest.raises(ValueError):
+        api.Weights(w2, n_nets=3)
+    with pytest.raises(ValueError):
+        api.Weights(gen.make_weights(), n_nets=2)
+    with pytest.raises(ValueError):
+        api.Weights({k: v[..., :-1] if k == "W1" else v for k, v in w2.items()})
+
+
 def test_no_gpu_means_error_not_fallback(L):
     """Without a usable device the compute entry points fail (no CPU path)."""
     import torch

@@ -251,12 +251,13 @@ def _split(x):
     return hi.double(), lo.double()
 
 
-def _emulate_bf16_network(wts, sp, G, split=True):
+def _emulate_bf16_network(wts, sp, G, split=True, round_out=True):
     """The tensor-core kernel's arithmetic in float64. Forward GEMMs: BF16
     operands (split = False) or A_hi B_hi + A_lo B_hi + A_hi B_lo from hi/lo
     BF16 pairs (split = True); backward: BF16 operands; celu'(z) of the
     hidden layers recovered from the stored BF16 activation; dE/dG rounded
-    to BF16 on output."""
+    to BF16 on output (one net) or left unrounded (round_out = False: an
+    ensemble member, whose dE/dG leaves the kernel in FP32)."""
     e = np.zeros(len(sp))
     g = np.zeros((len(sp), 1008))
     cel = lambda z: torch.where(z > 0, z, 0.1 * (torch.exp(z / 0.1) - 1))
@@ -283,7 +284,8 @@ def _emulate_bf16_network(wts, sp, G, split=True):
         g3 = _bf16(w4 * torch.where(z3 > 0, torch.ones_like(z3), torch.exp(z3 / 0.1)))
         g2 = _bf16((g3 @ _bf16(W3)) * dcel(h2b))
         g1 = _bf16((g2 @ _bf16(W2)) * dcel(h1b))
-        g[idx] = _bf16(g1 @ _bf16(W1)).numpy()   # dE/dG leaves the kernel as BF16
+        gg = g1 @ _bf16(W1)
+        g[idx] = (_bf16(gg) if round_out else gg).numpy()   # one net: dE/dG leaves the kernel as BF16
     return e, g
 
 
