@@ -15,9 +15,11 @@ e2e    the same stream through the C-ABI server (mlp_server_replay_clients
        with --e2e-clients native client threads: host coordinates in, host
        energies and forces out, every request due at t = 0), wall time of the
        median of three runs after a warm-up run; p50/p99 request latency.
-Also reported: Poisson-arrival latency sweep, the one-molecule-per-launch
-FP32 path, the roofline of the dominant kernel and the FP64 oracle on the
-host cores (cpu_baseline).
+Also reported: the same device-resident stream with an ensemble of
+--ensemble-nets nets (energy = mean of the nets, forces = mean gradient),
+Poisson-arrival latency sweep, the one-molecule-per-launch FP32 path, the
+roofline of the dominant kernel and the FP64 oracle on the host cores
+(cpu_baseline). --nets K makes the ensemble the headline model instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -419,8 +421,14 @@ def term_counts(stream):
 # kernel source whose SHA-1 is given; reported as `traffic` only while the
 # source is unchanged (otherwise null: the counters no longer describe it).
 MEASURED_TRAFFIC = {
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "a7ec9b769ac00b5f640729099c15318b01970572",
-               "bytes_per_atom": (603.203584e6 + 236.504832e6) / 131056},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
+    # launch (profiles/); valid only while the kernel source is the one that was captured
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
+               "bytes_per_atom": (597.866496e6 + 221.936896e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
+                 "bytes_per_atom": (599.007488e6 + 246.604032e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
+                        "bytes_per_atom": (300.643840e6 + 108.841728e6) / 65518},
 }
 
 
