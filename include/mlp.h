@@ -142,6 +142,78 @@ MLP_API int mlp_energy_forces(mlp_system *s, const double *coords, double *energ
 MLP_API int mlp_energy_forces_device(mlp_system *s, const double *d_coords, double *d_energy, float *d_forces,
                              void *stream);
 
+/* ML/MM mechanical embedding (paper, section "OpenMM-ML": a mixed system
+ * models a listed subset of the atoms with the MLP and everything else,
+ * including the interaction between the two regions, with a conventional
+ * force field that the caller supplies). s holds the n ML-region atoms
+ * (created with their elements, in the order of d_index); d_index [n] int32
+ * (device) gives their rows in d_coords_full [n_full][3] FP64 (device). One
+ * evaluation, asynchronous on `stream`: the region's positions are gathered
+ * into the system's own buffer (they become its stored positions), the
+ * region is evaluated on its own (the system's cell or open boundary),
+ * d_energy (FP64 scalar) receives the ML energy, and the ML forces go to rows
+ * d_index of d_forces_full [n_full][3] FP32 (device; may be NULL): added to
+ * what the caller placed there when accumulate != 0 (e.g. the classical
+ * forces), written over those rows otherwise; other rows are not touched.
+ * Returns MLP_EINVAL for NULL arguments or n_full outside [n, 2^31). An index
+ * outside [0, n_full) is flagged on the device (its row is skipped) and
+ * reported as MLP_EINVAL by the next call or mlp_sync; indices must be
+ * distinct (a repeated row would be updated twice). */
+MLP_API int mlp_energy_forces_subset_device(mlp_system *s, const double *d_coords_full, int64_t n_full,
+                                            const int32_t *d_index, double *d_energy, float *d_forces_full,
+                                            int accumulate, void *stream);
+
+/* ------------------------------------------------------------------ dynamics */
+
+/* Langevin dynamics of a system with the LF-Middle discretization (paper,
+ * section "New Integrators"; the ML runs of section "Performance of MLPs",
+ * Table 3, use a Langevin integrator with a 2 fs step). Velocities live at
+ * half steps; one step from forces F(x_t) (eV/A), masses m (amu) of the
+ * elements (H 1.008, C 12.011, N 14.007, O 15.999, S 32.06, F 18.998,
+ * Cl 35.45):
+ *   v <- v + dt F / m;  x <- x + dt/2 v;  v <- a v + sqrt((1 - a^2) kT / m) R;
+ *   x <- x + dt/2 v;    a = exp(-friction dt)
+ * in A, fs, amu, eV (F / m: 1 eV/(A amu) = 9.648533212e-3 A/fs^2; kT / m:
+ * 1 eV/amu = 1 / 103.6426965 A^2/fs^2; k_B = 8.617333262e-5 eV/K). The three
+ * normal deviates R of atom i at step t come from Philox4x64-10 (Salmon et
+ * al., SC 2011) with counter (t, i, 0, 0) and key (seed, 0): its words w0..w3
+ * give u_q = (w_q >> 11) 2^-53 and, by Box-Muller, R = sqrt(-2 ln(1 - u0))
+ * (cos 2 pi u1, sin 2 pi u1) and sqrt(-2 ln(1 - u2)) cos 2 pi u3. A trajectory
+ * is therefore a function of (x0, v0, seed, first step index) only. */
+typedef struct mlp_langevin mlp_langevin;
+typedef struct {
+    double dt_fs;            /* step, > 0 */
+    double friction_per_ps;  /* gamma >= 0 (0: leapfrog, no thermostat) */
+    double temperature_K;    /* >= 0 */
+    uint64_t seed;           /* Philox key */
+    int use_graph;           /* != 0: capture one step as a CUDA graph and replay it */
+} mlp_langevin_params;
+
+/* Creates an integrator for system s (which it uses for the forces; s must
+ * outlive it). MLP_EINVAL for NULL arguments or dt <= 0, friction < 0,
+ * temperature < 0; MLP_ENOMEM. */
+MLP_API int mlp_langevin_create(mlp_system *s, const mlp_langevin_params *p, mlp_langevin **out);
+MLP_API void mlp_langevin_destroy(mlp_langevin *L);
+
+/* Runs n_steps steps after the work queued on `stream` and waits for them
+ * (graph mode replays on the integrator's own stream): d_x [n][3] and d_v
+ * [n][3] FP64 (device; positions in A, velocities in A/fs at the half step
+ * before), updated in place; steps are numbered step0 .. step0 + n_steps - 1
+ * (the Philox counter); d_energy (device FP64 [n_steps], may be NULL)
+ * receives the potential energy at the start of each step. With use_graph
+ * the first run on a buffer set captures one step and every later step is a
+ * graph replay (re-captured when d_x, d_v or d_energy change).
+ * The system's neighbor list is rebuilt on the first step and then, with a
+ * skin, whenever an atom has moved more than half the skin (device check);
+ * without a skin on every step. Errors of any step (neighbor capacity,
+ * network kernel) are reported at the end of the run. */
+MLP_API int mlp_langevin_run(mlp_langevin *L, double *d_x, double *d_v, int64_t step0, int32_t n_steps,
+                             double *d_energy, void *stream);
+
+/* Kernel-level access for tests: the three normal deviates of atoms 0..n-1
+ * at step `step` (host FP64 [n][3] out), from the device generator. */
+MLP_API int mlp_debug_langevin_normals(uint64_t seed, int64_t step, int32_t n, double *normals);
+
 /* Forward only (autograd forward): d_energy = E(d_coords). keep_aev != 0
  * keeps the AEVs on the device for a following mlp_backward_device on the
  * same coordinates; otherwise the backward recomputes them. */

@@ -18,6 +18,10 @@ Parity status per function (what pins it, from tests/test_oracle.py):
                                       ensemble: K copies of one net, net-by-net means
   oracle_energy_forces .............. central finite differences, zero net force/torque
   oracle_forces_subset / local energy  equality with the full evaluation
+  oracle_ml_region .................. invariance to the classical region, zero rows, finite differences
+  oracle_philox4x64 ................. numpy.random.Philox (the same published generator)
+  oracle_langevin_normals ........... moments and quantiles of the normal distribution
+  oracle_lfmiddle_step .............. leapfrog invariant (no friction), equipartition and velocity decay
 """
 from __future__ import annotations
 
@@ -92,6 +96,20 @@ def lib():
                                            _dp, ctypes.c_int]
         L.oracle_aev_subset.restype = None
         L.oracle_aev_subset.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.c_int, _ip, _dp]
+        u64 = ctypes.c_uint64
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.oracle_philox4x64.restype = None
+        L.oracle_philox4x64.argtypes = [u64p, u64p, u64p]
+        L.oracle_langevin_normals.restype = None
+        L.oracle_langevin_normals.argtypes = [u64, ctypes.c_int64, ctypes.c_int, _dp]
+        L.oracle_lfmiddle_step.restype = None
+        L.oracle_lfmiddle_step.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, u64, ctypes.c_int64]
+        L.oracle_langevin_run.restype = None
+        L.oracle_langevin_run.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, ctypes.POINTER(_Weights), ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, u64, ctypes.c_int64, ctypes.c_int, _dp]
+        L.oracle_ml_region.restype = ctypes.c_double
+        L.oracle_ml_region.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), ctypes.c_int, _ip, _dp]
         L.oracle_energy_forces_batch.restype = None
         L.oracle_energy_forces_batch.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_long), _ip, _dp, _dp,
                                                  ctypes.POINTER(_Weights), _dp, _dp, ctypes.c_int]
@@ -222,6 +240,62 @@ def energy_forces(species, coords, cell, w, per_atom=False):
     c = _cell(cell)
     E = lib().oracle_energy_forces(n, _i(s), _d(x), None if c is None else _d(c), w.ref(), _d(e), _d(F))
     return (E, F, e) if per_atom else (E, F)
+
+
+def philox4x64(counter, key):
+    """Philox4x64-10 block: 4 uint64 words of counter (4 words) under key (2 words)."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    p = ctypes.POINTER(ctypes.c_uint64)
+    lib().oracle_philox4x64(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def langevin_normals(seed, step, n):
+    """Normal deviates [n, 3] of atoms 0..n-1 at `step` (Philox counter (step, i), key (seed, 0))."""
+    out = np.zeros((n, 3))
+    for i in range(n):
+        lib().oracle_langevin_normals(int(seed), int(step), i, _d(out[i]))
+    return out
+
+
+def lfmiddle_step(species, x, v, F, dt, friction_per_ps, temperature, seed, step):
+    """One LF-Middle update from forces F; returns new (x, v)."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    F = _f64(F)
+    s = _i32(species)
+    lib().oracle_lfmiddle_step(s.shape[0], _i(s), _d(x), _d(v), _d(F), float(dt), float(friction_per_ps),
+                               float(temperature), int(seed), int(step))
+    return x, v
+
+
+def langevin_run(species, x, v, cell, w, dt, friction_per_ps, temperature, seed, step0, n_steps):
+    """n_steps LF-Middle steps with the oracle's forces: (x, v, E_pot[n_steps])."""
+    w = _as_weights(w)
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    s = _i32(species)
+    E = np.zeros(max(1, n_steps))
+    c = _cell(cell)
+    lib().oracle_langevin_run(s.shape[0], _i(s), _d(x), _d(v), None if c is None else _d(c), w.ref(), float(dt),
+                              float(friction_per_ps), float(temperature), int(seed), int(step0), int(n_steps), _d(E))
+    return x, v, E[:n_steps]
+
+
+def ml_region(species, coords, cell, w, index):
+    """ML part of a mechanically embedded system: (E_ML, F_full[n_full, 3])
+    with the subset's forces in rows `index` and zeros elsewhere."""
+    w = _as_weights(w)
+    x = _f64(coords)
+    s = _i32(species)
+    idx = _i32(index)
+    F = np.zeros_like(x)
+    c = _cell(cell)
+    E = lib().oracle_ml_region(x.shape[0], _i(s), _d(x), None if c is None else _d(c), w.ref(), idx.shape[0],
+                               _i(idx), _d(F))
+    return E, F
 
 
 def aev_grad(species, coords, cell, w):

@@ -44,6 +44,7 @@
  * value for random-init weights has no published number.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
@@ -490,6 +491,32 @@ double oracle_local_energy(int n, const int *species, const double *xyz, const d
     return E;
 }
 
+/* ML/MM mechanical embedding (section "OpenMM-ML": a listed subset of the
+ * atoms is modeled by the MLP; the rest, and the interaction between the two
+ * regions, by a conventional force field). The ML part of the energy is the
+ * potential of the subset alone: E_ML = E(species[index], xyz[index]) with the
+ * system's cell; its forces act on the subset only. F_full[n_full][3] receives
+ * them in rows index[q] and zeros everywhere else. */
+double oracle_ml_region(int n_full, const int *species, const double *xyz, const double *cell,
+                        const oracle_weights *w, int n_ml, const int *index, double *F_full)
+{
+    int *sp = (int *)malloc(sizeof(int) * (n_ml > 0 ? n_ml : 1));
+    double *x = (double *)malloc(sizeof(double) * 3 * (n_ml > 0 ? n_ml : 1));
+    double *F = (double *)malloc(sizeof(double) * 3 * (n_ml > 0 ? n_ml : 1));
+    for (int q = 0; q < n_ml; ++q) {
+        sp[q] = species[index[q]];
+        for (int c = 0; c < 3; ++c) x[3 * q + c] = xyz[3 * index[q] + c];
+    }
+    double E = oracle_energy_forces(n_ml, sp, x, cell, w, NULL, F);
+    for (int c = 0; c < 3 * n_full; ++c) F_full[c] = 0.0;
+    for (int q = 0; q < n_ml; ++q)
+        for (int c = 0; c < 3; ++c) F_full[3 * index[q] + c] = F[3 * q + c];
+    free(sp);
+    free(x);
+    free(F);
+    return E;
+}
+
 /* Independent molecules back to back (atoms mol_start[m] .. mol_start[m+1]),
  * each evaluated by oracle_energy_forces; cells[3 m] per molecule or NULL.
  * Molecules are spread over nthreads OpenMP threads when built with OpenMP. */
@@ -541,6 +568,110 @@ void oracle_aev_subset(int n, const int *species, const double *xyz, const doubl
     int *nb = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
     for (int q = 0; q < nidx; ++q) aev_atom(idx[q], n, species, xyz, cell, nb, G_out + (size_t)AEV_LEN * q);
     free(nb);
+}
+
+/* ------------------------------------------------------------ Langevin dynamics */
+/* Section "New Integrators": the LF-Middle discretization of the Langevin
+ * equation; section "Performance of MLPs" (Table 3): the ML simulations run
+ * with a Langevin integrator and a 2 fs step. One step, velocities at half
+ * steps (leapfrog), forces F(x_t):
+ *   v <- v + dt F / m                      (v: t - dt/2 -> t + dt/2)
+ *   x <- x + (dt / 2) v
+ *   v <- a v + sqrt((1 - a^2) kT / m) R,   a = exp(-gamma dt), R ~ N(0, 1)
+ *   x <- x + (dt / 2) v
+ * Units: A, fs, amu, eV; F / m in eV / (A amu) = 9.648533212e-3 A / fs^2;
+ * kT / m in eV / amu = 1 / 103.6426965 A^2 / fs^2.
+ * The normal deviates are drawn from Philox4x64-10 (Salmon, Moraes, Dror,
+ * Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011): atom i at
+ * step t uses counter (t, i, 0, 0) and key (seed, 0); its four 64-bit words
+ * give uniforms u = (w >> 11) 2^-53 and, by Box-Muller on the pairs (0, 1)
+ * and (2, 3), normals R_x, R_y, R_z (the fourth is unused):
+ *   r = sqrt(-2 ln(1 - u_a)), R = r cos(2 pi u_b), r sin(2 pi u_b). */
+
+static const double LGV_ACC = 9.648533212e-3;
+static const double LGV_KE = 103.6426965;
+static const double LGV_KB = 8.617333262e-5;
+static const double LGV_MASS[NSP] = {1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45};
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+/* Philox4x64 with 10 rounds (the published definition). */
+void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ull, c0, &hi0, &lo0);
+        mulhilo64(0xCA5A826395121157ull, c2, &hi1, &lo1);
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ull; /* Weyl sequence: golden ratio */
+        k1 += 0xBB67AE8584CAA73Bull; /* sqrt(3) - 1 */
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* The three normal deviates of atom i at step t (see above). */
+void oracle_langevin_normals(uint64_t seed, int64_t step, int atom, double R[3])
+{
+    const uint64_t ctr[4] = {(uint64_t)step, (uint64_t)atom, 0, 0}, key[2] = {seed, 0};
+    uint64_t w[4];
+    oracle_philox4x64(ctr, key, w);
+    double u[4];
+    for (int q = 0; q < 4; ++q) u[q] = (double)(w[q] >> 11) * 0x1.0p-53;
+    const double r0 = sqrt(-2.0 * log(1.0 - u[0])), r1 = sqrt(-2.0 * log(1.0 - u[2]));
+    R[0] = r0 * cos(2.0 * M_PI * u[1]);
+    R[1] = r0 * sin(2.0 * M_PI * u[1]);
+    R[2] = r1 * cos(2.0 * M_PI * u[3]);
+}
+
+/* One LF-Middle update of n atoms from forces F (eV / A); dt in fs, gamma in
+ * 1 / ps, temperature in K. x and v are updated in place. */
+void oracle_lfmiddle_step(int n, const int *species, double *x, double *v, const double *F, double dt,
+                          double gamma_per_ps, double temperature, uint64_t seed, int64_t step)
+{
+    const double a = exp(-gamma_per_ps * 1e-3 * dt);
+    const double kT = LGV_KB * temperature;
+    for (int i = 0; i < n; ++i) {
+        const double m = LGV_MASS[species[i]];
+        const double sig = sqrt((1.0 - a * a) * kT / (m * LGV_KE));
+        double R[3];
+        oracle_langevin_normals(seed, step, i, R);
+        for (int c = 0; c < 3; ++c) {
+            double vv = v[3 * i + c] + dt * F[3 * i + c] * LGV_ACC / m;
+            double xx = x[3 * i + c] + 0.5 * dt * vv;
+            vv = a * vv + sig * R[c];
+            xx += 0.5 * dt * vv;
+            v[3 * i + c] = vv;
+            x[3 * i + c] = xx;
+        }
+    }
+}
+
+/* n_steps LF-Middle steps with the oracle's forces, starting at step index
+ * step0; E_pot[s] = potential energy at the start of step s (may be NULL). */
+void oracle_langevin_run(int n, const int *species, double *x, double *v, const double *cell,
+                         const oracle_weights *w, double dt, double gamma_per_ps, double temperature,
+                         uint64_t seed, int64_t step0, int n_steps, double *E_pot)
+{
+    double *F = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    for (int s = 0; s < n_steps; ++s) {
+        const double E = oracle_energy_forces(n, species, x, cell, w, NULL, F);
+        if (E_pot) E_pot[s] = E;
+        oracle_lfmiddle_step(n, species, x, v, F, dt, gamma_per_ps, temperature, seed, step0 + s);
+    }
+    free(F);
 }
 
 int oracle_aev_length(void) { return AEV_LEN; }

@@ -10,5 +10,5 @@ the binding raises ImportError (build it with
 `python -m paper_2310_03121_b300.build`).
 """
 from ._lib import MLP_BF16, MLP_FP32, MLPError, load  # noqa: F401
-from .api import (Batch, Server, System, Weights, debug_network, fail_next_allocation,  # noqa: F401
-                  launch_count, profile_enable, profile_read, profile_reset)
+from .api import (Batch, Langevin, Server, System, Weights, debug_langevin_normals, debug_network,  # noqa: F401
+                  fail_next_allocation, launch_count, profile_enable, profile_read, profile_reset)

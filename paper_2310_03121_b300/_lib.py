@@ -43,6 +43,11 @@ class Cutoffs(ctypes.Structure):
     _fields_ = [("rc_rad", ctypes.c_double), ("rc_ang", ctypes.c_double), ("skin", ctypes.c_double)]
 
 
+class LangevinParams(ctypes.Structure):
+    _fields_ = [("dt_fs", ctypes.c_double), ("friction_per_ps", ctypes.c_double), ("temperature_K", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("use_graph", ctypes.c_int)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_batch_atoms", ctypes.c_int32), ("max_batch_mols", ctypes.c_int32),
                 ("max_atoms_per_mol", ctypes.c_int32), ("streams", ctypes.c_int32),
@@ -75,6 +80,7 @@ SIGNATURES = {
     "mlp_destroy": (None, [vp]),
     "mlp_energy_forces": (ip, [vp, dp, dp, fp]),
     "mlp_energy_forces_device": (ip, [vp, vp, vp, vp, vp]),
+    "mlp_energy_forces_subset_device": (ip, [vp, vp, i64, vp, vp, vp, ip, vp]),
     "mlp_forward_device": (ip, [vp, vp, vp, ip, vp]),
     "mlp_backward_device": (ip, [vp, vp, vp, vp, vp]),
     "mlp_sync": (ip, [vp]),
@@ -105,6 +111,10 @@ SIGNATURES = {
     "mlp_debug_aev": (ip, [vp, fp]),
     "mlp_debug_atom_energies": (ip, [vp, fp, fp]),
     "mlp_debug_network": (ip, [vp, ip, i32, i8p, fp, fp, fp]),
+    "mlp_langevin_create": (ip, [vp, ctypes.POINTER(LangevinParams), ctypes.POINTER(vp)]),
+    "mlp_langevin_destroy": (None, [vp]),
+    "mlp_langevin_run": (ip, [vp, vp, vp, i64, i32, vp, vp]),
+    "mlp_debug_langevin_normals": (ip, [u64, i64, i32, dp]),
 }
 
 _lib = None

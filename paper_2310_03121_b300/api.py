@@ -125,6 +125,29 @@ class System:
                                               _stream_ptr(stream)), "mlp_energy_forces_device")
         return energy, forces
 
+    def energy_forces_subset_device(self, coords_full, index, forces_full=None, energy=None, accumulate=True,
+                                    stream=None):
+        """ML/MM mechanical embedding (mlp_energy_forces_subset_device): this
+        system is the ML region; `index` (torch.int32 [n] on CUDA) gives its
+        rows in `coords_full` (torch.float64 [n_full,3] on CUDA). The ML forces
+        go to those rows of `forces_full` (float32 [n_full,3], created zeroed
+        if None), added to its contents when `accumulate`. Returns
+        (E float64 [1], forces_full)."""
+        import torch
+
+        assert coords_full.is_cuda and coords_full.dtype == torch.float64 and coords_full.is_contiguous()
+        assert index.is_cuda and index.dtype == torch.int32 and index.is_contiguous() and index.numel() == self.n
+        n_full = coords_full.shape[0]
+        if energy is None:
+            energy = torch.empty(1, dtype=torch.float64, device=coords_full.device)
+        if forces_full is None:
+            forces_full = torch.zeros((n_full, 3), dtype=torch.float32, device=coords_full.device)
+        assert forces_full.dtype == torch.float32 and forces_full.is_contiguous() and forces_full.shape[0] == n_full
+        check(load().mlp_energy_forces_subset_device(self.handle, _tptr(coords_full), int(n_full), _tptr(index),
+                                                     _tptr(energy), _tptr(forces_full), 1 if accumulate else 0,
+                                                     _stream_ptr(stream)), "mlp_energy_forces_subset_device")
+        return energy, forces_full
+
     def forward_device(self, coords, energy, keep_aev=True, stream=None):
         check(load().mlp_forward_device(self.handle, _tptr(coords), _tptr(energy), int(bool(keep_aev)),
                                         _stream_ptr(stream)), "mlp_forward_device")
@@ -170,6 +193,50 @@ class System:
         except Exception:
             pass
 
+
+class Langevin:
+    """LF-Middle Langevin dynamics of a System (mlp_langevin_*): positions
+    and velocities stay on the device (torch.float64 [n, 3]); run() advances
+    them in place and returns the potential energy at the start of each step.
+    Units: A, fs, amu, eV; friction in 1/ps, temperature in K."""
+
+    def __init__(self, system, dt_fs=2.0, friction_per_ps=1.0, temperature_K=300.0, seed=0, use_graph=True):
+        L = load()
+        self.system = system
+        p = _lib.LangevinParams(float(dt_fs), float(friction_per_ps), float(temperature_K), int(seed),
+                                1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        check(L.mlp_langevin_create(system.handle, ctypes.byref(p), ctypes.byref(h)), "mlp_langevin_create")
+        self.handle = h
+
+    def run(self, x, v, step0, n_steps, energies=True, stream=None):
+        import torch
+
+        for t in (x, v):
+            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.shape == (self.system.n, 3)
+        E = torch.empty(max(1, n_steps), dtype=torch.float64, device=x.device) if energies else None
+        check(load().mlp_langevin_run(self.handle, _tptr(x), _tptr(v), int(step0), int(n_steps),
+                                      None if E is None else _tptr(E), _stream_ptr(stream)), "mlp_langevin_run")
+        return E[:n_steps] if E is not None else None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().mlp_langevin_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def debug_langevin_normals(seed, step, n):
+    """The device generator's normal deviates of atoms 0..n-1 at `step` ([n, 3])."""
+    out = np.zeros((n, 3))
+    check(load().mlp_debug_langevin_normals(int(seed), int(step), int(n), out.ctypes.data_as(ctypes.POINTER(
+        ctypes.c_double))), "mlp_debug_langevin_normals")
+    return out
 
 class Batch:
     """Many small open-boundary molecules per launch sequence (mlp_batch_create)."""

@@ -23,7 +23,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I", os.path.join(ROOT, "include")]
 
 SOURCES = ["runtime.cu", "engine.cu", "kernels_nbr.cu", "kernels_aev.cu", "kernels_mlp_f32.cu",
-           "kernels_mlp_tc.cu", "kernels_misc.cu", "api.cu", "server.cu", "noalloc.cu"]
+           "kernels_mlp_tc.cu", "kernels_misc.cu", "api.cu", "server.cu", "noalloc.cu", "integrator.cu"]
 
 
 def _headers():

@@ -11,38 +11,9 @@
 
 #include "../../include/mlp.h"
 #include "engine.cuh"
+#include "system.cuh"
 
 using namespace mlp;
-
-struct mlp_weights {
-    DevWeights dw;
-};
-
-struct mlp_system {
-    int n = 0;
-    int periodic = 0;
-    double L[3] = {0, 0, 0};
-    mlp_cutoffs cut{};
-    const mlp_weights* w = nullptr;
-    int precision = 0;
-    Workspace ws;
-    cudaStream_t stream = nullptr;
-    int8_t* d_species = nullptr;
-    double* d_xyz = nullptr;
-    double* d_E = nullptr;
-    float* d_F = nullptr;
-    double* h_xyz = nullptr;   // pinned staging
-    double* h_E = nullptr;
-    float* h_F = nullptr;
-    void* dev_block = nullptr;
-    long long calls = 0;
-    int rebuild_interval = 10;
-    bool kept = false;
-    const double* kept_coords = nullptr;
-    bool nbr_valid = false;
-    cudaEvent_t done = nullptr;
-    bool pending = false;   // counters of an asynchronous call not yet checked
-};
 
 struct mlp_batch {
     int precision = 0;
@@ -70,7 +41,7 @@ namespace mlp {
 const DevWeights& weights_of(const mlp_weights* w) { return w->dw; }
 }  // namespace mlp
 
-namespace {
+namespace mlp {
 
 int check_cuda_device() {
     int count = 0;
@@ -83,25 +54,25 @@ int check_cuda_device() {
     return MLP_OK;
 }
 
-inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
-
-// float -> bf16 (round to nearest even) on the host
-inline __nv_bfloat16 to_bf16(float f) { return __float2bfloat16_rn(f); }
-
 int sys_finish_pending(mlp_system* s) {
     if (!s->pending) return MLP_OK;
     cudaError_t e = cudaEventSynchronize(s->done);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize");
     s->pending = false;
     int rc = check_counters(s->ws);
-    if (rc) return rc;
+    if (rc) {   // reported now: not again as an earlier evaluation's error
+        cudaMemset(s->ws.err_sticky, 0, sizeof(int));
+        cudaStreamSynchronize(nullptr);
+        return rc;
+    }
     // errors of earlier evaluations that were not checked one by one
     int sticky = 0;
     e = cudaMemcpy(&sticky, s->ws.err_sticky, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(error flags)");
     if (sticky) {
         cudaMemset(s->ws.err_sticky, 0, sizeof(int));
-        if (sticky & 4) return set_error(MLP_EINVAL, "element code outside [0, 7) in an earlier evaluation");
+        if (sticky & 4)
+            return set_error(MLP_EINVAL, "bad input (element code or ML-region index) in an earlier evaluation");
         if (sticky & 8) return set_error(MLP_ECUDA, "tensor-core network kernel error in an earlier evaluation");
         return set_error(MLP_EOVERFLOW, "neighbor capacity exceeded in an earlier evaluation");
     }
@@ -117,8 +88,22 @@ int sys_check_if_done(mlp_system* s) {
     if (q == cudaErrorNotReady) return MLP_OK;
     if (q != cudaSuccess) return cuda_error(q, "cudaEventQuery");
     s->pending = false;
-    return check_counters(s->ws);
+    const int rc = check_counters(s->ws);
+    if (rc) {   // reported now, not again later (error path only: clear before any new launch)
+        cudaMemset(s->ws.err_sticky, 0, sizeof(int));
+        cudaStreamSynchronize(nullptr);
+    }
+    return rc;
 }
+
+}  // namespace mlp
+
+namespace {
+
+inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+// float -> bf16 (round to nearest even) on the host
+inline __nv_bfloat16 to_bf16(float f) { return __float2bfloat16_rn(f); }
 
 int sys_make_workspace(mlp_system* s, int nbr_cap) {
     // open systems: at most ~2 cells per atom plus slack
@@ -135,6 +120,9 @@ int sys_make_workspace(mlp_system* s, int nbr_cap) {
     return MLP_OK;
 }
 
+}  // namespace
+
+namespace mlp {
 EvalSpec sys_spec(mlp_system* s, const double* d_xyz) {
     EvalSpec sp;
     sp.n_atoms = s->n;
@@ -150,6 +138,9 @@ EvalSpec sys_spec(mlp_system* s, const double* d_xyz) {
     return sp;
 }
 
+}  // namespace mlp
+
+namespace {
 int sys_enqueue(mlp_system* s, EvalSpec& sp, cudaStream_t st) {
     int rc = enqueue_eval(s->ws, s->w->dw, sp, st);
     if (rc) return rc;
@@ -481,6 +472,26 @@ int mlp_energy_forces_device(mlp_system* s, const double* d_coords, double* d_en
     EvalSpec sp = sys_spec(s, d_coords);
     sp.d_E = d_energy;
     sp.d_F = d_forces;
+    return sys_enqueue(s, sp, static_cast<cudaStream_t>(stream));
+}
+
+int mlp_energy_forces_subset_device(mlp_system* s, const double* d_coords_full, int64_t n_full,
+                                    const int32_t* d_index, double* d_energy, float* d_forces_full, int accumulate,
+                                    void* stream) {
+    clear_error();
+    if (!s || !d_coords_full || !d_index || !d_energy) return set_error(MLP_EINVAL, "NULL argument");
+    if (n_full < s->n || n_full > (int64_t)INT32_MAX)
+        return set_error(MLP_EINVAL, "n_full %lld outside [%d, 2^31)", (long long)n_full, s->n);
+    int rc = sys_check_if_done(s);
+    if (rc) return rc;
+    s->kept = false;
+    EvalSpec sp = sys_spec(s, s->d_xyz);   // the region's positions: gathered into the system's own buffer
+    sp.d_index = d_index;
+    sp.d_coords_full = d_coords_full;
+    sp.n_full = n_full;
+    sp.accumulate = accumulate != 0;
+    sp.d_E = d_energy;
+    sp.d_F = d_forces_full;
     return sys_enqueue(s, sp, static_cast<cudaStream_t>(stream));
 }
 

@@ -65,7 +65,7 @@ struct Counters {
     int species[8];        // atoms per element
     int nbr_overflow;      // largest neighbor count seen above capacity (0 = fine)
     int ang_overflow;      // largest radial/angular count above the staging limits (0 = fine)
-    int bad_species;       // 1 if an element code outside [0, 7) was seen
+    int bad_species;       // bad input: 1 element code outside [0, 7), 2 molecule offsets, 4 ML-region index
     int rebuild;           // 1 if this evaluation rebuilds the neighbor list
     int net_error;         // tensor-core network kernel gave up on a bounded wait (0 = fine; else a code)
     int pad[3];

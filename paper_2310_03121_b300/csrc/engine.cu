@@ -190,6 +190,9 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     if (!sp.reuse_aev) {
         ce = cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st);
         if (ce != cudaSuccess) return cuda_error(ce, "cudaMemsetAsync(counters)");
+        if (sp.d_index)
+            launch_gather_subset(st, n, sp.d_index, sp.d_coords_full, sp.n_full, const_cast<double*>(sp.d_xyz),
+                                 ws.ctr);
         NbrArgs na{ws.hi, ws.lo, ws.nbr, ws.nbr_cnt, ws.nbr_cap, sp.r_list * sp.r_list};
         if (batch) {
             launch_stage_batch(st, sp.n_mols, n, sp.d_mol_start, sp.d_xyz, sp.d_species, ws.hi, ws.lo, ws.rank,
@@ -228,7 +231,8 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.dG16, ws.grad, fast);
     launch_finalize(st, sp.n_mols, sp.d_mol_start, n, ws.e, ws.grad, sp.energy ? sp.d_E : nullptr,
-                    sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign, ws.ctr, ws.err_sticky);
+                    sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign, ws.ctr, ws.err_sticky,
+                    sp.d_index, sp.n_full, sp.accumulate);
     ce = cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (ce != cudaSuccess) return cuda_error(ce, "cudaMemcpyAsync(counters)");
     ce = cudaGetLastError();
@@ -240,6 +244,7 @@ int check_counters(const Workspace& ws) {
     const Counters& c = *ws.h_ctr;
     if (c.bad_species & 1) return set_error(-1, "element code outside [0, 7) in the input");
     if (c.bad_species & 2) return set_error(-1, "molecule offsets do not partition [0, n_atoms)");
+    if (c.bad_species & 4) return set_error(-1, "ML-region index outside [0, n_full)");
     if (c.nbr_overflow)
         return set_error(-7, "neighbor list overflow: an atom has %d neighbors (capacity %d)", c.nbr_overflow,
                          ws.nbr_cap);

@@ -100,6 +100,14 @@ struct EvalSpec {
     float* d_F = nullptr;               // [n_atoms][3]
     const double* d_grad_scale = nullptr;
     float sign = -1.f;                  // -1: forces; +1: energy gradient
+    // ML/MM region: d_xyz (n_atoms rows, owned by the caller of enqueue_eval)
+    // is first gathered from rows d_index of d_coords_full [n_full][3], and
+    // the forces go to rows d_index of d_F (n_full rows), added when
+    // accumulate is set
+    const int* d_index = nullptr;
+    const double* d_coords_full = nullptr;
+    long long n_full = 0;
+    bool accumulate = false;
 };
 
 // Enqueues one evaluation on `st`; returns MLP_OK or an error code (argument

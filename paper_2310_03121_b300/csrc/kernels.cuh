@@ -121,12 +121,20 @@ void launch_gather_batch(cudaStream_t st, int n_mols, const MolRef* refs, const 
 void launch_scatter_results(cudaStream_t st, int n_mols, const MolRef* refs, const int* mol_start, const double* d_E,
                             const float* d_F);
 
+// ---- ML/MM region (kernels_misc.cu): xyz[q] = coords_full[index[q]]; an
+// index outside [0, n_full) sets bad-input flag 4 and its row is zero.
+void launch_gather_subset(cudaStream_t st, int n, const int* index, const double* coords_full, long long n_full,
+                          double* xyz, Counters* ctr);
+
 // ---- finalize (kernels_misc.cu)
 // Also ORs this evaluation's error flags (1 neighbor overflow, 2 AEV staging
-// overflow, 4 bad element code, 8 network kernel error) into *sticky when
-// sticky != nullptr.
+// overflow, 4 bad input, 8 network kernel error) into *sticky when
+// sticky != nullptr. With F_index, force row i goes to row F_index[i] of F
+// (n_full rows; rows outside [0, n_full) skipped), added to it when
+// accumulate is set.
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,
-                     const Counters* ctr, int* sticky);
+                     const Counters* ctr, int* sticky, const int* F_index = nullptr, long long n_full = 0,
+                     bool accumulate = false);
 
 }  // namespace mlp

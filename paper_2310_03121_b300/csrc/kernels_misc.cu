@@ -15,7 +15,8 @@ constexpr int kEBlock = 128;
 __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_atoms, const float* __restrict__ e,
                            const double* __restrict__ grad, double* __restrict__ E, float* __restrict__ F,
                            const double* __restrict__ grad_scale, float sign, const Counters* __restrict__ ctr,
-                           int* __restrict__ sticky) {
+                           int* __restrict__ sticky, const int* __restrict__ F_index, long long n_full,
+                           int accumulate) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && sticky) {
         // error flags of this evaluation, kept until the host reads and clears them
         const int f = (ctr->nbr_overflow ? 1 : 0) | (ctr->ang_overflow ? 2 : 0) | (ctr->bad_species ? 4 : 0) |
@@ -44,7 +45,33 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
     if (!F) return;
     const int fb = blockIdx.x - n_mols;
     const int nfb = gridDim.x - n_mols;
-    for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) F[q] = (float)(scale * grad[q]);
+    if (!F_index) {
+        for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) F[q] = (float)(scale * grad[q]);
+        return;
+    }
+    // ML/MM region: into the full system's force rows
+    for (int q = fb * kEBlock + threadIdx.x; q < 3 * n_atoms; q += nfb * kEBlock) {
+        const int i = q / 3, c = q - 3 * i;
+        const int row = F_index[i];
+        if (row < 0 || (long long)row >= n_full) continue;
+        float* dst = F + 3 * (size_t)row + c;
+        const float v = (float)(scale * grad[q]);
+        *dst = accumulate ? *dst + v : v;
+    }
+}
+
+__global__ void k_gather_subset(int n, const int* __restrict__ index, const double* __restrict__ full,
+                                long long n_full, double* __restrict__ xyz, Counters* __restrict__ ctr) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 3 * n) return;
+    const int i = q / 3, c = q - 3 * i;
+    const int row = index[i];
+    if (row < 0 || (long long)row >= n_full) {
+        if (c == 0) atomicOr(&ctr->bad_species, 4);
+        xyz[q] = 0.0;
+        return;
+    }
+    xyz[q] = full[3 * (size_t)row + c];
 }
 
 // One block per molecule: contiguous copies between the molecule's host
@@ -81,15 +108,22 @@ void launch_scatter_results(cudaStream_t st, int n_mols, const MolRef* refs, con
     MLP_LAUNCH("scatter", st, k_scatter_results<<<n_mols, 128, 0, st>>>(refs, mol_start, d_E, d_F));
 }
 
+void launch_gather_subset(cudaStream_t st, int n, const int* index, const double* coords_full, long long n_full,
+                          double* xyz, Counters* ctr) {
+    if (n <= 0) return;
+    MLP_LAUNCH("gather_subset", st,
+               k_gather_subset<<<(3 * n + 255) / 256, 256, 0, st>>>(n, index, coords_full, n_full, xyz, ctr));
+}
+
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,
-                     const Counters* ctr, int* sticky) {
+                     const Counters* ctr, int* sticky, const int* F_index, long long n_full, bool accumulate) {
     const int fblocks = F ? (3 * n_atoms + kEBlock * 4 - 1) / (kEBlock * 4) : 0;
     const int eblocks = E ? n_mols : 0;
     const int blocks = eblocks + fblocks > 0 ? eblocks + fblocks : 1;
     MLP_LAUNCH("finalize", st,
                k_finalize<<<blocks, kEBlock, 0, st>>>(eblocks, mol_start, n_atoms, e, grad, E, F, grad_scale, sign,
-                                                      ctr, sticky));
+                                                      ctr, sticky, F_index, n_full, accumulate ? 1 : 0));
 }
 
 }  // namespace mlp

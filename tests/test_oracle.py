@@ -313,6 +313,30 @@ def test_ensemble_forces_match_central_differences():
     assert np.abs(F.sum(0)).max() <= 1e-10 * max(np.abs(F).max(), 1.0)
 
 
+def test_ml_region_mechanical_embedding(W):
+    """Section "OpenMM-ML": the ML part of a mixed system depends on the ML
+    atoms only. Moving the other atoms leaves E_ML and its forces unchanged,
+    their force rows are zero, and the ML rows are minus the finite-difference
+    gradient of E_ML."""
+    c = gen.make_config(1)
+    idx = np.arange(0, 72, 3)                        # a subset of the ligand
+    E, F = oracle.ml_region(c.species, c.coords, c.cell, W, idx)
+    rest = np.setdiff1d(np.arange(c.n), idx)
+    assert np.all(F[rest] == 0.0)
+    x2 = c.coords.copy()
+    x2[rest] += np.random.default_rng(3).normal(scale=0.3, size=(rest.size, 3))
+    E2, F2 = oracle.ml_region(c.species, x2, c.cell, W, idx)
+    assert E2 == E and np.array_equal(F2, F)
+    for m in (idx[0], idx[5], rest[0]):
+        for a in range(3):
+            xp, xm = c.coords.copy(), c.coords.copy()
+            xp[m, a] += 1e-5
+            xm[m, a] -= 1e-5
+            fd = -(oracle.ml_region(c.species, xp, c.cell, W, idx)[0] -
+                   oracle.ml_region(c.species, xm, c.cell, W, idx)[0]) / 2e-5
+            assert abs(F[m, a] - fd) <= 1e-6 * max(np.abs(F).max(), 1e-3)
+
+
 def test_forces_fd_periodic(W):
     c = gen.random_molecule(60, seed=3, density=0.1, periodic=True)
     E, F = oracle.energy_forces(c.species, c.coords, c.cell, W)
@@ -439,3 +463,83 @@ def test_parallel_atom_energies_equal_serial(W):
     G = oracle.aev(c.species, c.coords)
     idx = [3, 100, 671]
     np.testing.assert_array_equal(oracle.aev_subset(c.species, c.coords, None, idx), G[idx])
+
+
+# ------------------------------------------------------------------ Langevin (LF-Middle)
+ACC_UNITS = 9.648533212e-3   # (eV / A) / amu in A / fs^2
+KE_UNITS = 103.6426965       # amu A^2 / fs^2 in eV
+KB_EV = 8.617333262e-5       # eV / K
+MASS = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
+
+
+@pytest.mark.parametrize("counter,key", [([1, 0, 0, 0], [123, 456]), ([7, 3, 0, 0], [2**63 + 5, 0]),
+                                         ([0, 1, 0, 0], [1, 2]), ([12345, 678, 9, 10], [2**64 - 1, 2**64 - 1])])
+def test_philox_matches_numpy(counter, key):
+    """Philox4x64-10 against numpy.random.Philox, which implements the same
+    published generator (it advances its counter before each block)."""
+    c = np.array(counter, dtype=object)
+    prev = [int(x) for x in c]
+    for w in range(4):                              # counter - 1 with borrow
+        if prev[w] > 0:
+            prev[w] -= 1
+            break
+        prev[w] = 2**64 - 1
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(prev, dtype=np.uint64))
+    ref = bg.random_raw(4)
+    out = oracle.philox4x64(np.array(counter, dtype=np.uint64), np.array(key, dtype=np.uint64))
+    assert np.array_equal(out, ref)
+
+
+def test_langevin_normals_distribution():
+    R = oracle.langevin_normals(2024, 17, 40000).ravel()
+    n = R.size
+    assert abs(R.mean()) < 4 / np.sqrt(n)
+    assert abs(R.var() - 1.0) < 4 * np.sqrt(2.0 / n)
+    assert abs(np.mean(R ** 4) - 3.0) < 0.1
+    p = np.mean(R < 1.0)                            # Phi(1) = 0.841344746
+    assert abs(p - 0.841344746) < 4 * np.sqrt(p * (1 - p) / n)
+    Rm = R.reshape(-1, 3)
+    assert abs(np.corrcoef(Rm[:, 0], Rm[:, 1])[0, 1]) < 4 / np.sqrt(Rm.shape[0])
+    assert abs(np.corrcoef(Rm[:, 1], Rm[:, 2])[0, 1]) < 4 / np.sqrt(Rm.shape[0])
+    assert not np.array_equal(oracle.langevin_normals(2024, 18, 10), oracle.langevin_normals(2024, 17, 10))
+    assert np.array_equal(oracle.langevin_normals(2024, 17, 10), Rm[:10])
+
+
+def test_lfmiddle_without_friction_is_leapfrog():
+    """No friction, no temperature: the step is leapfrog, which for a harmonic
+    force F = -k x conserves v_(n-1/2) v_(n+1/2) + w^2 x_n^2 (w^2 = k / m in
+    A / fs^2 units) exactly, step after step."""
+    sp = np.array([0, 1, 3, 6, 4])
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(5, 3))
+    v = rng.normal(scale=0.01, size=(5, 3))
+    k = 2.5
+    w2 = (k * ACC_UNITS / MASS[sp])[:, None]
+    inv = []
+    for step in range(400):
+        F = -k * x
+        x_new, v_new = oracle.lfmiddle_step(sp, x, v, F, 2.0, 0.0, 0.0, 9, step)
+        inv.append(v * v_new + w2 * x * x)
+        x, v = x_new, v_new
+    inv = np.array(inv)
+    assert np.abs(inv - inv[0]).max() <= 1e-12 * np.abs(inv[0]).max()
+
+
+def test_lfmiddle_equipartition_and_decay():
+    """Free particles: the friction step leaves the Maxwell-Boltzmann
+    distribution invariant (<m v^2> = k T per component) and shrinks the
+    velocity memory by a = exp(-gamma dt) per step."""
+    n, T, gamma, dt = 20000, 300.0, 5.0, 2.0
+    sp = np.random.default_rng(2).integers(0, 7, size=n)
+    m = MASS[sp][:, None]
+    x = np.zeros((n, 3))
+    v = np.zeros((n, 3))
+    F = np.zeros((n, 3))
+    for step in range(400):
+        x, v = oracle.lfmiddle_step(sp, x, v, F, dt, gamma, T, 11, step)
+    a = np.exp(-gamma * 1e-3 * dt)
+    T_est = np.sum(m * v * v) * KE_UNITS / (3 * n * KB_EV)
+    assert abs(T_est - T * (1 - a ** 800)) < 0.01 * T
+    x2, v2 = oracle.lfmiddle_step(sp, x, v, F, dt, gamma, T, 11, 400)
+    slope = np.sum(v * v2 * m) / np.sum(v * v * m)
+    assert abs(slope - a) < 0.005
