@@ -15,7 +15,9 @@ e2e    the same stream through the C-ABI server (mlp_server_replay_clients
        with --e2e-clients native client threads: host coordinates in, host
        energies and forces out, every request due at t = 0), wall time of the
        median of three runs after a warm-up run; p50/p99 request latency.
-Also reported: the same device-resident stream with an ensemble of
+Also reported: Langevin dynamics at 2 fs (LF-Middle, graph-replayed steps)
+of the 72-atom ligand and the 672-atom ligand-in-water system in ns/day,
+one net and the 8-net ensemble; the same device-resident stream with an ensemble of
 --ensemble-nets nets (energy = mean of the nets, forces = mean gradient),
 Poisson-arrival latency sweep, the one-molecule-per-launch FP32 path, the
 roofline of the dominant kernel and the FP64 oracle on the host cores
@@ -377,6 +379,10 @@ def run_ours(args):
     if not args.no_plain and rank == 0:
         result["plain_fp32"] = plain_fp32(P, W, stream, args)
 
+    # ---------------- Langevin dynamics (2 fs), graph-replayed steps
+    if not args.no_md and rank == 0:
+        result["langevin_md"] = langevin_md(P, args)
+
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(stream, wts, args.cpu_seconds)
     if rank == 0:
@@ -541,6 +547,60 @@ def plain_fp32(P, W, stream, args):
             "path": "mlp_batch_run with one molecule per call (host buffers, synchronous)"}
 
 
+def langevin_md(P, args):
+    """LF-Middle Langevin dynamics at 2 fs (Table 3's integrator and step)
+    through mlp_langevin_run with graph replay: the 72-atom ligand of the
+    ligand-in-water workload as the ML region on its own (the ML part of a
+    mechanically embedded system; the classical part is the caller's), and
+    the whole 672-atom workload, one net and the 8-net ensemble, BF16
+    network. Wall time per step of the fastest of several runs after a
+    warm-up run, each restarting from the initial coordinates. Random-init
+    weights have no repulsive core: the 672-atom system collapses (neighbor
+    capacity) within ~50 steps with one net, so its runs are 40 steps."""
+    import torch
+
+    import gen
+
+    c = gen.make_config(1)
+    masses = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
+    out = []
+    weights = {1: P.Weights(gen.make_weights()), 8: P.Weights(gen.make_weights(nets=8))}
+    cases = (("ligand, 72 atoms", np.arange(72), args.md_steps, 3),
+             ("ligand in water, 672 atoms", np.arange(c.n), 40, 8))
+    for name, idx, steps, reps in cases:
+        sp, x0 = c.species[idx], c.coords[idx]
+        m = masses[sp][:, None]
+        v0 = np.random.default_rng(0).normal(size=x0.shape) * np.sqrt(8.617333262e-5 * 300.0 / (m * 103.6426965))
+        for nets, W in weights.items():
+            s = P.System(W, sp, x0, None, precision="bf16")
+            L = P.Langevin(s, dt_fs=2.0, friction_per_ps=1.0, temperature_K=300.0, seed=1, use_graph=True)
+            walls, err = [], None
+            for rep in range(reps + 1):
+                x = torch.from_numpy(np.ascontiguousarray(x0)).cuda()
+                v = torch.from_numpy(np.ascontiguousarray(v0)).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    L.run(x, v, 0, steps, energies=False)     # waits for the last step
+                except P.MLPError as e:
+                    err = str(e)
+                    break
+                walls.append(time.perf_counter() - t0)
+            row = {"system": name, "nets": nets, "atoms": int(idx.size), "steps_per_run": steps}
+            if err or len(walls) < 2:
+                row["aborted"] = err
+            else:
+                us = min(walls[1:]) / steps * 1e6          # the first run captures the graph
+                row.update({"us_per_step": us, "ns_per_day": 2.0e-6 * 86400.0 / (us * 1e-6),
+                            "atom_steps_per_s": idx.size / (us * 1e-6)})
+            out.append(row)
+            L.close()
+            s.close()
+    for W in weights.values():
+        W.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,6 +621,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nets", type=int, default=1, help="ensemble size of the headline measurement")
+    ap.add_argument("--no-md", action="store_true", help="skip the Langevin dynamics timing")
+    ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--ensemble-nets", type=int, default=8,
                     help="also time an ensemble of this many nets on the same stream (<= 1: skip)")
     args = ap.parse_args()

@@ -700,6 +700,20 @@ int mlp_debug_neighbors(mlp_system* s, int32_t* counts, int32_t* list, int32_t c
 }
 
 // dE/dG of a workspace as FP32 on the host (the BF16 networks store it as BF16).
+// Per-atom energies of the last evaluation (the mean over the nets of an ensemble).
+static cudaError_t copy_e_to_host(const Workspace& ws, int n, float* out) {
+    const int K = ws.e_nets();
+    if (K == 1) return cudaMemcpy(out, ws.e, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    std::vector<float> all((size_t)K * ws.cap_atoms);
+    cudaError_t e = cudaMemcpy(all.data(), ws.e, 4 * all.size(), cudaMemcpyDeviceToHost);
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc += all[(size_t)k * ws.cap_atoms + i];
+        out[i] = (float)(acc / K);
+    }
+    return e;
+}
+
 static cudaError_t copy_dG_to_host(const Workspace& ws, std::vector<float>& out) {
     const size_t cnt = (size_t)ws.rows_cap * kAevLd;
     out.resize(cnt);
@@ -761,7 +775,7 @@ int mlp_debug_atom_energies(mlp_system* s, float* e_out, float* dEdG) {
     int rc = sys_finish_pending(s);
     if (rc) return rc;
     cudaStreamSynchronize(s->stream);
-    cudaMemcpy(e_out, s->ws.e, 4 * (size_t)s->n, cudaMemcpyDeviceToHost);
+    copy_e_to_host(s->ws, s->n, e_out);
     if (dEdG) {
         std::vector<int> rows;
         rc = atom_rows(s, rows);
@@ -830,13 +844,13 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
         cudaMemcpy(ws.G16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
         if (ws.G16lo) cudaMemcpy(ws.G16lo, all_lo.data(), 2 * all_lo.size(), cudaMemcpyHostToDevice);
         if (!launch_mlp_bf16(nullptr, ws.rows_cap, ws.ctr, w->dw.bf16, ws.G16, ws.G16lo, precision == MLP_BF16,
-                             ws.row_atom, ws.e, ws.dG16, ws.g1ens, true, ws.tc_err)) {
+                             ws.row_atom, ws.e, ws.cap_atoms, ws.dG16, ws.g1ens, true, ws.tc_err)) {
             workspace_destroy(ws);
             return MLP_ECUDA;
         }
     }
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(e_out, ws.e, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = copy_e_to_host(ws, n, e_out);
     if (e == cudaSuccess && dEdG) {
         std::vector<float> all(R * kAevLd);
         e = copy_dG_to_host(ws, all);

@@ -73,7 +73,7 @@ void plan_workspace(Plan& P, Workspace& ws) {
     P.add(&ws.row_atom, R);
     P.add(&ws.ctr, 1);
     P.add(&ws.grad, 3 * n);
-    P.add(&ws.e, n);
+    P.add(&ws.e, n * (size_t)ws.e_nets());
     if (ws.precision == 0) {
         P.add(&ws.dG, R * kAevLd);
     } else {
@@ -226,13 +226,13 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     } else {
         if (!mlp_tc_available()) return set_error(-1, "BF16 tensor-core network is not available in this build");
         if (!launch_mlp_bf16(st, ws.rows_cap, ws.ctr, w.bf16, ws.G16, ws.G16lo, ws.precision == 1, ws.row_atom,
-                             ws.e, ws.dG16, ws.g1ens, sp.network_backward, &ws.ctr->net_error))
+                             ws.e, ws.cap_atoms, ws.dG16, ws.g1ens, sp.network_backward, &ws.ctr->net_error))
             return -5;
     }
     if (sp.network_backward) launch_forces(st, aa, ws.dG, ws.dG16, ws.grad, fast);
     launch_finalize(st, sp.n_mols, sp.d_mol_start, n, ws.e, ws.grad, sp.energy ? sp.d_E : nullptr,
                     sp.network_backward ? sp.d_F : nullptr, sp.d_grad_scale, sp.sign, ws.ctr, ws.err_sticky,
-                    sp.d_index, sp.n_full, sp.accumulate);
+                    sp.d_index, sp.n_full, sp.accumulate, ws.e_nets(), ws.cap_atoms);
     ce = cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (ce != cudaSuccess) return cuda_error(ce, "cudaMemcpyAsync(counters)");
     ce = cudaGetLastError();

@@ -50,6 +50,9 @@ struct Workspace {
     int cap_atoms = 0, cap_mols = 0, rows_cap = 0, nbr_cap = 0, max_cells = 0;
     int precision = 0;
     int nets = 1;   // ensemble size of the weights it serves
+    // rows of per-atom energies: one per net for the BF16 ensemble (averaged
+    // by the finalize kernel); the FP32 path accumulates the mean in place
+    int e_nets() const { return (precision != 0 && nets > 1) ? nets : 1; }
     bool cell_path = false;
     size_t bytes = 0;
     std::vector<void*> owned;
@@ -65,7 +68,7 @@ struct Workspace {
     __nv_bfloat16* dG16 = nullptr;    // BF16 networks
     __nv_bfloat16* g1ens = nullptr;   // BF16 ensemble: every net's g1, [rows][nets * 256]
     MlpF32Bufs fb{};
-    float* e = nullptr;
+    float* e = nullptr;               // [e_nets()][cap_atoms]
     Grid* grid = nullptr;
     int *cell_of_atom = nullptr, *cell_rank = nullptr, *cell_count = nullptr, *cell_start = nullptr,
         *cell_atoms = nullptr;

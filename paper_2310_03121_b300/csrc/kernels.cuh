@@ -96,14 +96,15 @@ struct NetBF16 {
 bool mlp_tc_available();
 bool make_weight_maps(NetBF16& w);
 // split = true: forward GEMMs from hi/lo BF16 pairs of both operands (G_lo
-// required); false: single BF16 pass everywhere. dE/dG goes to dG (BF16). An
-// ensemble (w.n_nets > 1) leaves the mean energy in e and the mean dE/dG in
-// dG; with backward it also needs g1, BF16 [rows_cap][n_nets * 256] scratch
-// for every net's last hidden-layer gradient (two launches: the network
-// kernel, then the mean dE/dG GEMM).
+// required); false: single BF16 pass everywhere. Per-atom energies go to e
+// and dE/dG to dG (BF16). An ensemble (w.n_nets = K > 1) writes net k's
+// energies to e + k * e_stride (the finalize kernel averages them) and the
+// mean dE/dG to dG; with backward it also needs g1, BF16 [rows_cap][K * 256]
+// scratch for every net's last hidden-layer gradient (two launches: the
+// network kernel over all (tile, net) pairs, then the mean dE/dG GEMM).
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w,
                      const __nv_bfloat16* G, const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e,
-                     __nv_bfloat16* dG, __nv_bfloat16* g1, bool backward, int* err_flag);
+                     int e_stride, __nv_bfloat16* dG, __nv_bfloat16* g1, bool backward, int* err_flag);
 
 // ---- serving batches (kernels_misc.cu): one molecule per request, its inputs
 // and result area in page-locked host memory that kernels address directly
@@ -131,10 +132,11 @@ void launch_gather_subset(cudaStream_t st, int n, const int* index, const double
 // overflow, 4 bad input, 8 network kernel error) into *sticky when
 // sticky != nullptr. With F_index, force row i goes to row F_index[i] of F
 // (n_full rows; rows outside [0, n_full) skipped), added to it when
-// accumulate is set.
+// accumulate is set. e_nets > 1: e holds e_nets rows of e_stride per-atom
+// energies (one per net of an ensemble), averaged per atom in FP64.
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,
                      const Counters* ctr, int* sticky, const int* F_index = nullptr, long long n_full = 0,
-                     bool accumulate = false);
+                     bool accumulate = false, int e_nets = 1, int e_stride = 0);
 
 }  // namespace mlp

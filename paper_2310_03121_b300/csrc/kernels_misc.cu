@@ -16,7 +16,7 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
                            const double* __restrict__ grad, double* __restrict__ E, float* __restrict__ F,
                            const double* __restrict__ grad_scale, float sign, const Counters* __restrict__ ctr,
                            int* __restrict__ sticky, const int* __restrict__ F_index, long long n_full,
-                           int accumulate) {
+                           int accumulate, int e_nets, int e_stride) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && sticky) {
         // error flags of this evaluation, kept until the host reads and clears them
         const int f = (ctr->nbr_overflow ? 1 : 0) | (ctr->ang_overflow ? 2 : 0) | (ctr->bad_species ? 4 : 0) |
@@ -28,7 +28,16 @@ __global__ void k_finalize(int n_mols, const int* __restrict__ mol_start, int n_
         const int a = mol_start ? mol_start[m] : 0;
         const int b = mol_start ? mol_start[m + 1] : n_atoms;
         double acc = 0.0;
-        for (int i = a + threadIdx.x; i < b; i += kEBlock) acc += (double)e[i];
+        if (e_nets == 1) {
+            for (int i = a + threadIdx.x; i < b; i += kEBlock) acc += (double)e[i];
+        } else {   // ensemble: atom energy = mean over the nets (fixed order)
+            const double inv = 1.0 / (double)e_nets;
+            for (int i = a + threadIdx.x; i < b; i += kEBlock) {
+                double ei = 0.0;
+                for (int k = 0; k < e_nets; ++k) ei += (double)e[(size_t)k * e_stride + i];
+                acc += ei * inv;
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         __shared__ double ws[kEBlock / 32];
@@ -117,13 +126,15 @@ void launch_gather_subset(cudaStream_t st, int n, const int* index, const double
 
 void launch_finalize(cudaStream_t st, int n_mols, const int* mol_start, int n_atoms, const float* e,
                      const double* grad, double* E, float* F, const double* grad_scale, float sign,
-                     const Counters* ctr, int* sticky, const int* F_index, long long n_full, bool accumulate) {
+                     const Counters* ctr, int* sticky, const int* F_index, long long n_full, bool accumulate,
+                     int e_nets, int e_stride) {
     const int fblocks = F ? (3 * n_atoms + kEBlock * 4 - 1) / (kEBlock * 4) : 0;
     const int eblocks = E ? n_mols : 0;
     const int blocks = eblocks + fblocks > 0 ? eblocks + fblocks : 1;
     MLP_LAUNCH("finalize", st,
                k_finalize<<<blocks, kEBlock, 0, st>>>(eblocks, mol_start, n_atoms, e, grad, E, F, grad_scale, sign,
-                                                      ctr, sticky, F_index, n_full, accumulate ? 1 : 0));
+                                                      ctr, sticky, F_index, n_full, accumulate ? 1 : 0, e_nets,
+                                                      e_stride));
 }
 
 }  // namespace mlp

@@ -108,7 +108,8 @@ struct TcArgs {
     const Counters* ctr;
     const int* row_atom;
     const float *b1, *b2, *b3, *W4, *b4;   // net-major: block k * 7 + s
-    float* e;
+    float* e;         // per-atom energies; an ensemble: [K][e_stride], one row per net
+    int e_stride;
     int backward;
     int nets;         // ensemble size K (1: single net)
     float inv_nets;   // 1 / K
@@ -200,6 +201,11 @@ __device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap
 __device__ __forceinline__ uint64_t policy_evict_last() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -421,16 +427,16 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
     for (int q = 0; q < 12; ++q) prefetch_map(maps[q]);
     const uint64_t keep = policy_evict_last(), evict = policy_evict_first();
     auto job = [&](int k, int s) -> bool { return prod_job(P, make_job<SPLIT>(M, k, s), sbase, bar0, abrt, keep); };
-    int tile_no = 0;   // (tile, net) units started
-    for (int t = blockIdx.x;; t += gridDim.x) {
+    const uint64_t gpol = nets > 1 ? policy_evict_normal() : evict;   // see the G loads below
+    // units u = blockIdx.x + i * gridDim.x: (tile u / nets, net u % nets)
+    for (int u = blockIdx.x, tile_no = 0;; u += gridDim.x, ++tile_no) {
+        const int t = u / nets, net = u - t * nets;
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
         int sn, rown, nvn;
-        const bool has_next = tile_info(counts, t + (int)gridDim.x, sn, rown, nvn);
-        bool ok = true;
-        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+        const bool has_next = tile_info(counts, (u + (int)gridDim.x) / nets, sn, rown, nvn);
+        {
             const int es = net * kNSpecies + s;   // weight block of (net, element)
-            ok = false;
             if (tile_no == 0) prefetch_g(M, row0, SPLIT);
             // F1 stages cover every region: the previous unit's epilogues and MMAs must be done with them
             if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
@@ -444,8 +450,9 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
                     break;
                 }
                 const uint32_t full = bar0 + 8u * (kBarF1Full + st), dst = sbase + (uint32_t)st * stage;
-                // G stays in L2 while later nets of this tile still need it
-                const uint64_t gpol = net < nets - 1 ? keep : evict;
+                // one net: G streams through L2 (evict-first, the weights stay); an
+                // ensemble: the nets of a tile run on neighbouring CTAs at the same
+                // time and share each G chunk through L2 (normal priority)
                 mbar_expect_tx(full, stage);
                 tma_load_2d_hint(dst, &M.G, c * 64, row0, full, gpol);
                 if (SPLIT) {
@@ -469,13 +476,11 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
             if (backward && (!job(kJobB3, es) || !job(kJobB2, es))) break;
             if (b1 && (!job(kJobB1 + 0, es) || !job(kJobB1 + 1, es) || !job(kJobB1 + 2, es) || !job(kJobB1 + 3, es)))
                 break;
-            // the next tile's G: requested after this tile's last weight load, so
+            // the next unit's G: requested after this unit's last weight load, so
             // that the weight loads never queue behind it
-            if (net == nets - 1 && has_next) prefetch_g(M, rown, SPLIT);
+            if (has_next) prefetch_g(M, rown, SPLIT);
             MLP_TC_MARK(30);
-            ok = true;
         }
-        if (!ok) break;
     }
 }
 
@@ -548,14 +553,12 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
         mma_commit(bar0 + 8u * (kBarAcc + half));
         return true;
     };
-    int tile_no = 0;   // (tile, net) units started
-    for (int t = blockIdx.x;; t += gridDim.x) {
+    for (int u = blockIdx.x, tile_no = 0;; u += gridDim.x, ++tile_no) {
+        const int t = u / nets, net = u - t * nets;
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
-        bool ok = true;
-        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+        {
             const int es = net * kNSpecies + s;
-            ok = false;
             // F1 writes accumulator half 0: the previous unit's last reader of it
             // (EB1 block 2, else E3 or EB2, which arrive on the operand barrier) must be done
             if (tile_no > 0 && !(b1 ? wait_b1(0) : wait_op())) break;
@@ -608,9 +611,7 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
                 if (!wait_b1(1) || !job(kJobB1 + 3, es, 1)) break;
                 MLP_TC_MARK(26);
             }
-            ok = true;
         }
-        if (!ok) break;
     }
 }
 
@@ -694,16 +695,13 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
     const uint64_t stream_out = policy_evict_first();
     const int nets = ENS ? p.nets : 1;
     uint32_t n_epart = 0;
-    int tile_no = 0;   // (tile, net) units
-    float e_sum = 0.f; // ensemble: this row's energy summed over the nets so far (part 0)
     (void)warp;
-    for (int t = blockIdx.x;; t += gridDim.x) {
+    for (int u = blockIdx.x, tile_no = 0;; u += gridDim.x, ++tile_no) {
+        const int t = u / nets, net = u - t * nets;
         int s, row0, nvalid;
         if (!tile_info(counts, t, s, row0, nvalid)) break;
-        bool ok = true;
-        for (int net = 0; net < nets && ok; ++net, ++tile_no) {
+        {
             const int es = net * kNSpecies + s;
-            ok = false;
             if (warp == 2) MLP_TC_MARK(0);
             const float* b1 = p.b1 + es * kH1;
             const float* b2 = p.b2 + es * kH2;
@@ -783,12 +781,8 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                         e += __uint_as_float(v.x);
                         e += __uint_as_float(v.y);
                         e += __uint_as_float(v.z);
-                        if (ENS) {
-                            e_sum = net == 0 ? e : e_sum + e;
-                            if (net == nets - 1) p.e[p.row_atom[row0 + r]] = e_sum * p.inv_nets;
-                        } else {
-                            p.e[p.row_atom[row0 + r]] = e;
-                        }
+                        // ensemble: net k's energies go to row k of e[K][e_stride]
+                        p.e[(ENS ? (size_t)net * (size_t)p.e_stride : 0) + p.row_atom[row0 + r]] = e;
                     }
                 }
                 ++n_epart;
@@ -798,7 +792,6 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
             if (!p.backward) {
                 __syncwarp();
                 if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
-                ok = true;
                 continue;
             }
 
@@ -847,7 +840,6 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 }
                 __syncwarp();
                 if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
-                ok = true;
                 continue;
             }
 
@@ -905,9 +897,7 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
             }
             __syncwarp();
             if (warp == 2) MLP_TC_MARK(19);
-            ok = true;
         }
-        if (!ok) break;
     }
 }
 
@@ -1266,8 +1256,8 @@ bool make_weight_maps(NetBF16& w) {
 }
 
 bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const NetBF16& w, const __nv_bfloat16* G,
-                     const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, __nv_bfloat16* dG,
-                     __nv_bfloat16* g1, bool backward, int* err_flag) {
+                     const __nv_bfloat16* G_lo, bool split, const int* row_atom, float* e, int e_stride,
+                     __nv_bfloat16* dG, __nv_bfloat16* g1, bool backward, int* err_flag) {
     TcMaps M;
     const bool ens = w.n_nets > 1;
     if (!w.maps_ok || !make_map(&M.G, G, kAevLd, (uint64_t)rows_cap, 128) ||
@@ -1306,9 +1296,10 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
         if (sms <= 0) sms = 148;
     }
     const int tiles = rows_cap / kTileRows;
-    const int grid = tiles < sms ? tiles : sms;
-    TcArgs a{ctr,   row_atom, w.b1, w.b2, w.b3, w.W4, w.b4, e, backward ? 1 : 0, w.n_nets, 1.f / (float)w.n_nets,
-             err_flag};
+    const int units = tiles * w.n_nets;   // (tile, net) pairs, spread over the CTAs
+    const int grid = units < sms ? units : sms;
+    TcArgs a{ctr,          row_atom,   w.b1, w.b2, w.b3, w.W4, w.b4, e, e_stride, backward ? 1 : 0, w.n_nets,
+             1.f / (float)w.n_nets, err_flag};
     if (ens) {
         if (split)
             MLP_LAUNCH("mlp_tc", st, k_mlp_tc<true, true><<<grid, kThreads, kSmemAlloc, st>>>(M, a));
