@@ -10,7 +10,7 @@
 // p = unordered element pair index. cos(theta' - Z) is formed as
 // cos theta' cos Z + sin theta' sin Z, so no acos is evaluated.
 //
-// Work decomposition (one warp per atom, 8 warps per block):
+// Work decomposition (one warp per atom; 1 warp per block forward, 2 backward):
 //   * the neighbor list is read 32 entries at a time, one neighbor per lane
 //     (displacement, distance, element, cutoff value in registers); only the
 //     neighbors within 3.5 A are staged in shared memory, as unit vector,
@@ -24,9 +24,7 @@
 //     (conflict-free, fixed order -> deterministic).
 // The backward recomputes the terms with their derivatives and contracts
 // them with dE/dG (staged in shared memory): radial one neighbor per lane
-// (on the fast path the 16 Gaussians come from a two-sided recurrence started
-// at the nearest shift: 3 exponentials instead of 16), angular one pair per
-// lane with its 4 distance and 8 angle factors in registers (the angular
+// (16 unrolled exponentials), angular one pair per lane with its 4 distance and 8 angle factors in registers (the angular
 // block of dE/dG is staged in rows of 33 floats per element pair so that
 // lanes reading the same column of different pair rows do not share a bank). Gradients on
 // neighbors go to FP64 global sums (radial: per neighbor; angular:
@@ -60,7 +58,12 @@ void init_constants_for_current_device() {
 
 namespace {
 
-constexpr int kWarps = 8;
+// Warps (one atom each) per block. Small blocks: a block's shared memory is
+// released only when its slowest atom is done, so with atoms of uneven
+// neighbor counts fewer warps per block keep more warps busy (measured:
+// AEV 1 warp 12% and forces 2 warps 10% faster than 8 warps per block).
+constexpr int kAevWarps = 1;
+constexpr int kForceWarps = 2;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <bool FAST>
@@ -251,11 +254,11 @@ __device__ __forceinline__ void put_g(__nv_bfloat16* out, __nv_bfloat16* out_lo,
 }
 
 template <bool FAST, typename OutT>
-__global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
+__global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
                                                       int* __restrict__ row_atom) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + w;
+    const int i = blockIdx.x * kAevWarps + w;
     if (i >= a.n) return;
     AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kAevSmemPerWarp);
     AevScratch& X = *reinterpret_cast<AevScratch*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
@@ -409,6 +412,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_aev(AevArgs a, OutT* __restrict
                     cur_p = pq;
                     acc = 0.f;
                 }
+#pragma unroll 4
                 for (int q = q0; q < q1; ++q) acc = fmaf(X.pf[q * 9 + z], X.rf[q * 5 + aa], acc);
             }
             __syncwarp();
@@ -435,31 +439,14 @@ __device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, 
         }
         return 0.25f * s;
     }
-    // Gaussians by a two-sided recurrence from the shift nearest to r:
-    //   G_{k+1} = G_k m_k, m_{k+1} = m_k C ;  G_{k-1} = G_k n_k, n_{k-1} = n_k C,
-    // m_k = exp(2 eta D d_k - eta D^2), n_k = exp(-2 eta D d_k - eta D^2),
-    // C = exp(-2 eta D^2), d_k = r - R_k, D the shift spacing.
-    const float R0 = c_aev.shf_r[0];
-    const float D = c_aev.shf_r[1] - c_aev.shf_r[0];
-    const float C = M<true>::ex(-2.f * kEtaRad * D * D);
-    int kc = __float2int_rn((r - R0) * (1.f / D));
-    kc = min(max(kc, 0), kRadShifts - 1);
-    const float dc = r - c_aev.shf_r[kc];
-    const float Gc = M<true>::ex(-kEtaRad * dc * dc);
-    s = g[kc] * Gc * (-2.f * kEtaRad * dc * fc + dfc);
-    float gu = Gc, mu = M<true>::ex(2.f * kEtaRad * D * dc - kEtaRad * D * D), du = dc;
-    for (int kk = kc + 1; kk < kRadShifts; ++kk) {
-        gu *= mu;
-        mu *= C;
-        du -= D;
-        s += g[kk] * gu * (-2.f * kEtaRad * du * fc + dfc);
-    }
-    float gd = Gc, nd = M<true>::ex(-2.f * kEtaRad * D * dc - kEtaRad * D * D), dd = dc;
-    for (int kk = kc - 1; kk >= 0; --kk) {
-        gd *= nd;
-        nd *= C;
-        dd += D;
-        s += g[kk] * gd * (-2.f * kEtaRad * dd * fc + dfc);
+    // fast path: the 16 Gaussians as hardware exponentials, fully unrolled
+    // (shifts from constant memory); measured 8% faster for the whole force
+    // kernel than a two-sided recurrence from the nearest shift (3
+    // exponentials, but rolled loops)
+#pragma unroll
+    for (int k = 0; k < kRadShifts; ++k) {
+        const float dk = r - c_aev.shf_r[k];
+        s = fmaf(g[k] * M<true>::ex2(-kEtaRad * 1.4426950408889634f * dk * dk), -2.f * kEtaRad * dk * fc + dfc, s);
     }
     return 0.25f * s;
 }
@@ -481,11 +468,11 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&v)[8]) {
 }
 
 template <bool FAST, typename TG>
-__global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
+__global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
                                                          double* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kWarps + w;
+    const int i = blockIdx.x * kForceWarps + w;
     if (i >= a.n) return;
     AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kForceSmemPerWarp);
     float* gs = reinterpret_cast<float*>(smem + w * kForceSmemPerWarp + sizeof(AngStage));
@@ -495,26 +482,41 @@ __global__ void __launch_bounds__(kWarps * 32) k_forces(AevArgs a, const TG* __r
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
     const TG* grow = dG + (size_t)rw * kAevLd;
     // 8 columns per lane and load (16 B of BF16 or 32 B of FP32); the 8 stay
-    // inside one radial block or one 32-column angular row
-    for (int c = 8 * lane; c < kAevLen; c += 256) {
-        float v[8];
-        load8(grow + c, v);
-        const int dst = c < kRadLen ? c : kRadLen + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
+    // inside one radial block or one 32-column angular row. All of a lane's
+    // loads are issued before the first store, so the row costs one memory
+    // round trip, not four.
+    const int cnt = min(a.nbr_cnt[i], a.cap);
+    const int* row = a.nbr + (size_t)i * a.cap;
+    NbrLane nl0;
+    {
+        float v[4][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) gs[dst + q] = v[q];
+        for (int q = 0; q < 4; ++q) {
+            const int c = 8 * lane + 256 * q;
+            if (c < kAevLen) load8(grow + c, v[q]);
+        }
+        // the first 32 neighbors' loads overlap the dE/dG row's
+        nl0 = load_neighbor<FAST>(a, row, lane, cnt, hi_i, lo_i);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = 8 * lane + 256 * q;
+            if (c < kAevLen) {
+                const int dst = c < kRadLen ? c : kRadLen + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) gs[dst + e] = v[q][e];
+            }
+        }
     }
     for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
     __syncwarp();
 
     float fix = 0.f, fiy = 0.f, fiz = 0.f;   // dE/dr_i partial sums of this lane
-    const int cnt = min(a.nbr_cnt[i], a.cap);
-    const int* row = a.nbr + (size_t)i * a.cap;
     int mA = 0;
     // radial: one neighbor per lane. The gradient on an angular neighbor goes
     // to its (still private) shared-memory slot, which the angular terms add
     // to and which is flushed once; other neighbors go straight to the FP64 sums.
     for (int base = 0; base < cnt; base += 32) {
-        const NbrLane nl = load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
+        const NbrLane nl = base == 0 ? nl0 : load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
         int pA;
         mA = stage_angular<FAST>(nl, mA, s, a, &pA);
         if (nl.inR) {
@@ -637,50 +639,50 @@ void set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast) {
-    const size_t sm = kWarps * kAevSmemPerWarp;
-    const int gs = (a.n + kWarps - 1) / kWarps;
+    const size_t sm = kAevWarps * kAevSmemPerWarp;
+    const int gs = (a.n + kAevWarps - 1) / kAevWarps;
     if (fast) {
         static bool once = (set_smem(k_aev<true, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     } else {
         static bool once = (set_smem(k_aev<false, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     }
 }
 
 void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,
                      bool fast) {
-    const size_t sm = kWarps * kAevSmemPerWarp;
-    const int gs = (a.n + kWarps - 1) / kWarps;
+    const size_t sm = kAevWarps * kAevSmemPerWarp;
+    const int gs = (a.n + kAevWarps - 1) / kAevWarps;
     if (fast) {
         static bool once = (set_smem(k_aev<true, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     } else {
         static bool once = (set_smem(k_aev<false, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
+        MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     }
 }
 
 void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, const __nv_bfloat16* dG16, double* grad,
                    bool fast) {
-    const size_t sm = kWarps * kForceSmemPerWarp;
-    const int gs = (a.n + kWarps - 1) / kWarps;
+    const size_t sm = kForceWarps * kForceSmemPerWarp;
+    const int gs = (a.n + kForceWarps - 1) / kForceWarps;
     if (dG16) {
         static bool once = (set_smem(k_forces<true, __nv_bfloat16>, sm), true);
         (void)once;
-        MLP_LAUNCH("forces", st, k_forces<true, __nv_bfloat16><<<gs, kWarps * 32, sm, st>>>(a, dG16, grad));
+        MLP_LAUNCH("forces", st, k_forces<true, __nv_bfloat16><<<gs, kForceWarps * 32, sm, st>>>(a, dG16, grad));
     } else if (fast) {
         static bool once = (set_smem(k_forces<true, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("forces", st, k_forces<true, float><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
+        MLP_LAUNCH("forces", st, k_forces<true, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
     } else {
         static bool once = (set_smem(k_forces<false, float>, sm), true);
         (void)once;
-        MLP_LAUNCH("forces", st, k_forces<false, float><<<gs, kWarps * 32, sm, st>>>(a, dG, grad));
+        MLP_LAUNCH("forces", st, k_forces<false, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
     }
 }
 
