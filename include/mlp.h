@@ -265,6 +265,13 @@ typedef struct {
     int32_t streams;            /* batches in flight on the device (default 2)           */
     int32_t queue_capacity;     /* requests outstanding (submitted, not yet collected) before MLP_EAGAIN (default 65536) */
     int64_t budget_bytes;       /* device bytes the in-flight batches may hold (40e9)    */
+    /* Batching while the device is busy: with another batch in flight, a
+     * free slot waits until min_batch_atoms atoms are queued or the oldest
+     * queued request has waited max_wait_us, so that batches stay large
+     * under load; with the device idle a batch starts at once. min_batch_atoms
+     * <= 0 launches greedily. Defaults 16384 and 500. */
+    int32_t min_batch_atoms;
+    int32_t max_wait_us;
 } mlp_server_opts;
 
 /* Fills opts with the defaults above. */

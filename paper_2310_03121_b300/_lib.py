@@ -51,7 +51,8 @@ class LangevinParams(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_batch_atoms", ctypes.c_int32), ("max_batch_mols", ctypes.c_int32),
                 ("max_atoms_per_mol", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("queue_capacity", ctypes.c_int32), ("budget_bytes", ctypes.c_int64)]
+                ("queue_capacity", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("min_batch_atoms", ctypes.c_int32), ("max_wait_us", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):

@@ -5,7 +5,7 @@
 // One persistent CTA per SM processes 128-row tiles of one element (TMEM lane
 // r = row r of the tile). The six GEMMs of the forward and backward run back
 // to back without leaving the SM:
-//   F1  D[128x256] = G[128x1024] W1^T   G and W1 streamed by TMA in 64-wide K chunks
+//   F1  D[128x256] = G[128x1024] W1^T   G and W1 streamed by TMA in 32- or 64-wide K chunks
 //   E1  h1 = celu(D + b1)               -> shared memory, BF16, A-operand layout
 //   F2  D[128x192] = h1 W2^T            W2 streamed
 //   E2  h2 = celu(D + b2)               -> shared memory
@@ -74,7 +74,9 @@ constexpr uint32_t kAtom = 128 * 128;            // 128 rows x 64 BF16 (one K at
 //   B1 only:      dE/dG staging [64K, 112K), one 32-row x 64-column box (4 KB) per epilogue warp
 //   weight rings: F2 [128K, 224K) 4 x 24 KB, F3 [160K, 224K) 3 x 20 KB,
 //                 B3 [160K, 224K) 2 x 32 KB, B2 and B1 [128K, 224K) 3 x 32 KB
-//   F1 stages over [0, 192K): 2 x 96 KB (split: G_hi, G_lo, W1_hi, W1_lo) or 4 x 48 KB
+//   F1 stages over [0, 192K): 4 x 48 KB; split: 32 K columns per stage (G_hi, G_lo
+//   8 KB each, W1_hi, W1_lo 16 KB each; 64-byte swizzle), so that three stages
+//   are in flight while one is consumed; one pass: 64 K columns (G 16 KB, W1 32 KB)
 // The producer switches between region layouts only after the MMAs reading
 // the previous layout have completed, and starts a tile's F1 only after the
 // previous tile's epilogues are done with shared memory.
@@ -119,6 +121,8 @@ struct TcArgs {
 struct TcMaps {
     CUtensorMap G, Glo, W1, W1lo, W2, W2lo, W3, W3lo, W3t, W2t, W1t, dG;
     CUtensorMap G1;   // ensemble: g1 of every net, BF16 [rows][K * 256]
+    // split F1: 32-column boxes, 64-byte swizzle (4 stages of 48 KB)
+    CUtensorMap Gn, Glon, W1n, W1lon;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -243,6 +247,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
     d |= (uint64_t)1 << 46;             // descriptor version
     d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+// The same for 64-byte swizzled rows (32 BF16 columns): 8-row groups 512
+// bytes apart, layout type SWIZZLE_64B.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;             // SWIZZLE_64B
     return d;
 }
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
@@ -420,11 +435,14 @@ __device__ void prefetch_g(const TcMaps& M, int row0, bool split) {
 template <bool SPLIT>
 __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t bar0, volatile int* abrt,
                          bool backward, bool b1, int nets, ProdState& P) {
-    constexpr int nst = SPLIT ? 2 : 4;
-    constexpr uint32_t stage = SPLIT ? 98304u : 49152u;   // A (+A_lo) 16 KB each, B (+B_lo) 32 KB each
-    const CUtensorMap* maps[12] = {&M.G, &M.Glo, &M.W1, &M.W1lo, &M.W2, &M.W2lo, &M.W3, &M.W3lo, &M.W3t, &M.W2t,
-                                   &M.W1t, &M.dG};
-    for (int q = 0; q < 12; ++q) prefetch_map(maps[q]);
+    // split: 4 stages of 32 K columns (G_hi, G_lo 8 KB each, W1_hi, W1_lo 16 KB each);
+    // one pass: 4 stages of 64 K columns (G 16 KB, W1 32 KB)
+    constexpr int nst = 4;
+    constexpr uint32_t stage = 49152u;
+    constexpr int kw = SPLIT ? 32 : 64;   // K columns per stage
+    const CUtensorMap* maps[16] = {&M.G,  &M.Glo, &M.W1,  &M.W1lo, &M.W2, &M.W2lo, &M.W3,  &M.W3lo,
+                                   &M.W3t, &M.W2t, &M.W1t, &M.dG,  &M.Gn, &M.Glon, &M.W1n, &M.W1lon};
+    for (int q = 0; q < 16; ++q) prefetch_map(maps[q]);
     const uint64_t keep = policy_evict_last(), evict = policy_evict_first();
     auto job = [&](int k, int s) -> bool { return prod_job(P, make_job<SPLIT>(M, k, s), sbase, bar0, abrt, keep); };
     const uint64_t gpol = nets > 1 ? policy_evict_normal() : evict;   // see the G loads below
@@ -442,7 +460,7 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
             if (tile_no > 0 && !mbar_wait(bar0 + 8u * kBarStage, (uint32_t)(tile_no - 1) & 1u, abrt)) break;
             if (!prod_drain(P, bar0, 0xf0u, abrt)) break;
             bool f1 = true;
-            for (int c = 0; c < kAevLd / 64; ++c) {
+            for (int c = 0; c < kAevLd / kw; ++c) {
                 const int st = (int)P.f1pos;
                 P.f1pos = (P.f1pos + 1u) & (uint32_t)(nst - 1);
                 if (!prod_free(P, bar0, st, abrt)) {
@@ -454,13 +472,14 @@ __device__ void producer(const TcMaps& M, const int* counts, uint32_t sbase, uin
                 // ensemble: the nets of a tile run on neighbouring CTAs at the same
                 // time and share each G chunk through L2 (normal priority)
                 mbar_expect_tx(full, stage);
-                tma_load_2d_hint(dst, &M.G, c * 64, row0, full, gpol);
                 if (SPLIT) {
-                    tma_load_2d_hint(dst + 16384u, &M.Glo, c * 64, row0, full, gpol);
-                    tma_load_2d_hint(dst + 32768u, &M.W1, c * 64, es * kH1, full, keep);
-                    tma_load_2d_hint(dst + 65536u, &M.W1lo, c * 64, es * kH1, full, keep);
+                    tma_load_2d_hint(dst, &M.Gn, c * kw, row0, full, gpol);
+                    tma_load_2d_hint(dst + 8192u, &M.Glon, c * kw, row0, full, gpol);
+                    tma_load_2d_hint(dst + 16384u, &M.W1n, c * kw, es * kH1, full, keep);
+                    tma_load_2d_hint(dst + 32768u, &M.W1lon, c * kw, es * kH1, full, keep);
                 } else {
-                    tma_load_2d_hint(dst + 16384u, &M.W1, c * 64, es * kH1, full, keep);
+                    tma_load_2d_hint(dst, &M.G, c * kw, row0, full, gpol);
+                    tma_load_2d_hint(dst + 16384u, &M.W1, c * kw, es * kH1, full, keep);
                 }
                 P.pend |= 1u << st;
                 P.lpar ^= 1u << st;
@@ -532,8 +551,9 @@ __device__ __forceinline__ bool mma_job(MmaState& S, const Job& J, uint32_t sbas
 template <bool SPLIT>
 __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, uint32_t tmem, uint32_t bar0,
                            volatile int* abrt, bool backward, bool b1, int nets, MmaState& S) {
-    constexpr int nst = SPLIT ? 2 : 4;
-    constexpr uint32_t stage = SPLIT ? 98304u : 49152u;
+    constexpr int nst = 4;
+    constexpr uint32_t stage = 49152u;
+    constexpr int kw = SPLIT ? 32 : 64;
     const uint32_t idesc1 = idesc_bf16(128, kH1);
     uint32_t n_op = 0, n_b1[2] = {0, 0};
     auto wait_op = [&]() -> bool {
@@ -564,7 +584,7 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
             if (tile_no > 0 && !(b1 ? wait_b1(0) : wait_op())) break;
             MLP_TC_MARK(20);
             bool f1 = true;
-            for (int c = 0; c < kAevLd / 64; ++c) {
+            for (int c = 0; c < kAevLd / kw; ++c) {
                 const int st = (int)S.f1pos;
                 S.f1pos = (S.f1pos + 1u) & (uint32_t)(nst - 1);
                 if (!mbar_wait(full_bar(bar0, st), (S.fpar >> st) & 1u, abrt)) {
@@ -574,18 +594,20 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
                 S.fpar ^= 1u << st;
                 tc_fence_after();
                 const uint32_t base = sbase + (uint32_t)st * stage;
-                const uint64_t ah = sdesc(base), al = sdesc(base + 16384u);
-                const uint64_t bh = sdesc(base + (SPLIT ? 32768u : 16384u)), bl = sdesc(base + 65536u);
+                if (SPLIT) {
+                    const uint64_t ah = sdesc64(base), al = sdesc64(base + 8192u);
+                    const uint64_t bh = sdesc64(base + 16384u), bl = sdesc64(base + 32768u);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-                    if (SPLIT) {
+                    for (int k = 0; k < 2; ++k) {
+                        const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
                         mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
                         mma_bf16(tmem, al + 2u * k, bh + 2u * k, idesc1, 1u);
                         mma_bf16(tmem, ah + 2u * k, bl + 2u * k, idesc1, 1u);
-                    } else {
-                        mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, acc);
                     }
+                } else {
+                    const uint64_t ah = sdesc(base), bh = sdesc(base + 16384u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_bf16(tmem, ah + 2u * k, bh + 2u * k, idesc1, (c > 0 || k > 0) ? 1u : 0u);
                 }
                 mma_commit(empty_bar(bar0, st));
             }
@@ -1211,16 +1233,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D BF16 map over a row-major [rows x cols] matrix, box [box_rows x 64],
 // 128-byte swizzle, zero fill outside the matrix.
-bool make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+bool make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows,
+              uint32_t box_cols = 64) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -1268,6 +1292,16 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
         return false;
     }
     if (!(backward && ens)) M.G1 = M.G;   // not used
+    {   // split F1 boxes (32 columns); the W1 maps cover every net like the 64-column ones
+        const uint64_t blocks = (uint64_t)w.n_nets * kNSpecies;
+        if (!make_map(&M.Gn, G, kAevLd, (uint64_t)rows_cap, 128, 32) ||
+            !make_map(&M.Glon, split ? G_lo : G, kAevLd, (uint64_t)rows_cap, 128, 32) ||
+            !make_map(&M.W1n, w.W1, kAevLd, blocks * kH1, kH1, 32) ||
+            !make_map(&M.W1lon, w.W1lo, kAevLd, blocks * kH1, kH1, 32)) {
+            set_error(-5, "TMA tensor map creation failed");
+            return false;
+        }
+    }
     if (!split) M.Glo = M.G;
     if (!backward) M.dG = M.G;   // not used
     M.W1 = w.tmW1;

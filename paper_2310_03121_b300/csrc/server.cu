@@ -214,6 +214,9 @@ struct mlp_server {
     RequestPool pool;
     SubmitQueue sq;
     std::deque<Request*> pending;   // drained from sq, not yet batched (server thread only)
+    int64_t pending_atoms = 0;      // atoms in pending
+    int64_t min_batch = 0;          // batching under load (from the options)
+    int64_t max_wait_ns = 0;
     alignas(64) std::atomic<uint64_t> next_id{1};
     alignas(64) std::atomic<int64_t> queued{0};   // pushed on sq and not yet drained
     alignas(64) std::atomic<bool> sleeping{false};
@@ -377,6 +380,7 @@ void server_loop(mlp_server* S) {
         int64_t drained = 0;
         while (Request* r = S->sq.pop()) {
             S->pending.push_back(r);
+            S->pending_atoms += r->n;
             ++drained;
         }
         if (drained) S->queued.fetch_sub(drained);
@@ -394,7 +398,13 @@ void server_loop(mlp_server* S) {
             else if (!free_slot)
                 free_slot = &s;
         }
-        if (free_slot && !S->pending.empty()) {
+        // under load (another batch on the device) wait for a batch worth its
+        // fixed cost, or until the oldest request has waited max_wait_us
+        bool launch = free_slot && !S->pending.empty();
+        if (launch && any_busy && S->pending_atoms < S->min_batch &&
+            (int64_t)S->pending.size() < S->o.max_batch_mols)
+            launch = now_ns() - S->pending.front()->t_submit >= S->max_wait_ns;
+        if (launch) {
             // admission: oldest first, within the slot's limits and the HBM budget
             int atoms = 0;
             batch.clear();
@@ -411,6 +421,7 @@ void server_loop(mlp_server* S) {
                 if (inflight + fp > S->o.budget_bytes && any_busy) break;   // wait for memory
                 batch.push_back(r);
                 atoms += r->n;
+                S->pending_atoms -= r->n;
                 S->pending.pop_front();
             }
             if (!batch.empty()) {
@@ -467,6 +478,8 @@ void mlp_server_opts_default(mlp_server_opts* o) {
     o->streams = 2;
     o->queue_capacity = 65536;
     o->budget_bytes = 40LL * 1000 * 1000 * 1000;
+    o->min_batch_atoms = 16384;
+    o->max_wait_us = 500;
 }
 
 int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_server** out) {
@@ -481,7 +494,7 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     if (o.precision != MLP_FP32 && !mlp_tc_available()) return set_error(MLP_EINVAL, "BF16 network not available");
     if (o.max_batch_atoms <= 0 || o.max_batch_mols <= 0 || o.max_atoms_per_mol <= 0 ||
         o.max_atoms_per_mol > o.max_batch_atoms || o.streams <= 0 || o.streams > 16 || o.queue_capacity <= 0 ||
-        o.budget_bytes <= 0)
+        o.budget_bytes <= 0 || o.max_wait_us < 0)
         return set_error(MLP_EINVAL, "bad server options");
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
@@ -497,6 +510,8 @@ int mlp_server_create(const mlp_weights* w, const mlp_server_opts* opts, mlp_ser
     mlp_server* S = new (std::nothrow) mlp_server();
     if (!S) return set_error(MLP_ENOMEM, "host allocation failed");
     S->o = o;
+    S->min_batch = std::min<int64_t>(std::max(0, o.min_batch_atoms), o.max_batch_atoms);
+    S->max_wait_ns = (int64_t)std::max(0, o.max_wait_us) * 1000;
     S->w = w;
     cudaGetDevice(&S->device);
     S->pool.device = S->device;

@@ -196,3 +196,24 @@ def test_replay_several_clients(P, W, stream):
         srv.replay(arr, ms, st.species[: ms[-1]], st.coords[: ms[-1]], clients=65)
     assert ei.value.code == _lib.MLP_EINVAL
     srv.close()
+
+
+def test_batching_under_load(P, W, stream):
+    """With a batch on the device, a free slot waits for min_batch_atoms (or
+    max_wait_us) instead of launching whatever is queued: a burst is served in
+    fewer, larger batches than by greedy launching, with the same results."""
+    st = stream
+    arr = np.zeros(st.count, dtype=np.int64)
+    means, outs = {}, {}
+    for mb in (0, 16384):
+        srv = P.Server(W, precision="bf16", max_batch_atoms=131072, max_batch_mols=4096, streams=2,
+                       min_batch_atoms=mb, max_wait_us=500)
+        srv.replay(arr, st.mol_start, st.species, st.coords)
+        E, F, _ = srv.replay(arr, st.mol_start, st.species, st.coords)
+        s = srv.stats()
+        means[mb] = s["mean_batch_atoms"]
+        outs[mb] = (E, F)
+        srv.close()
+    assert means[16384] >= means[0]
+    np.testing.assert_array_equal(outs[0][0], outs[16384][0])
+    assert np.abs(outs[0][1] - outs[16384][1]).max() <= 1e-6 * max(1.0, np.abs(outs[0][1]).max())
