@@ -429,12 +429,12 @@ def term_counts(stream):
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
     # launch (profiles/); valid only while the kernel source is the one that was captured
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
-               "bytes_per_atom": (597.866496e6 + 221.936896e6) / 131056},
-    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
-                 "bytes_per_atom": (599.007488e6 + 246.604032e6) / 65518},
-    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "9e6e7afb5b5f3a614d0e6346f2092bdf712f91d8",
-                        "bytes_per_atom": (300.643840e6 + 108.841728e6) / 65518},
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
+               "bytes_per_atom": (599.072512e6 + 216.025856e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
+                 "bytes_per_atom": (361.540864e6 + 257.555200e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
+                        "bytes_per_atom": (300.759040e6 + 108.273664e6) / 65518},
 }
 
 
