@@ -129,7 +129,8 @@ struct AngStage {
 
 // Forward scratch of one warp (after its angular stage).
 struct AevScratch {
-    float accR[2 * kRadLen];    // radial accumulators, two halves of 16 shift lanes
+    float accR[2 * kRadLen];    // radial accumulators [element][half][shift]: the two 16-lane
+                                // halves of a warp use disjoint banks whatever their elements
     // per pair (one per lane): 2 fc fc P_z for the 8 sections and the 4
     // distance Gaussians; rows of 9 and 5 floats so that both the writing
     // lanes (one row each) and the reading lanes (one row, 8 or 4 columns)
@@ -148,7 +149,11 @@ static_assert(sizeof(AngStage) % 16 == 0, "AngStage must keep the per-warp regio
 // pair) so that lanes reading the same column of different rows hit
 // different banks
 constexpr int kGsAngStride = 33;
-constexpr int kGsFloats = kRadLen + kNPairs * kGsAngStride;
+// the radial block in rows of 17 floats per element, so that lanes on
+// neighbors of different elements read different banks
+constexpr int kGsRadStride = 17;
+constexpr int kGsRad = kNSpecies * kGsRadStride;
+constexpr int kGsFloats = kGsRad + kNPairs * kGsAngStride;
 constexpr size_t kForceSmemPerWarp = round16(sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float));
 static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-warp shared regions must be 16-byte aligned");
 
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
     const int* row = a.nbr + (size_t)i * a.cap;
     const int k = lane & 15, h = lane >> 4;
     const float Rk = c_aev.shf_r[k];
-    float* accR = X.accR + h * kRadLen;
+    float* accR = X.accR + h * kRadShifts;
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
     for (int base = 0; base < cnt; base += 32) {
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             const float ff = __shfl_sync(kFull, fcr, src);
             if (src < nq && ff > 0.f) {
                 const float dr = rr - Rk;
-                accR[ss * kRadShifts + k] += 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) * ff;
+                accR[ss * 2 * kRadShifts + k] += 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) * ff;
             }
         }
         mA = stage_angular<FAST>(nl, mA, s, a);
@@ -421,7 +426,10 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
         for (; next_p < kNPairs; ++next_p) put_g(out, out_lo, kRadLen + 32 * next_p + lane, 0.f);
     }
     // radial block (two halves) and the zero padding of the row
-    for (int c = lane; c < kRadLen; c += 32) put_g(out, out_lo, c, X.accR[c] + X.accR[kRadLen + c]);
+    for (int c = lane; c < kRadLen; c += 32) {
+        const int a = 2 * kRadShifts * (c >> 4) + (c & 15);
+        put_g(out, out_lo, c, X.accR[a] + X.accR[a + kRadShifts]);
+    }
     if (lane < kAevLd - kAevLen) put_g(out, out_lo, kAevLen + lane, 0.f);
     if (lane == 0) row_atom[rw] = i;
 }
@@ -501,7 +509,8 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
         for (int q = 0; q < 4; ++q) {
             const int c = 8 * lane + 256 * q;
             if (c < kAevLen) {
-                const int dst = c < kRadLen ? c : kRadLen + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
+                const int dst = c < kRadLen ? kGsRadStride * (c >> 4) + (c & 15)
+                                            : kGsRad + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) gs[dst + e] = v[q][e];
             }
@@ -523,7 +532,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
             const float x = nl.r * (1.f / kRcRad);
             const float fc = 0.5f * M<FAST>::cpi(x) + 0.5f;
             const float dfc = -0.5f * (3.14159265358979f / kRcRad) * M<FAST>::spi(x);
-            const float sc = radial_dEdr<FAST>(gs + nl.sp * kRadShifts, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
+            const float sc = radial_dEdr<FAST>(gs + nl.sp * kGsRadStride, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
             const float gx = sc * nl.d.x, gy = sc * nl.d.y, gz = sc * nl.d.z;
             if (pA >= 0) {
                 fslot[3 * pA] = gx;
@@ -566,7 +575,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
                     R[aa] = M<FAST>::ex(-kEtaAng * dr * dr);
                     dR[aa] = -2.f * kEtaAng * dr * R[aa];
                 }
-                const float* gp = gs + kRadLen + kGsAngStride * p;
+                const float* gp = gs + kGsRad + kGsAngStride * p;
                 float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
                 for (int z = 0; z < kAngZ; ++z) {
