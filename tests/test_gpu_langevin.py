@@ -137,3 +137,28 @@ def test_bad_parameters(P, W):
     for kw in ({"dt_fs": 0.0}, {"friction_per_ps": -1.0}, {"temperature_K": -5.0}):
         with pytest.raises(P.MLPError):
             P.Langevin(s, **kw)
+
+
+def test_checkpoint_and_resume(P, W):
+    """A trajectory is a function of (x, v, seed, step): saving x, v and the
+    step to the host and resuming in a fresh system and integrator gives the
+    run that never stopped."""
+    c = gen.make_config(1)
+    v0 = _start(c, 4)
+    s = P.System(W, c.species, c.coords, c.cell, precision="bf16")
+    L = P.Langevin(s, dt_fs=2.0, friction_per_ps=1.0, temperature_K=300.0, seed=21)
+    x, v = _dev(c.coords), _dev(v0)
+    L.run(x, v, 0, 24, energies=False)
+    xa, va = x.cpu().numpy(), v.cpu().numpy()
+    s1 = P.System(W, c.species, c.coords, c.cell, precision="bf16")
+    L1 = P.Langevin(s1, dt_fs=2.0, friction_per_ps=1.0, temperature_K=300.0, seed=21)
+    x1, v1 = _dev(c.coords), _dev(v0)
+    L1.run(x1, v1, 0, 12, energies=False)
+    ckpt = (x1.cpu().numpy(), v1.cpu().numpy(), 12)       # host checkpoint
+    L1.close()
+    s2 = P.System(W, c.species, ckpt[0], c.cell, precision="bf16")
+    L2 = P.Langevin(s2, dt_fs=2.0, friction_per_ps=1.0, temperature_K=300.0, seed=21)
+    x2, v2 = _dev(ckpt[0]), _dev(ckpt[1])
+    L2.run(x2, v2, ckpt[2], 12, energies=False)
+    assert np.abs(x2.cpu().numpy() - xa).max() <= 1e-9 * max(1.0, np.abs(xa).max())
+    assert np.abs(v2.cpu().numpy() - va).max() <= 1e-9 * max(1.0, np.abs(va).max())
