@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace mlp {
@@ -15,6 +17,21 @@ namespace mlp {
 void launch_begin(const char* name, cudaStream_t st);
 void launch_end(const char* name, cudaStream_t st);
 void init_constants_for_current_device();
+
+// One-time setup per (device, key) -- kernel attributes, constant tables --
+// safe to call from several host threads: the setup runs under a lock, once
+// for each device it is called on.
+std::mutex& once_mutex();
+bool once_first(int device, const void* key);   // caller holds once_mutex(); records the pair
+template <typename F>
+void once_per_device(const void* key, F&& setup) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(once_mutex());
+    if (once_first(dev, key)) setup();
+}
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
 
 #define MLP_LAUNCH(name, st, ...)            \
     do {                                     \

@@ -39,21 +39,18 @@ namespace mlp {
 __constant__ AevConsts c_aev;
 
 void init_constants_for_current_device() {
-    static bool done[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && done[dev]) return;
-    AevConsts h;
-    const double pi = 3.14159265358979323846;
-    for (int k = 0; k < kRadShifts; ++k) h.shf_r[k] = (float)(0.8 + k * (4.9 - 0.8) / 15.0);
-    for (int a = 0; a < kAngA; ++a) h.shf_a[a] = (float)(0.8 + a * (kRcAng - 0.8) / 4.0);
-    for (int z = 0; z < kAngZ; ++z) {
-        double Z = (2.0 * z + 1.0) * pi / 16.0;
-        h.cos_z[z] = (float)cos(Z);
-        h.sin_z[z] = (float)sin(Z);
-    }
-    cudaMemcpyToSymbol(c_aev, &h, sizeof(h));
-    if (dev < 64) done[dev] = true;
+    once_per_device(&c_aev, [] {
+        AevConsts h;
+        const double pi = 3.14159265358979323846;
+        for (int k = 0; k < kRadShifts; ++k) h.shf_r[k] = (float)(0.8 + k * (4.9 - 0.8) / 15.0);
+        for (int a = 0; a < kAngA; ++a) h.shf_a[a] = (float)(0.8 + a * (kRcAng - 0.8) / 4.0);
+        for (int z = 0; z < kAngZ; ++z) {
+            double Z = (2.0 * z + 1.0) * pi / 16.0;
+            h.cos_z[z] = (float)cos(Z);
+            h.sin_z[z] = (float)sin(Z);
+        }
+        cudaMemcpyToSymbol(c_aev, &h, sizeof(h));
+    });
 }
 
 namespace {
@@ -651,12 +648,10 @@ void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, 
     const size_t sm = kAevWarps * kAevSmemPerWarp;
     const int gs = (a.n + kAevWarps - 1) / kAevWarps;
     if (fast) {
-        static bool once = (set_smem(k_aev<true, float>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_aev<true, float>, [&] { set_smem(k_aev<true, float>, sm); });
         MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     } else {
-        static bool once = (set_smem(k_aev<false, float>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_aev<false, float>, [&] { set_smem(k_aev<false, float>, sm); });
         MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
     }
 }
@@ -666,12 +661,10 @@ void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_b
     const size_t sm = kAevWarps * kAevSmemPerWarp;
     const int gs = (a.n + kAevWarps - 1) / kAevWarps;
     if (fast) {
-        static bool once = (set_smem(k_aev<true, __nv_bfloat16>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_aev<true, __nv_bfloat16>, [&] { set_smem(k_aev<true, __nv_bfloat16>, sm); });
         MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     } else {
-        static bool once = (set_smem(k_aev<false, __nv_bfloat16>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_aev<false, __nv_bfloat16>, [&] { set_smem(k_aev<false, __nv_bfloat16>, sm); });
         MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
     }
 }
@@ -681,16 +674,13 @@ void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, const __n
     const size_t sm = kForceWarps * kForceSmemPerWarp;
     const int gs = (a.n + kForceWarps - 1) / kForceWarps;
     if (dG16) {
-        static bool once = (set_smem(k_forces<true, __nv_bfloat16>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_forces<true, __nv_bfloat16>, [&] { set_smem(k_forces<true, __nv_bfloat16>, sm); });
         MLP_LAUNCH("forces", st, k_forces<true, __nv_bfloat16><<<gs, kForceWarps * 32, sm, st>>>(a, dG16, grad));
     } else if (fast) {
-        static bool once = (set_smem(k_forces<true, float>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_forces<true, float>, [&] { set_smem(k_forces<true, float>, sm); });
         MLP_LAUNCH("forces", st, k_forces<true, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
     } else {
-        static bool once = (set_smem(k_forces<false, float>, sm), true);
-        (void)once;
+        once_per_device((const void*)k_forces<false, float>, [&] { set_smem(k_forces<false, float>, sm); });
         MLP_LAUNCH("forces", st, k_forces<false, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
     }
 }

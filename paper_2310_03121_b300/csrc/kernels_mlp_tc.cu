@@ -1216,19 +1216,16 @@ __global__ void __launch_bounds__(kEnsThreads, 1) k_mlp_b1_ens(const __grid_cons
 
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        else
-            cudaGetLastError();
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -1314,22 +1311,14 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
     M.W3t = w.tmW3t;
     M.W2t = w.tmW2t;
     M.W1t = w.tmW1t;
-    static bool attr = false;
-    if (!attr) {
+    once_per_device((const void*)k_mlp_b1_ens, [] {
         cudaFuncSetAttribute(k_mlp_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
         cudaFuncSetAttribute(k_mlp_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
         cudaFuncSetAttribute(k_mlp_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
         cudaFuncSetAttribute(k_mlp_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
         cudaFuncSetAttribute(k_mlp_b1_ens, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsSmemAlloc);
-        attr = true;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
+    });
+    const int sms = sm_count();
     const int tiles = rows_cap / kTileRows;
     const int units = tiles * w.n_nets;   // (tile, net) pairs, spread over the CTAs
     const int grid = units < sms ? units : sms;

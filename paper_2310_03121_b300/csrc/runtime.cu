@@ -6,6 +6,8 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -176,6 +178,33 @@ void profile_reset() {
     std::lock_guard<std::mutex> lk(P.mu);
     resolve_locked(P);
     P.totals.clear();
+}
+
+std::mutex& once_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+
+bool once_first(int device, const void* key) {
+    static std::set<std::pair<int, const void*>> seen;
+    return seen.insert({device, key}).second;
+}
+
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(once_mutex());
+    int& c = cache[dev & 63];
+    if (c <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 148;
+        }
+        c = v;
+    }
+    return c;
 }
 
 }  // namespace mlp
