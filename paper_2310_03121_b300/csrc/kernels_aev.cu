@@ -169,18 +169,17 @@ struct NbrLane {
 };
 
 template <bool FAST>
-__device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* row, int q, int cnt,
-                                                 const float4& hi_i, const float4& lo_i) {
+__device__ __forceinline__ NbrLane make_neighbor(int j, const float4& hj, const float4& lj, const float4& hi_i,
+                                                 const float4& lo_i, const Box& box) {
     NbrLane nl;
     nl.d = make_float3(0.f, 0.f, 0.f);
     nl.r = 1.f;
     nl.sp = 0;
     nl.j = 0;
     nl.inR = nl.inA = false;
-    if (q < cnt) {
-        nl.j = row[q];
-        const float4 hj = a.hi[nl.j], lj = a.lo[nl.j];
-        nl.d = displacement(hi_i, lo_i, hj, lj, a.box);
+    if (j >= 0) {
+        nl.j = j;
+        nl.d = displacement(hi_i, lo_i, hj, lj, box);
         const float r2 = nl.d.x * nl.d.x + nl.d.y * nl.d.y + nl.d.z * nl.d.z;
         nl.r = FAST ? M<true>::sq(r2) : sqrtf(r2);
         nl.inR = nl.r < kRcRad;
@@ -188,6 +187,45 @@ __device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* ro
         nl.sp = species_of(hj);
     }
     return nl;
+}
+
+template <bool FAST>
+__device__ __forceinline__ NbrLane load_neighbor(const AevArgs& a, const int* row, int q, int cnt,
+                                                 const float4& hi_i, const float4& lo_i) {
+    const int j = q < cnt ? row[q] : -1;
+    float4 hj = make_float4(0.f, 0.f, 0.f, 0.f), lj = hj;
+    if (j >= 0) {
+        hj = a.hi[j];
+        lj = a.lo[j];
+    }
+    return make_neighbor<FAST>(j, hj, lj, hi_i, lo_i, a.box);
+}
+
+// The first two chunks (list positions q and q + 32) with both chunks' loads
+// in flight together: two dependent memory round trips instead of five for
+// an atom with 33 to 64 neighbors. Returns the atom's neighbor count.
+template <bool FAST>
+__device__ __forceinline__ int load_neighbors2(const AevArgs& a, const int* row, const int* cnt_p, int q,
+                                               const float4& hi_i, const float4& lo_i, NbrLane& n0, NbrLane& n1) {
+    // the list entries are read up to the row's capacity before the count is
+    // known (slots past the count hold stale indices and are discarded), so
+    // count and entries take one round trip together
+    int j0 = q < a.cap ? row[q] : -1, j1 = q + 32 < a.cap ? row[q + 32] : -1;
+    const int cnt = min(*cnt_p, a.cap);
+    if (q >= cnt) j0 = -1;
+    if (q + 32 >= cnt) j1 = -1;
+    float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), l0 = h0, h1 = h0, l1 = h0;
+    if (j0 >= 0) {
+        h0 = a.hi[j0];
+        l0 = a.lo[j0];
+    }
+    if (j1 >= 0) {
+        h1 = a.hi[j1];
+        l1 = a.lo[j1];
+    }
+    n0 = make_neighbor<FAST>(j0, h0, l0, hi_i, lo_i, a.box);
+    n1 = make_neighbor<FAST>(j1, h1, l1, hi_i, lo_i, a.box);
+    return cnt;
 }
 
 // Appends this chunk's angular neighbors to the stage; returns the new count.
@@ -265,18 +303,18 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
     AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kAevSmemPerWarp);
     AevScratch& X = *reinterpret_cast<AevScratch*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
+    const int* row = a.nbr + (size_t)i * a.cap;
+    NbrLane nl0, nl1;
+    const int cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
     for (int c = lane; c < 2 * kRadLen; c += 32) X.accR[c] = 0.f;
     __syncwarp();
 
-    const int cnt = min(a.nbr_cnt[i], a.cap);
-    const int* row = a.nbr + (size_t)i * a.cap;
     const int k = lane & 15, h = lane >> 4;
     const float Rk = c_aev.shf_r[k];
     float* accR = X.accR + h * kRadShifts;
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
-    for (int base = 0; base < cnt; base += 32) {
-        const NbrLane nl = load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
+    auto chunk = [&](const NbrLane& nl, int base) {
         const float fcr = nl.inR ? 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcRad)) + 0.5f : 0.f;
         const int nq = min(32, cnt - base);
         for (int q = 0; q < nq; q += 2) {
@@ -290,7 +328,10 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             }
         }
         mA = stage_angular<FAST>(nl, mA, s, a);
-    }
+    };
+    if (cnt > 0) chunk(nl0, 0);
+    if (cnt > 32) chunk(nl1, 32);
+    for (int base = 64; base < cnt; base += 32) chunk(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i), base);
     if (mA > kMaxAng) mA = 0;   // reported as an error by the host; keep every index in range
     __syncwarp();
     const int si = species_of(hi_i);
@@ -490,9 +531,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
     // inside one radial block or one 32-column angular row. All of a lane's
     // loads are issued before the first store, so the row costs one memory
     // round trip, not four.
-    const int cnt = min(a.nbr_cnt[i], a.cap);
     const int* row = a.nbr + (size_t)i * a.cap;
-    NbrLane nl0;
+    NbrLane nl0, nl1;
+    int cnt;
     {
         float v[4][8];
 #pragma unroll
@@ -500,8 +541,8 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
             const int c = 8 * lane + 256 * q;
             if (c < kAevLen) load8(grow + c, v[q]);
         }
-        // the first 32 neighbors' loads overlap the dE/dG row's
-        nl0 = load_neighbor<FAST>(a, row, lane, cnt, hi_i, lo_i);
+        // the first 64 neighbors' loads overlap the dE/dG row's
+        cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c = 8 * lane + 256 * q;
@@ -521,8 +562,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
     // radial: one neighbor per lane. The gradient on an angular neighbor goes
     // to its (still private) shared-memory slot, which the angular terms add
     // to and which is flushed once; other neighbors go straight to the FP64 sums.
-    for (int base = 0; base < cnt; base += 32) {
-        const NbrLane nl = base == 0 ? nl0 : load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i);
+    auto chunk = [&](const NbrLane& nl) {
         int pA;
         mA = stage_angular<FAST>(nl, mA, s, a, &pA);
         if (nl.inR) {
@@ -544,7 +584,10 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
             fiy -= gy;
             fiz -= gz;
         }
-    }
+    };
+    if (cnt > 0) chunk(nl0);
+    if (cnt > 32) chunk(nl1);
+    for (int base = 64; base < cnt; base += 32) chunk(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i));
     const int mS = min(mA, kMaxAng);   // staged slots (flushed even on overflow)
     if (mA > kMaxAng) mA = 0;
     __syncwarp();
