@@ -40,6 +40,8 @@ struct AevConsts {
     float shf_a[kAngA];
     float cos_z[kAngZ];
     float sin_z[kAngZ];
+    float hcos_z[kAngZ];   // cos_z / 2, sin_z / 2: 1 + cos(theta - theta_z) over 2 in two FMAs
+    float hsin_z[kAngZ];
 };
 
 // Orthorhombic box: L (float), split L = Lhi + Llo, 1/L; periodic = 0 for open.

@@ -48,6 +48,8 @@ void init_constants_for_current_device() {
             double Z = (2.0 * z + 1.0) * pi / 16.0;
             h.cos_z[z] = (float)cos(Z);
             h.sin_z[z] = (float)sin(Z);
+            h.hcos_z[z] = (float)(0.5 * cos(Z));
+            h.hsin_z[z] = (float)(0.5 * sin(Z));
         }
         cudaMemcpyToSymbol(c_aev, &h, sizeof(h));
     });
@@ -74,6 +76,7 @@ struct M<false> {   // accurate FP32 library functions (FP32 path)
     static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float dv(float a, float b) { return a / b; }
     static __device__ __forceinline__ float rcp(float x) { return 1.f / x; }
+    static __device__ __forceinline__ float gauss(float eta, float d) { return expf(-eta * d * d); }
 };
 template <>
 struct M<true> {    // hardware approximations with subnormals flushed (BF16-network path)
@@ -100,6 +103,8 @@ struct M<true> {    // hardware approximations with subnormals flushed (BF16-net
     // exp(x) = 2^(x log2 e); b^e = 2^(e log2 b)
     static __device__ __forceinline__ float ex(float x) { return ex2(x * 1.4426950408889634f); }
     static __device__ __forceinline__ float pw(float b, float e) { return ex2(e * lg2(b)); }
+    // exp(-eta d^2) with -eta log2 e folded into one constant (eta is a compile-time constant)
+    static __device__ __forceinline__ float gauss(float eta, float d) { return ex2((-eta * 1.4426950408889634f) * d * d); }
     static __device__ __forceinline__ float cpi(float x) {
         float y;
         asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(3.14159265358979f * x));
@@ -153,6 +158,7 @@ constexpr int kGsRad = kNSpecies * kGsRadStride;
 constexpr int kGsFloats = kGsRad + kNPairs * kGsAngStride;
 constexpr size_t kForceSmemPerWarp = round16(sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float));
 static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-warp shared regions must be 16-byte aligned");
+static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AEV row start on 16 bytes");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -293,6 +299,21 @@ __device__ __forceinline__ void put_g(__nv_bfloat16* out, __nv_bfloat16* out_lo,
     if (out_lo) out_lo[c] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Zeros columns [c0, c1) of an AEV row (and of its lo row) with 16-byte
+// stores; c0 and c1 are multiples of 16 bytes' worth of columns (every
+// element-pair block starts on one: 112 + 32 p columns).
+template <typename OutT>
+__device__ __forceinline__ void zero_cols(OutT* out, OutT* out_lo, int c0, int c1, int lane) {
+    constexpr int per = 16 / (int)sizeof(OutT);
+    const int n = (c1 - c0) / per;
+    uint4* d = reinterpret_cast<uint4*>(out + c0);
+    uint4* dl = out_lo ? reinterpret_cast<uint4*>(out_lo + c0) : nullptr;
+    for (int q = lane; q < n; q += 32) {
+        d[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (dl) dl[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 template <bool FAST, typename OutT>
 __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
                                                       int* __restrict__ row_atom) {
@@ -324,7 +345,7 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             const float ff = __shfl_sync(kFull, fcr, src);
             if (src < nq && ff > 0.f) {
                 const float dr = rr - Rk;
-                accR[ss * 2 * kRadShifts + k] += 0.25f * M<FAST>::ex(-kEtaRad * dr * dr) * ff;
+                accR[ss * 2 * kRadShifts + k] += 0.25f * M<FAST>::gauss(kEtaRad, dr) * ff;
             }
         }
         mA = stage_angular<FAST>(nl, mA, s, a);
@@ -395,7 +416,7 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
         int cur_p = -1, next_p = 0, p = 0;
         auto flush = [&]() {
             if (cur_p < 0) return;
-            for (; next_p < cur_p; ++next_p) put_g(out, out_lo, kRadLen + 32 * next_p + lane, 0.f);
+            if (next_p < cur_p) zero_cols(out, out_lo, kRadLen + 32 * next_p, kRadLen + 32 * cur_p, lane);
             put_g(out, out_lo, kRadLen + 32 * cur_p + lane, acc);
             next_p = cur_p + 1;
         };
@@ -430,16 +451,19 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
                 const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
                 const float sn = M<FAST>::sq(1.f - c * c);
                 const float f2 = 2.f * s.fc[J] * s.fc[K];
+                // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
+                const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
 #pragma unroll
                 for (int zz = 0; zz < kAngZ; ++zz) {
-                    const float b = 0.5f + 0.5f * (c * c_aev.cos_z[zz] + sn * c_aev.sin_z[zz]);
-                    X.pf[lane * 9 + zz] = f2 * M<FAST>::pw(b, kZeta);
+                    const float b = fmaf(c, c_aev.hcos_z[zz], fmaf(sn, c_aev.hsin_z[zz], 0.5f));
+                    X.pf[lane * 9 + zz] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b), lf2))
+                                               : f2 * M<false>::pw(b, kZeta);
                 }
                 const float rbar = 0.5f * (uj.w + uk.w);
 #pragma unroll
                 for (int q = 0; q < kAngA; ++q) {
                     const float dr = rbar - c_aev.shf_a[q];
-                    X.rf[lane * 5 + q] = M<FAST>::ex(-kEtaAng * dr * dr);
+                    X.rf[lane * 5 + q] = M<FAST>::gauss(kEtaAng, dr);
                 }
             }
             const int prevp = __shfl_up_sync(kFull, myp, 1);
@@ -461,14 +485,14 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             __syncwarp();
         }
         flush();
-        for (; next_p < kNPairs; ++next_p) put_g(out, out_lo, kRadLen + 32 * next_p + lane, 0.f);
+        // the absent blocks after the last present one, and the row's padding
+        zero_cols(out, out_lo, kRadLen + 32 * next_p, kAevLd, lane);
     }
-    // radial block (two halves) and the zero padding of the row
+    // radial block (two halves)
     for (int c = lane; c < kRadLen; c += 32) {
         const int a = 2 * kRadShifts * (c >> 4) + (c & 15);
         put_g(out, out_lo, c, X.accR[a] + X.accR[a + kRadShifts]);
     }
-    if (lane < kAevLd - kAevLen) put_g(out, out_lo, kAevLen + lane, 0.f);
     if (lane == 0) row_atom[rw] = i;
 }
 
@@ -605,6 +629,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
                 const float c = 0.95f * cos0;
                 const float sn = M<FAST>::sq(1.f - c * c);
                 const float isn = M<FAST>::rcp(sn);
+                const float hz_isn = 0.5f * kZeta * isn;
                 const float rbar = 0.5f * (uj.w + uk.w);
                 const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
                 const int p = pair_index(s.sp[j], s.sp[kk]);
@@ -612,18 +637,27 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
 #pragma unroll
                 for (int aa = 0; aa < kAngA; ++aa) {
                     const float dr = rbar - c_aev.shf_a[aa];
-                    R[aa] = M<FAST>::ex(-kEtaAng * dr * dr);
+                    R[aa] = M<FAST>::gauss(kEtaAng, dr);
                     dR[aa] = -2.f * kEtaAng * dr * R[aa];
                 }
                 const float* gp = gs + kGsRad + kGsAngStride * p;
                 float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
                 for (int z = 0; z < kAngZ; ++z) {
-                    const float cm = c * c_aev.cos_z[z] + sn * c_aev.sin_z[z];
-                    const float sm = sn * c_aev.cos_z[z] - c * c_aev.sin_z[z];
-                    const float b = 0.5f + 0.5f * cm;
-                    const float Pz = 2.f * M<FAST>::pw(b, kZeta);
-                    const float dPdc = 0.5f * kZeta * Pz * sm * M<FAST>::rcp(b) * isn;
+                    // b = (1 + cos(theta - theta_z)) / 2, sm = sin(theta - theta_z)
+                    const float b = fmaf(c, c_aev.hcos_z[z], fmaf(sn, c_aev.hsin_z[z], 0.5f));
+                    const float sm = fmaf(sn, c_aev.cos_z[z], -c * c_aev.sin_z[z]);
+                    float Pz, dPdc;
+                    if (FAST) {
+                        // Q = 2 b^(zeta - 1): Pz = 2 b^zeta = Q b and dPz/dc = (zeta / 2) Q sm / sin,
+                        // no reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z)
+                        const float Q = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b), 1.f));
+                        Pz = Q * b;
+                        dPdc = hz_isn * Q * sm;
+                    } else {
+                        Pz = 2.f * M<false>::pw(b, kZeta);
+                        dPdc = 0.5f * kZeta * Pz * sm * M<false>::rcp(b) * isn;
+                    }
                     float S1 = 0.f, S2 = 0.f;
 #pragma unroll
                     for (int aa = 0; aa < kAngA; ++aa) {
