@@ -48,7 +48,7 @@ UNIT = "atom-evals/s"
 WORKLOAD = ("served stream: 20,000 open-boundary molecules, N log-uniform in [8, 256] (1,426,039 atoms), "
             "ANI-2x-shaped network 1008-256-192-160-1 x 7 elements")
 
-# Algorithmic work per atom of each kernel (measurement section).
+# Algorithmic work per atom of each kernel.
 MLP_FLOP_FWD = 2 * (1008 * 256 + 256 * 192 + 192 * 160 + 160)          # 676,160
 MLP_FLOP_BWD = 2 * (160 * 192 + 192 * 256 + 256 * 1008)                 # 675,840
 MLP_FLOP_B1 = 2 * 256 * 1008                                             # 516,096 (dE/dG = g1 W1)
@@ -396,6 +396,11 @@ def run_ours(args):
     # ---------------- Langevin dynamics (2 fs), graph-replayed steps
     if not args.no_md and rank == 0:
         result["langevin_md"] = langevin_md(P, args)
+        result["box_md"] = box_md(P, args)
+
+    # ---------------- every synthetic system at both precisions, one evaluation per call
+    if not args.no_configs and rank == 0:
+        result["systems"] = per_system(P, args)
 
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(stream, wts, args.cpu_seconds)
@@ -410,7 +415,7 @@ def run_ours(args):
 
 
 # Counted FP32 operations of the algorithm per term (FMA = 2, transcendental = 1),
-# from the loop bodies of the kernels (see DESIGN.md, section 5):
+# from the loop bodies of the kernels:
 FLOP_AEV_PER_NEIGHBOR = 100     # 16 radial shifts + cutoff
 FLOP_AEV_PER_PAIR = 180         # geometry, 8 angle factors, 4 distance factors, 32 products
 FLOP_FORCE_PER_NEIGHBOR = 175   # 16 radial shifts with derivatives + cutoff + vector
@@ -443,12 +448,12 @@ def term_counts(stream):
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
     # launch (profiles/); valid only while the kernel source is the one that was captured
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
-               "bytes_per_atom": (599.072512e6 + 216.025856e6) / 131056},
-    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
-                 "bytes_per_atom": (361.540864e6 + 257.555200e6) / 65518},
-    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "331dfb396f11dc5a735ff5a768e944a806e7e200",
-                        "bytes_per_atom": (300.759040e6 + 108.273664e6) / 65518},
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
+               "bytes_per_atom": (603.639808e6 + 215.792640e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
+                 "bytes_per_atom": (361.978368e6 + 257.837824e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
+                        "bytes_per_atom": (300.741120e6 + 108.992512e6) / 65518},
 }
 
 
@@ -615,6 +620,91 @@ def langevin_md(P, args):
     return out
 
 
+def per_system(P, args):
+    """Each synthetic system (the 24-atom molecule, the 672-atom ligand in
+    water, the 6,561-atom and 21,080-atom periodic water boxes) at both
+    precisions through the device path (mlp_energy_forces_device, coordinates
+    resident on the device): ms per evaluation and atom-evals/s, CUDA events
+    on the launching stream around each evaluation, L2 flushed (256 MB write)
+    before each."""
+    import torch
+
+    import gen
+
+    W = P.Weights(gen.make_weights())
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    names = {0: "24-atom molecule", 1: "672-atom ligand in water", 2: "6,561-atom water box (periodic)",
+             4: "21,080-atom solvated box (periodic)"}
+    out = []
+    for k, name in names.items():
+        c = gen.make_config(k)
+        x = torch.from_numpy(np.ascontiguousarray(c.coords)).cuda()
+        for prec in ("fp32", "bf16"):
+            s = P.System(W, c.species, c.coords, c.cell, precision=prec)
+            for _ in range(3):
+                s.energy_forces_device(x)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.config_reps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.energy_forces_device(x)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = float(np.median(ms))
+            out.append({"system": name, "atoms": int(c.n), "precision": prec, "ms_per_eval": t,
+                        "atom_evals_per_s": c.n / (t * 1e-3)})
+            s.close()
+    W.close()
+    return out
+
+
+def box_md(P, args):
+    """Langevin dynamics (LF-Middle) of the 21,080-atom periodic solvated box
+    at 0.5 fs with a 5.6 A list (0.5 A skin, rebuilt on the device when an
+    atom has moved half the skin), BF16 network: wall time per step over runs
+    of 100 graph-replayed steps, up to args.box_md_steps steps. Random-init
+    weights have no repulsive core, so the run stops at the first run that
+    reports an error (atoms collapsing past the neighbor capacity) and the
+    rate is over the completed runs."""
+    import torch
+
+    import gen
+
+    c = gen.make_config(4)
+    W = P.Weights(gen.make_weights())
+    masses = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
+    m = masses[c.species][:, None]
+    v0 = np.random.default_rng(0).normal(size=c.coords.shape) * np.sqrt(8.617333262e-5 * 300.0 / (m * 103.6426965))
+    s = P.System(W, c.species, c.coords, c.cell, precision="bf16", skin=0.5)
+    L = P.Langevin(s, dt_fs=0.5, friction_per_ps=1.0, temperature_K=300.0, seed=1, use_graph=True)
+    x = torch.from_numpy(np.ascontiguousarray(c.coords)).cuda()
+    v = torch.from_numpy(np.ascontiguousarray(v0)).cuda()
+    per_run, done, walls, err = 100, 0, [], None
+    while done < args.box_md_steps:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            L.run(x, v, done, per_run, energies=False)
+        except P.MLPError as e:
+            err = str(e)
+            break
+        walls.append(time.perf_counter() - t0)
+        done += per_run
+    L.close()
+    s.close()
+    W.close()
+    row = {"system": "21,080-atom solvated box (periodic), 0.5 fs, skin 0.5 A", "atoms": int(c.n),
+           "steps_completed": done, "stopped": err}
+    timed = walls[1:]                      # the first run captures the graph
+    if timed:
+        us = sum(timed) / (per_run * len(timed)) * 1e6
+        row.update({"us_per_step": us, "atom_steps_per_s": c.n / (us * 1e-6)})
+    return row
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -639,6 +729,9 @@ def main():
                     help="host-core seconds of the reference (oracle) run, spread over its steps")
     ap.add_argument("--no-md", action="store_true", help="skip the Langevin dynamics timing")
     ap.add_argument("--md-steps", type=int, default=1000)
+    ap.add_argument("--box-md-steps", type=int, default=1000)
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-system timing")
+    ap.add_argument("--config-reps", type=int, default=20)
     ap.add_argument("--ensemble-nets", type=int, default=8,
                     help="also time an ensemble of this many nets on the same stream (<= 1: skip)")
     args = ap.parse_args()
