@@ -73,8 +73,9 @@ constexpr uint32_t kAtom = 128 * 128;            // 128 rows x 64 BF16 (one K at
 //   split only:   h1_lo [64K, 128K) from E1 to F2, h2_lo [112K, 160K) from E2 to F3
 //   B1 only:      dE/dG staging [64K, 112K), one 32-row x 64-column box (4 KB) per epilogue warp
 //   weight rings: F2 [128K, 200K) 3 x 24 KB, F3 [160K, 200K) 2 x 20 KB,
-//                 B3 [160K, 208K) 2 x 24 KB, B2 and B1 [128K, 192K) 2 x 32 KB
-//                 (deeper rings, up to 224 KB, measured 2% slower)
+//                 B3 [160K, 208K) 2 x 24 KB, B2 and B1 [112K, 208K) 3 x 32 KB
+//                 (g3 is free once B3's MMAs are done; more shared memory
+//                 for deeper rings, up to 224 KB, measured 2% slower)
 //   F1 stages over [0, 192K): 4 x 48 KB; split: 32 K columns per stage (G_hi, G_lo
 //   8 KB each, W1_hi, W1_lo 16 KB each; 64-byte swizzle), so that three stages
 //   are in flight while one is consumed; one pass: 64 K columns (G 16 KB, W1 32 KB)
@@ -358,11 +359,11 @@ __device__ __forceinline__ Job make_job(const TcMaps& M, int k, int s) {
         case kJobB3:
             return Job{&M.W3t, nullptr, s * kH2, 3, 2, kOffG3, 0, 256, kH2, 10 * kAtom, 24576u, 2, 0};
         case kJobB2:
-            return Job{&M.W2t, nullptr, s * kH1, 3, 4, kOffH2, 0, 0, kH1, 8 * kAtom, 32768u, 2, 0};
+            return Job{&M.W2t, nullptr, s * kH1, 3, 4, kOffH2, 0, 0, kH1, 7 * kAtom, 32768u, 3, 0};
         default: {
             const int j = k - kJobB1;
             return Job{&M.W1t, nullptr, s * kAevLd + 256 * j, 4, 4, kOffH1, 0, 256u * (uint32_t)(j & 1), 256,
-                       8 * kAtom, 32768u, 2, 0};
+                       7 * kAtom, 32768u, 3, 0};
         }
     }
 }
