@@ -751,7 +751,15 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
             if (warp == 2) MLP_TC_MARK(4);
 
             // ---- E3: energy (column-part partial sums per row, added in
-            // fixed order by part 0) and g3 = w4 * celu'(z3)
+            // fixed order by the last part, which has 3 of the 10 16-column
+            // chunks, part 0 has 4) and g3 = w4 * celu'(z3). The finishing
+            // part's global reads are issued before the accumulator is ready.
+            int e_atom = 0;
+            float e_b4 = 0.f;
+            if (part == kParts - 1 && r < nvalid) {
+                e_atom = p.row_atom[row0 + r];
+                e_b4 = __ldg(p.b4 + es);
+            }
             if (!epi_acc(X, 0)) break;
             if (warp == 2) MLP_TC_MARK(5);
             {
@@ -783,16 +791,16 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 asm volatile("st.shared.f32 [%0], %1;" ::"r"(ep + 4u * (uint32_t)part), "f"(es_part) : "memory");
                 __syncwarp();
                 if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarEPart);
-                if (part == 0) {
+                if (part == kParts - 1) {
                     if (!epi_wait(X, bar0 + 8u * kBarEPart, n_epart & 1u)) break;
                     if (r < nvalid) {
                         const uint4 v = ld_shared_v4(ep);
-                        float e = __ldg(p.b4 + es);
+                        float e = e_b4;
                         e += __uint_as_float(v.x);
                         e += __uint_as_float(v.y);
                         e += __uint_as_float(v.z);
                         // ensemble: net k's energies go to row k of e[K][e_stride]
-                        p.e[(ENS ? (size_t)net * (size_t)p.e_stride : 0) + p.row_atom[row0 + r]] = e;
+                        p.e[(ENS ? (size_t)net * (size_t)p.e_stride : 0) + e_atom] = e;
                     }
                 }
                 ++n_epart;
