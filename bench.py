@@ -452,12 +452,12 @@ def term_counts(stream):
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
     # launch (profiles/); valid only while the kernel source is the one that was captured
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
-               "bytes_per_atom": (603.639808e6 + 215.792640e6) / 131056},
-    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
-                 "bytes_per_atom": (361.978368e6 + 257.837824e6) / 65518},
-    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "c4e907addbdc7337e143a3605714222e4f38d786",
-                        "bytes_per_atom": (300.741120e6 + 108.992512e6) / 65518},
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
+               "bytes_per_atom": (559.401984e6 + 217.676544e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
+                 "bytes_per_atom": (360.886784e6 + 256.885760e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
+                        "bytes_per_atom": (300.726528e6 + 109.793536e6) / 65518},
 }
 
 
