@@ -129,16 +129,19 @@ struct AngStage {
     int idx[kMaxAng];      // atom index
 };
 
+constexpr int kPairRow = 34;
+
 // Forward scratch of one warp (after its angular stage).
 struct AevScratch {
     float accR[2 * kRadLen];    // radial accumulators [element][half][shift]: the two 16-lane
                                 // halves of a warp use disjoint banks whatever their elements
-    // per pair (one per lane): 2 fc fc P_z for the 8 sections and the 4
-    // distance Gaussians; rows of 9 and 5 floats so that both the writing
-    // lanes (one row each) and the reading lanes (one row, 8 or 4 columns)
-    // hit distinct banks
-    float pf[32 * 9];
-    float rf[32 * 5];
+    // per pair q (one per lane): 2 fc fc P_z for the 8 sections (pfT[z][q])
+    // and the 4 distance Gaussians (rfT[a][q]); rows of 34 floats, so that
+    // the writing lanes (consecutive q) and the reading lanes (8 or 4 rows,
+    // one address per row) hit distinct banks and two consecutive pairs of a
+    // row load as one 8-byte word
+    float pfT[kAngZ * kPairRow];
+    float rfT[kAngA * kPairRow];
     int ord[64];                // sorted (by element) position -> stage slot
     int off[kNPairs + 1];       // first pair of each element pair in pair order
     int pdesc[kNPairs];         // element groups of the pair: g1 | c1 << 8 | g2 << 16 | c2 << 24
@@ -159,6 +162,8 @@ constexpr int kGsFloats = kGsRad + kNPairs * kGsAngStride;
 constexpr size_t kForceSmemPerWarp = round16(sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float));
 static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-warp shared regions must be 16-byte aligned");
 static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AEV row start on 16 bytes");
+static_assert(offsetof(AevScratch, pfT) % 8 == 0 && offsetof(AevScratch, rfT) % 8 == 0 && kPairRow % 2 == 0,
+              "pair rows load two floats at a time");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -336,7 +341,8 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
     auto chunk = [&](const NbrLane& nl, int base) {
-        const float fcr = nl.inR ? 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcRad)) + 0.5f : 0.f;
+        // fc(r) / 4: the radial prefactor folded into the shuffled cutoff value
+        const float fcr = nl.inR ? fmaf(0.125f, M<FAST>::cpi(nl.r * (1.f / kRcRad)), 0.125f) : 0.f;
         const int nq = min(32, cnt - base);
         for (int q = 0; q < nq; q += 2) {
             const int src = q + h;
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             const float ff = __shfl_sync(kFull, fcr, src);
             if (src < nq && ff > 0.f) {
                 const float dr = rr - Rk;
-                accR[ss * 2 * kRadShifts + k] += 0.25f * M<FAST>::gauss(kEtaRad, dr) * ff;
+                accR[ss * 2 * kRadShifts + k] += M<FAST>::gauss(kEtaRad, dr) * ff;
             }
         }
         mA = stage_angular<FAST>(nl, mA, s, a);
@@ -432,14 +438,16 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
                 const int g1 = dsc & 255, c1 = (dsc >> 8) & 255, g2 = (dsc >> 16) & 255, c2 = (dsc >> 24) & 255;
                 int jj, kk;
                 if (g1 != g2) {   // two groups: l = ja * c2 + kb
-                    int ja = (int)(((float)l + 0.5f) / (float)c2);
+                    // (l + 1/2) / c2 lies at least 1 / (2 c2) from an integer, far beyond
+                    // the approximate reciprocal's error; the two checks keep it exact anyway
+                    int ja = (int)(((float)l + 0.5f) * M<true>::rcp((float)c2));
                     if (ja * c2 > l) --ja;
                     if ((ja + 1) * c2 <= l) ++ja;
                     jj = g1 + ja;
                     kk = g2 + (l - ja * c2);
                 } else {          // one group of c1: row-major pairs (ja < kb), row ja starts at ja (2 c1 - ja - 1) / 2
                     const int t = 2 * c1 - 1;
-                    int ja = (int)(0.5f * ((float)t - sqrtf((float)(t * t - 8 * l))));
+                    int ja = (int)(0.5f * ((float)t - M<true>::sq((float)(t * t - 8 * l))));
                     ja = max(0, min(ja, c1 - 2));
                     while (ja > 0 && ja * (t - ja) / 2 > l) --ja;
                     while ((ja + 1) * (t - ja - 1) / 2 <= l) ++ja;
@@ -456,14 +464,14 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
 #pragma unroll
                 for (int zz = 0; zz < kAngZ; ++zz) {
                     const float b = fmaf(c, c_aev.hcos_z[zz], fmaf(sn, c_aev.hsin_z[zz], 0.5f));
-                    X.pf[lane * 9 + zz] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b), lf2))
+                    X.pfT[zz * kPairRow + lane] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b), lf2))
                                                : f2 * M<false>::pw(b, kZeta);
                 }
                 const float rbar = 0.5f * (uj.w + uk.w);
 #pragma unroll
                 for (int q = 0; q < kAngA; ++q) {
                     const float dr = rbar - c_aev.shf_a[q];
-                    X.rf[lane * 5 + q] = M<FAST>::gauss(kEtaAng, dr);
+                    X.rfT[q * kPairRow + lane] = M<FAST>::gauss(kEtaAng, dr);
                 }
             }
             const int prevp = __shfl_up_sync(kFull, myp, 1);
@@ -479,8 +487,22 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
                     cur_p = pq;
                     acc = 0.f;
                 }
-#pragma unroll 4
-                for (int q = q0; q < q1; ++q) acc = fmaf(X.pf[q * 9 + z], X.rf[q * 5 + aa], acc);
+                // the run's pairs in order, two per 8-byte load where aligned
+                const float* pz = X.pfT + z * kPairRow;
+                const float* ra = X.rfT + aa * kPairRow;
+                int q = q0;
+                if (q & 1) {
+                    acc = fmaf(pz[q], ra[q], acc);
+                    ++q;
+                }
+#pragma unroll 2
+                for (; q + 1 < q1; q += 2) {
+                    const float2 p2 = *reinterpret_cast<const float2*>(pz + q);
+                    const float2 r2 = *reinterpret_cast<const float2*>(ra + q);
+                    acc = fmaf(p2.x, r2.x, acc);
+                    acc = fmaf(p2.y, r2.y, acc);
+                }
+                if (q < q1) acc = fmaf(pz[q], ra[q], acc);
             }
             __syncwarp();
         }
