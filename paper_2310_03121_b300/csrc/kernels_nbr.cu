@@ -181,17 +181,40 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
     Box box{};
     int count = 0;
     int* row = a.nbr + (size_t)i * a.cap;
-    for (int base = beg; base < end; base += 32) {
-        int j = base + lane;
-        bool ok = false;
-        if (j < end && j != i) {
-            float3 d = displacement(hi_i, lo_i, a.hi[j], a.lo[j], box);
-            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
-        }
+    auto emit = [&](int j, bool ok) {
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         int pos = count + __popc(mask & lanemask_lt());
         if (ok && pos < a.cap) row[pos] = j;
         count += __popc(mask);
+    };
+    // two chunks of 32 candidates per pass, both chunks' positions loaded
+    // before either is tested (one memory round trip per 64 candidates)
+    for (int base = beg; base < end; base += 64) {
+        const int j0 = base + lane, j1 = base + 32 + lane;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 h0 = z4, l0 = z4, h1 = z4, l1 = z4;
+        if (j0 < end) {
+            h0 = a.hi[j0];
+            l0 = a.lo[j0];
+        }
+        if (j1 < end) {
+            h1 = a.hi[j1];
+            l1 = a.lo[j1];
+        }
+        bool ok = false;
+        if (j0 < end && j0 != i) {
+            const float3 d = displacement(hi_i, lo_i, h0, l0, box);
+            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+        }
+        emit(j0, ok);
+        if (base + 32 < end) {
+            ok = false;
+            if (j1 < end && j1 != i) {
+                const float3 d = displacement(hi_i, lo_i, h1, l1, box);
+                ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+            }
+            emit(j1, ok);
+        }
     }
     if (lane == 0) {
         a.nbr_cnt[i] = count;
