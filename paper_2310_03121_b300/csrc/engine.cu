@@ -194,10 +194,14 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
             launch_gather_subset(st, n, sp.d_index, sp.d_coords_full, sp.n_full, const_cast<double*>(sp.d_xyz),
                                  ws.ctr);
         NbrArgs na{ws.hi, ws.lo, ws.nbr, ws.nbr_cnt, ws.nbr_cap, sp.r_list * sp.r_list};
-        if (batch) {
-            launch_stage_batch(st, sp.n_mols, n, sp.d_mol_start, sp.d_xyz, sp.d_species, ws.hi, ws.lo, ws.rank,
-                               ws.ctr, ws.grad);
-            launch_nbr_allpairs(st, n, sp.n_mols, sp.d_mol_start, na, ws.ctr);
+        // a small open system without a persistent list: all pairs of one
+        // molecule (2 launches) instead of the cell list (7 launches; launch
+        // latency dominates at this size, e.g. a ligand's integrator step)
+        const bool small_open = !batch && !sp.periodic && sp.half_skin2 <= 0.f && n <= kAllPairsMaxAtoms;
+        if (batch || small_open) {
+            launch_stage_batch(st, batch ? sp.n_mols : 1, n, batch ? sp.d_mol_start : nullptr, sp.d_xyz,
+                               sp.d_species, ws.hi, ws.lo, ws.rank, ws.ctr, ws.grad);
+            launch_nbr_allpairs(st, n, batch ? sp.n_mols : 1, batch ? sp.d_mol_start : nullptr, na, ws.ctr);
         } else {
             if (!ws.cell_path) return set_error(-1, "workspace has no cell list");
             launch_stage_system(st, n, sp.d_xyz, sp.d_species, sp.L, sp.periodic, sp.periodic ? 0 : 1, ws.hi, ws.lo,

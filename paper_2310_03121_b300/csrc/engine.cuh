@@ -84,6 +84,10 @@ int workspace_create(Workspace& ws, int cap_atoms, int cap_mols, int precision, 
                      int max_cells, int nets);
 void workspace_destroy(Workspace& ws);
 
+// Open systems of at most this many atoms without a persistent neighbor list
+// take the all-pairs neighbor search of the batch path.
+constexpr int kAllPairsMaxAtoms = 1024;
+
 struct EvalSpec {
     int n_atoms = 0;
     int n_mols = 1;

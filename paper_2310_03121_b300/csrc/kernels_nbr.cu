@@ -129,9 +129,11 @@ __global__ void k_stage_batch(int n_mols, int n_atoms, const int* __restrict__ m
                               const double* __restrict__ xyz, const int8_t* __restrict__ species,
                               float4* __restrict__ hi, float4* __restrict__ lo, int* __restrict__ rank,
                               Counters* ctr, double* __restrict__ grad) {
+    // mol_start == nullptr: one molecule of n_atoms atoms (a small open system)
     int m = blockIdx.x;
-    int a = mol_start[m], b = mol_start[m + 1];
-    if (m == 0 && threadIdx.x == 0 && (a != 0 || mol_start[n_mols] != n_atoms)) atomicOr(&ctr->bad_species, 2);
+    int a = mol_start ? mol_start[m] : 0, b = mol_start ? mol_start[m + 1] : n_atoms;
+    if (mol_start && m == 0 && threadIdx.x == 0 && (a != 0 || mol_start[n_mols] != n_atoms))
+        atomicOr(&ctr->bad_species, 2);
     if (a < 0 || b < a || b > n_atoms) {
         if (threadIdx.x == 0) atomicOr(&ctr->bad_species, 2);
         return;
@@ -161,7 +163,8 @@ __global__ void k_stage_batch(int n_mols, int n_atoms, const int* __restrict__ m
     }
 }
 
-// Warp per atom: every j of the atom's molecule.
+// Warp per atom: every j of the atom's molecule (mol_start == nullptr: the
+// n atoms are one molecule).
 __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_start, NbrArgs a, Counters* ctr) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -170,9 +173,9 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
     float4 hi_i = a.hi[i], lo_i = a.lo[i];
     int m = __float_as_int(lo_i.w);
     int beg = 0, end = 0;
-    if (m >= 0 && m < n_mols) {
-        beg = mol_start[m];
-        end = mol_start[m + 1];
+    if (m >= 0 && m < n_mols) {   // mol_start == nullptr: one molecule [0, n)
+        beg = mol_start ? mol_start[m] : 0;
+        end = mol_start ? mol_start[m + 1] : n;
     }
     if (beg < 0 || end > n || beg > end || i < beg || i >= end) {
         // atom not covered by a valid molecule (bad device input, already flagged)

@@ -55,11 +55,14 @@ CASES = {
     "config4": lambda: gen.make_config(4),
     "box300": lambda: _small_periodic(300),     # 4 x 4 x 4 cells
     "box173": lambda: _small_periodic(173, 5),  # L = 12 A: two cells per axis
+    # open systems of more than 1,024 atoms take the cell list; smaller open
+    # systems (config0, config1) the all-pairs search of one molecule
+    "open1500": lambda: gen.random_molecule(1500, seed=31, density=0.1),
 }
 
 
 # ------------------------------------------------------------------ neighbors
-@pytest.mark.parametrize("case", ["config0", "config1", "config2", "config4", "box300", "box173"])
+@pytest.mark.parametrize("case", ["config0", "config1", "config2", "config4", "box300", "box173", "open1500"])
 def test_neighbor_sets(P, W, case):
     c = CASES[case]()
     s = P.System(W, c.species, c.coords, c.cell, precision="fp32")
@@ -127,7 +130,7 @@ def _check_fp32(E, F, E_ref, F_ref):
     assert np.abs(F - F_ref).max() <= F_MAX_FP32, np.abs(F - F_ref).max()
 
 
-@pytest.mark.parametrize("case", ["config0", "config1", "box300", "box173"])
+@pytest.mark.parametrize("case", ["config0", "config1", "box300", "box173", "open1500"])
 def test_energy_forces_fp32(P, W, OW, case):
     c = CASES[case]()
     E_ref, F_ref, e_ref = oracle.energy_forces(c.species, c.coords, c.cell, OW, per_atom=True)
