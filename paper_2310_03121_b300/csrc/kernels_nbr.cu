@@ -184,6 +184,24 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
     Box box{};
     int count = 0;
     int* row = a.nbr + (size_t)i * a.cap;
+    // r_ij < r_list from the hi parts alone unless r^2 falls within the
+    // bound of that shortcut's error of r_list^2; there the split-precision
+    // displacement decides, so the list is the one the exact test gives.
+    // Error of the hi-only displacement per axis <= 2^-23 (|x_i| + |x_j|)
+    // (the lo parts and one rounding), taken twice: tau = 2^-22 times the L1
+    // norms; |r^2 - r^2_exact| <= 2 |d| tau + tau^2 + roundings of the sums.
+    const float rl = sqrtf(a.rl2);
+    const float l1_i = fabsf(hi_i.x) + fabsf(hi_i.y) + fabsf(hi_i.z);
+    auto within = [&](const float4& hj, const float4& lj) -> bool {
+        const float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float tau = 2.384185791015625e-7f * (l1_i + fabsf(hj.x) + fabsf(hj.y) + fabsf(hj.z));
+        const float margin = fmaf(4.f * rl, tau, fmaf(2.f * tau, tau, 9.5367431640625e-7f * a.rl2));
+        if (r2 < a.rl2 - margin) return true;
+        if (r2 > a.rl2 + margin) return false;
+        const float3 d = displacement(hi_i, lo_i, hj, lj, box);
+        return d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+    };
     auto emit = [&](int j, bool ok) {
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         int pos = count + __popc(mask & lanemask_lt());
@@ -204,20 +222,8 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
             h1 = a.hi[j1];
             l1 = a.lo[j1];
         }
-        bool ok = false;
-        if (j0 < end && j0 != i) {
-            const float3 d = displacement(hi_i, lo_i, h0, l0, box);
-            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
-        }
-        emit(j0, ok);
-        if (base + 32 < end) {
-            ok = false;
-            if (j1 < end && j1 != i) {
-                const float3 d = displacement(hi_i, lo_i, h1, l1, box);
-                ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
-            }
-            emit(j1, ok);
-        }
+        emit(j0, j0 < end && j0 != i && within(h0, l0));
+        if (base + 32 < end) emit(j1, j1 < end && j1 != i && within(h1, l1));
     }
     if (lane == 0) {
         a.nbr_cnt[i] = count;
