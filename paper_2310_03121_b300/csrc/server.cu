@@ -184,7 +184,9 @@ struct SubmitQueue {
 struct Slot {
     Workspace ws;
     cudaStream_t stream = nullptr;
+    cudaStream_t io = nullptr;                  // gather / scatter, highest priority
     cudaEvent_t done = nullptr;
+    cudaEvent_t in_ready = nullptr, out_ready = nullptr;
     void* dev_block = nullptr;
     void* host_block = nullptr;
     int *d_mol_start = nullptr, *h_mol_start = nullptr;
@@ -258,11 +260,15 @@ namespace {
 
 void slot_destroy(Slot& s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.io) cudaStreamSynchronize(s.io);
     workspace_destroy(s.ws);
     dev_free(s.dev_block);
     if (s.host_block) cudaFreeHost(s.host_block);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.io) cudaStreamDestroy(s.io);
     if (s.done) cudaEventDestroy(s.done);
+    if (s.in_ready) cudaEventDestroy(s.in_ready);
+    if (s.out_ready) cudaEventDestroy(s.out_ready);
     s = Slot();
 }
 
@@ -279,8 +285,18 @@ int slot_create(Slot& s, const mlp_server_opts& o, int nets) {
     if ((e = cudaMallocHost(&s.host_block, host)) != cudaSuccess) return cuda_error(e, "cudaMallocHost(slot)");
     if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_error(e, "cudaStreamCreate");
-    if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess)
+    if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s.in_ready, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s.out_ready, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_error(e, "cudaEventCreate");
+    // The gather and scatter kernels read and write the requests' page-locked
+    // host blocks over PCIe: on a stream of the highest priority their blocks
+    // are scheduled ahead of the other slot's compute blocks, so the transfers
+    // overlap that batch's kernels instead of queueing behind them.
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if ((e = cudaStreamCreateWithPriority(&s.io, cudaStreamNonBlocking, hi_prio)) != cudaSuccess)
+        return cuda_error(e, "cudaStreamCreateWithPriority");
     char* d = static_cast<char*>(s.dev_block);
     char* h = static_cast<char*>(s.host_block);
     s.d_mol_start = reinterpret_cast<int*>(d);
@@ -320,10 +336,12 @@ int launch_slot(mlp_server* S, Slot& s) {
     }
     s.n_atoms = off;
     s.n_mols = (int)s.reqs.size();
-    cudaStream_t st = s.stream;
-    cudaMemcpyAsync(s.d_mol_start, s.h_mol_start, 4 * (size_t)(s.n_mols + 1), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s.d_refs, s.h_refs, sizeof(MolRef) * (size_t)s.n_mols, cudaMemcpyHostToDevice, st);
-    launch_gather_batch(st, s.n_mols, s.d_refs, s.d_mol_start, s.d_xyz, s.d_species);
+    cudaStream_t st = s.stream, io = s.io;
+    cudaMemcpyAsync(s.d_mol_start, s.h_mol_start, 4 * (size_t)(s.n_mols + 1), cudaMemcpyHostToDevice, io);
+    cudaMemcpyAsync(s.d_refs, s.h_refs, sizeof(MolRef) * (size_t)s.n_mols, cudaMemcpyHostToDevice, io);
+    launch_gather_batch(io, s.n_mols, s.d_refs, s.d_mol_start, s.d_xyz, s.d_species);
+    cudaEventRecord(s.in_ready, io);
+    cudaStreamWaitEvent(st, s.in_ready, 0);
     EvalSpec sp;
     sp.n_atoms = s.n_atoms;
     sp.n_mols = s.n_mols;
@@ -335,10 +353,12 @@ int launch_slot(mlp_server* S, Slot& s) {
     sp.d_F = s.d_F;
     int rc = enqueue_eval(s.ws, weights_of(S->w), sp, st);
     if (rc) return rc;
-    launch_scatter_results(st, s.n_mols, s.d_refs, s.d_mol_start, s.d_E, s.d_F);
+    cudaEventRecord(s.out_ready, st);
+    cudaStreamWaitEvent(io, s.out_ready, 0);
+    launch_scatter_results(io, s.n_mols, s.d_refs, s.d_mol_start, s.d_E, s.d_F);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "serving kernels");
-    e = cudaEventRecord(s.done, st);
+    e = cudaEventRecord(s.done, io);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
     return MLP_OK;
 }
@@ -436,6 +456,7 @@ void server_loop(mlp_server* S) {
                 int rc = launch_slot(S, *free_slot);
                 if (rc) {
                     cudaStreamSynchronize(free_slot->stream);
+                    cudaStreamSynchronize(free_slot->io);
                     finish_slot(S, *free_slot, rc);
                 }
                 idle = 0;
