@@ -125,7 +125,8 @@ bool launch_mlp_bf16(cudaStream_t st, int rows_cap, const Counters* ctr, const N
 
 // ---- serving batches (kernels_misc.cu): one molecule per request, its inputs
 // and result area in page-locked host memory that kernels address directly
-// (unified addressing), so that no host thread copies request data.
+// (unified addressing), so that no host thread copies request data. Every
+// array starts on a 16-byte boundary.
 struct MolRef {
     const double* xyz;     // [n][3]
     const int8_t* species; // [n]

@@ -87,19 +87,41 @@ __global__ void k_gather_subset(int n, const int* __restrict__ index, const doub
 // block (read / written through its unified address) and the batch arrays.
 __global__ void k_gather_batch(const MolRef* __restrict__ refs, const int* __restrict__ mol_start,
                                double* __restrict__ xyz, int8_t* __restrict__ species) {
+    // The request's arrays start on 16 bytes (host blocks): read over PCIe in
+    // 16-byte (coordinates) and 4-byte (elements) words, fewer transactions.
     const int m = blockIdx.x;
     const MolRef r = refs[m];
     const int a = mol_start[m], n = mol_start[m + 1] - a;
-    for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) xyz[3 * (size_t)a + q] = r.xyz[q];
-    for (int q = threadIdx.x; q < n; q += blockDim.x) species[a + q] = r.species[q];
+    double* dst = xyz + 3 * (size_t)a;
+    const double2* src2 = reinterpret_cast<const double2*>(r.xyz);
+    const int n3 = 3 * n;
+    for (int q = threadIdx.x; q < n3 / 2; q += blockDim.x) {
+        const double2 v = src2[q];
+        dst[2 * q] = v.x;
+        dst[2 * q + 1] = v.y;
+    }
+    if ((n3 & 1) && threadIdx.x == 0) dst[n3 - 1] = r.xyz[n3 - 1];
+    const uint32_t* s4 = reinterpret_cast<const uint32_t*>(r.species);
+    for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
+        const uint32_t w = s4[q];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) species[a + 4 * q + b] = (int8_t)(w >> (8 * b));
+    }
+    for (int q = 4 * (n / 4) + threadIdx.x; q < n; q += blockDim.x) species[a + q] = r.species[q];
 }
 
 __global__ void k_scatter_results(const MolRef* __restrict__ refs, const int* __restrict__ mol_start,
                                   const double* __restrict__ E, const float* __restrict__ F) {
+    // written to the request's host block (16-byte aligned) in 16-byte words
     const int m = blockIdx.x;
     const MolRef r = refs[m];
     const int a = mol_start[m], n = mol_start[m + 1] - a;
-    for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) r.F[q] = F[3 * (size_t)a + q];
+    const float* src = F + 3 * (size_t)a;
+    float4* dst4 = reinterpret_cast<float4*>(r.F);
+    const int n3 = 3 * n;
+    for (int q = threadIdx.x; q < n3 / 4; q += blockDim.x)
+        dst4[q] = make_float4(src[4 * q], src[4 * q + 1], src[4 * q + 2], src[4 * q + 3]);
+    for (int q = 4 * (n3 / 4) + threadIdx.x; q < n3; q += blockDim.x) r.F[q] = src[q];
     if (threadIdx.x == 0) *r.E = E[m];
 }
 

@@ -61,7 +61,10 @@ struct Request {
     int8_t* species() { return reinterpret_cast<int8_t*>(F() + 3 * ((size_t)1 << cls)); }
     static size_t bytes(int cls) { return sizeof(Request) + 37 * ((size_t)1 << cls); }
 };
-static_assert(sizeof(Request) % 8 == 0, "request header keeps the coordinates 8-byte aligned");
+// Blocks are carved on 256 bytes and hold at least 8 atoms, so with a header
+// of a multiple of 16 bytes every array of a block starts on 16 bytes (the
+// serving kernels move them in 16-byte words).
+static_assert(sizeof(Request) % 16 == 0, "request header keeps the block's arrays 16-byte aligned");
 
 // Request blocks live in page-locked host slabs (the serving kernels read a
 // request's inputs and write its results through their unified addresses,
