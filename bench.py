@@ -341,6 +341,7 @@ def run_ours(args):
     result["gpu_launches_timed_total"] = int(launches)
     terms = term_counts(stream)
     result["roofline"] = roofline(prof, n_atoms, args.profile_steps, prec, terms, args.nets)
+    result["kernels_roofline"] = kernels_roofline(prof, n_atoms, args.profile_steps, prec, terms, args.nets)
     result["kernels_ms_per_step"] = {k: v[0] / max(1, args.profile_steps) for k, v in sorted(prof.items())}
     result["kernels_timing"] = ("CUDA events around every launch, on the launching stream, in "
                                 f"{args.profile_steps} extra steps run on one stream after the timed steps")
@@ -475,11 +476,44 @@ def measured_traffic(name, atoms_per_launch, nets=1):
     return m["bytes_per_atom"] * atoms_per_launch
 
 
-def roofline(prof, n_atoms, steps, prec, terms, nets=1):
+# Algorithmic DRAM bytes per atom of the small kernels (HBM bound):
+# staging reads the FP64 coordinates and the element (25 B) and writes the
+# split positions (32 B), the rank (4 B) and zeroed FP64 gradients (24 B);
+# the neighbor search writes ~30 list entries (4 B each) and a count; the
+# finalize kernel reads the atom energy (4 B) and FP64 gradient (24 B) and
+# writes FP32 forces (12 B).
+HBM_BYTES_PER_ATOM = {"stage": 85, "neighbors_allpairs": 124, "neighbors_cell": 124, "finalize": 40}
+
+
+def kernels_roofline(prof, n_atoms, steps, prec, terms, nets=1):
+    """Every timed kernel against its own bound: tensor (network), FP32 ALU
+    (AEV, forces, FP32 network) or HBM (staging, neighbors, finalize)."""
+    out = {}
+    for name in prof:
+        r = roofline(prof, n_atoms, steps, prec, terms, nets, only=name)
+        if r is not None:
+            out[name] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac") if k in r}
+    return out
+
+
+def roofline(prof, n_atoms, steps, prec, terms, nets=1, only=None):
     peaks, src = measured_peaks()
     if not prof:
         return None
-    name, (tot_ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    if only is not None:
+        name, (tot_ms, cnt) = only, prof[only]
+        if name in HBM_BYTES_PER_ATOM:
+            avg_ms = tot_ms / max(1, cnt)
+            atoms_per_launch = n_atoms / max(1e-9, cnt / max(1, steps))
+            ach = HBM_BYTES_PER_ATOM[name] * atoms_per_launch / (avg_ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"]}
+        if not (name.startswith("mlp") or name in ("aev", "forces")):
+            return None
+        if name == "mlp_tc_b1_ens":
+            return None   # reported with mlp_tc as the ensemble's network pair
+    else:
+        name, (tot_ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_ms = tot_ms / max(1, cnt)
     launches_per_step = cnt / max(1, steps)
     atoms_per_launch = n_atoms / max(1e-9, launches_per_step)
