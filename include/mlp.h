@@ -405,6 +405,14 @@ MLP_API int mlp_debug_atom_energies(mlp_system *s, float *e, float *dEdG);
 MLP_API int mlp_debug_network(const mlp_weights *w, int precision, int32_t n, const int8_t *species, const float *G,
                       float *e, float *dEdG);
 
+/* Failure detection without a fault: one thread of a one-block kernel runs the
+ * tensor-core kernels' bounded wait on a barrier phase that nothing completes.
+ * The wait gives up after its limit (2 s), records the waiting warp and
+ * barrier, and the kernel returns; *timed_out = 1 and *code = that record
+ * (bit 30 set, warp in bits 20..25, barrier address below). The context
+ * stays usable. MLP_ECUDA if the launch fails. */
+MLP_API int mlp_debug_wait_timeout(int32_t *timed_out, int32_t *code);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,4 +11,5 @@ the binding raises ImportError (build it with
 """
 from ._lib import MLP_BF16, MLP_FP32, MLPError, load  # noqa: F401
 from .api import (Batch, Langevin, Server, System, Weights, debug_langevin_normals, debug_network,  # noqa: F401
-                  fail_next_allocation, launch_count, profile_enable, profile_read, profile_reset)
+                  debug_wait_timeout, fail_next_allocation, launch_count, profile_enable, profile_read,
+                  profile_reset)

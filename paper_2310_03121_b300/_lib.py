@@ -116,6 +116,7 @@ SIGNATURES = {
     "mlp_langevin_destroy": (None, [vp]),
     "mlp_langevin_run": (ip, [vp, vp, vp, i64, i32, vp, vp]),
     "mlp_debug_langevin_normals": (ip, [u64, i64, i32, dp]),
+    "mlp_debug_wait_timeout": (ip, [i32p, i32p]),
 }
 
 _lib = None

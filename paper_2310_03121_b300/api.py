@@ -238,6 +238,14 @@ def debug_langevin_normals(seed, step, n):
         ctypes.c_double))), "mlp_debug_langevin_normals")
     return out
 
+def debug_wait_timeout():
+    """(timed_out, code) of the network kernels' bounded barrier wait run on a
+    phase that never completes (mlp_debug_wait_timeout); takes ~2 s."""
+    t, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    check(load().mlp_debug_wait_timeout(ctypes.byref(t), ctypes.byref(c)), "mlp_debug_wait_timeout")
+    return int(t.value), int(c.value)
+
+
 class Batch:
     """Many small open-boundary molecules per launch sequence (mlp_batch_create)."""
 

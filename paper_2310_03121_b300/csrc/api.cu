@@ -864,4 +864,17 @@ int mlp_debug_network(const mlp_weights* w, int precision, int32_t n, const int8
     return MLP_OK;
 }
 
+int mlp_debug_wait_timeout(int32_t* timed_out, int32_t* code) {
+    clear_error();
+    if (!timed_out || !code) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    int t = 0, c = 0;
+    const int e = debug_wait_timeout(&t, &c);
+    if (e) return cuda_error((cudaError_t)e, "mlp_debug_wait_timeout");
+    *timed_out = t;
+    *code = c;
+    return MLP_OK;
+}
+
 }  // extern "C"

@@ -111,6 +111,9 @@ struct NetBF16 {
     bool maps_ok;
 };
 bool mlp_tc_available();
+// Runs the network kernels' bounded barrier wait on a phase that never
+// completes; returns a CUDA error code (0 on success).
+int debug_wait_timeout(int* timed_out, int* code);
 bool make_weight_maps(NetBF16& w);
 // split = true: forward GEMMs from hi/lo BF16 pairs of both operands (G_lo
 // required); false: single BF16 pass everywhere. Per-atom energies go to e

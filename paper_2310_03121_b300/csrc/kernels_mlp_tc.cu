@@ -1254,6 +1254,43 @@ extern "C" __attribute__((visibility("default"))) int mlp_tc_trace_read(unsigned
 }
 #endif
 
+namespace {
+// The network kernels' bounded wait on a barrier phase that never completes
+// (nothing arrives): returns false after the 2 s limit with the waiting warp
+// and barrier recorded, and the kernel exits normally (no copies or tensor
+// memory outstanding). out[0] = 1 if the wait timed out, out[1] = the code.
+__global__ void k_debug_wait_timeout(int* out) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int abrt;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        abrt = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait(b, 0u, &abrt);
+        out[0] = ok ? 0 : 1;
+        out[1] = abrt;
+    }
+}
+}  // namespace
+
+int debug_wait_timeout(int* timed_out, int* code) {
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+    if (e != cudaSuccess) return (int)e;
+    cudaMemset(d, 0, 2 * sizeof(int));
+    k_debug_wait_timeout<<<1, 32>>>(d);
+    int h[2] = {0, 0};
+    e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return (int)e;
+    *timed_out = h[0];
+    *code = h[1];
+    return 0;
+}
+
 // One map per weight matrix over all nets: rows of (net, element) block
 // k * 7 + s start at (k * 7 + s) * rows-per-block.
 bool make_weight_maps(NetBF16& w) {
