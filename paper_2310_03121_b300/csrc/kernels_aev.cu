@@ -133,8 +133,9 @@ constexpr int kPairRow = 34;
 
 // Forward scratch of one warp (after its angular stage).
 struct AevScratch {
-    float accR[2 * kRadLen];    // radial accumulators [element][half][shift]: the two 16-lane
-                                // halves of a warp use disjoint banks whatever their elements
+    float accR[4 * kRadLen];    // radial accumulators [element][quarter][shift]: a warp's
+                                // quarters (8 lanes, 2 shifts each) take one neighbor each;
+                                // the two quarters of a half-warp use disjoint banks
     // per pair q (one per lane): 2 fc fc P_z for the 8 sections (pfT[z][q])
     // and the 4 distance Gaussians (rfT[a][q]); rows of 34 floats, so that
     // the writing lanes (consecutive q) and the reading lanes (8 or 4 rows,
@@ -164,6 +165,7 @@ static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-war
 static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AEV row start on 16 bytes");
 static_assert(offsetof(AevScratch, pfT) % 8 == 0 && offsetof(AevScratch, rfT) % 8 == 0 && kPairRow % 2 == 0,
               "pair rows load two floats at a time");
+static_assert(offsetof(AevScratch, accR) % 8 == 0, "radial accumulators are read two at a time");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -332,26 +334,30 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
     const int* row = a.nbr + (size_t)i * a.cap;
     NbrLane nl0, nl1;
     const int cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
-    for (int c = lane; c < 2 * kRadLen; c += 32) X.accR[c] = 0.f;
+    for (int c = lane; c < 4 * kRadLen; c += 32) X.accR[c] = 0.f;
     __syncwarp();
 
-    const int k = lane & 15, h = lane >> 4;
-    const float Rk = c_aev.shf_r[k];
-    float* accR = X.accR + h * kRadShifts;
+    // radial: four neighbors per step, a quarter-warp each, shifts 2 k2 and 2 k2 + 1 per lane
+    const int k2 = 2 * (lane & 7), h = lane >> 3;
+    const float R0 = c_aev.shf_r[k2], R1 = c_aev.shf_r[k2 + 1];
+    float* accR = X.accR + h * kRadShifts + k2;
     int mA = 0;
     // radial terms straight from the lanes that loaded the neighbors
     auto chunk = [&](const NbrLane& nl, int base) {
         // fc(r) / 4: the radial prefactor folded into the shuffled cutoff value
         const float fcr = nl.inR ? fmaf(0.125f, M<FAST>::cpi(nl.r * (1.f / kRcRad)), 0.125f) : 0.f;
         const int nq = min(32, cnt - base);
-        for (int q = 0; q < nq; q += 2) {
+        for (int q = 0; q < nq; q += 4) {
             const int src = q + h;
             const float rr = __shfl_sync(kFull, nl.r, src);
             const int ss = __shfl_sync(kFull, nl.sp, src);
             const float ff = __shfl_sync(kFull, fcr, src);
             if (src < nq && ff > 0.f) {
-                const float dr = rr - Rk;
-                accR[ss * 2 * kRadShifts + k] += M<FAST>::gauss(kEtaRad, dr) * ff;
+                float2* acc2 = reinterpret_cast<float2*>(accR + ss * 4 * kRadShifts);
+                float2 v = *acc2;
+                v.x += M<FAST>::gauss(kEtaRad, rr - R0) * ff;
+                v.y += M<FAST>::gauss(kEtaRad, rr - R1) * ff;
+                *acc2 = v;
             }
         }
         mA = stage_angular<FAST>(nl, mA, s, a);
@@ -510,10 +516,11 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
         // the absent blocks after the last present one, and the row's padding
         zero_cols(out, out_lo, kRadLen + 32 * next_p, kAevLd, lane);
     }
-    // radial block (two halves)
+    // radial block (four quarters, added in a fixed order)
     for (int c = lane; c < kRadLen; c += 32) {
-        const int a = 2 * kRadShifts * (c >> 4) + (c & 15);
-        put_g(out, out_lo, c, X.accR[a] + X.accR[a + kRadShifts]);
+        const int a = 4 * kRadShifts * (c >> 4) + (c & 15);
+        put_g(out, out_lo, c,
+              (X.accR[a] + X.accR[a + kRadShifts]) + (X.accR[a + 2 * kRadShifts] + X.accR[a + 3 * kRadShifts]));
     }
     if (lane == 0) row_atom[rw] = i;
 }
