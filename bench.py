@@ -369,10 +369,10 @@ def run_ours(args):
         lat = None
         # result buffers kept across replays (written once here, so no page is first touched while timed)
         out = (np.ones(stream.count), np.ones((n_atoms, 3), dtype=np.float32))
-        # two warm-up replays, then the median of at least 5 (the host threads
+        # four warm-up replays, then the median of at least 9 (the host threads
         # share the machine's cores, so single replays can be slowed from outside)
-        warm = 2
-        for i in range(warm + max(5, min(args.steps, 9))):
+        warm = 4
+        for i in range(warm + max(9, min(args.steps, 15))):
             E, F, wall = srv.replay(arr, stream.mol_start, stream.species, stream.coords, out=out,
                                     clients=args.e2e_clients)
             lt = srv.latencies()
