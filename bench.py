@@ -453,12 +453,12 @@ def term_counts(stream):
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
     # launch (profiles/); valid only while the kernel source is the one that was captured
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
-               "bytes_per_atom": (559.401984e6 + 217.676544e6) / 131056},
-    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
-                 "bytes_per_atom": (360.886784e6 + 256.885760e6) / 65518},
-    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "cfa3fd193e45ed43021ed317994b096946db0d7d",
-                        "bytes_per_atom": (300.726528e6 + 109.793536e6) / 65518},
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
+               "bytes_per_atom": (559.759616e6 + 217.994496e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
+                 "bytes_per_atom": (360.897792e6 + 257.773824e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
+                        "bytes_per_atom": (300.706560e6 + 108.813568e6) / 65518},
 }
 
 
