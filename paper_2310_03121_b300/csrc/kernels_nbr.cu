@@ -138,10 +138,17 @@ __global__ void k_stage_batch(int n_mols, int n_atoms, const int* __restrict__ m
         if (threadIdx.x == 0) atomicOr(&ctr->bad_species, 2);
         return;
     }
+    // element ranks aggregated per block: one global atomic per element
+    // present in the block's chunk (a molecule's atoms) instead of one per
+    // element and warp
+    __shared__ int cnt[kNSpecies], off[kNSpecies];
     for (int base = a; base < b; base += blockDim.x) {
         int i = base + threadIdx.x;
         bool valid = i < b;
         int s = 0;
+        if (threadIdx.x < kNSpecies) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        int local = 0;
         if (valid) {
             float hx, hy, hz, lx, ly, lz;
             split(xyz[3 * (size_t)i], hx, lx);
@@ -157,9 +164,13 @@ __global__ void k_stage_batch(int n_mols, int n_atoms, const int* __restrict__ m
             grad[3 * (size_t)i] = 0.0;
             grad[3 * (size_t)i + 1] = 0.0;
             grad[3 * (size_t)i + 2] = 0.0;
+            local = atomicAdd(&cnt[s], 1);
         }
-        int r = element_rank(valid, s, ctr);
-        if (valid) rank[i] = r;
+        __syncthreads();
+        if (threadIdx.x < kNSpecies && cnt[threadIdx.x] > 0)
+            off[threadIdx.x] = atomicAdd(&ctr->species[threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+        if (valid) rank[i] = off[s] + local;
     }
 }
 
