@@ -486,14 +486,43 @@ def measured_traffic(name, atoms_per_launch, nets=1):
 HBM_BYTES_PER_ATOM = {"stage": 85, "neighbors_allpairs": 124, "neighbors_cell": 124, "finalize": 40}
 
 
+# The binding counters of the issue-bound kernels (fraction of cycles with an
+# instruction issued, MUFU and FMA pipe utilisation) from one ncu capture of
+# the BF16 path (profiles/k_aev_served_bf16.md, profiles/k_forces_served_bf16.md);
+# reported only while kernels_aev.cu is the source that was captured.
+MEASURED_ISSUE = {
+    "file": "kernels_aev.cu", "sha1": "61f1ad290efac218f609cf019303410747651e79",
+    "aev": {"issue_active": 0.824, "xu_pipe": 0.229, "fma_pipe": 0.297},
+    "forces": {"issue_active": 0.724, "xu_pipe": 0.144, "fma_pipe": 0.348},
+}
+
+
+def measured_issue(name):
+    m = MEASURED_ISSUE
+    if name not in m:
+        return None
+    path = os.path.join(ROOT, "paper_2310_03121_b300", "csrc", m["file"])
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != m["sha1"]:
+                return None
+    except OSError:
+        return None
+    return dict(m[name], source="ncu capture of this source, BF16 path")
+
+
 def kernels_roofline(prof, n_atoms, steps, prec, terms, nets=1):
     """Every timed kernel against its own bound: tensor (network), FP32 ALU
-    (AEV, forces, FP32 network) or HBM (staging, neighbors, finalize)."""
+    (AEV, forces, FP32 network) or HBM (staging, neighbors, finalize); the
+    AEV and force kernels are bound by instruction issue, whose counters
+    (from ncu) are added when they describe the current source."""
     out = {}
     for name in prof:
         r = roofline(prof, n_atoms, steps, prec, terms, nets, only=name)
         if r is not None:
             out[name] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac") if k in r}
+            if prec == "bf16" and measured_issue(name):
+                out[name]["ncu"] = measured_issue(name)
     return out
 
 
