@@ -203,13 +203,14 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
     // norms; |r^2 - r^2_exact| <= 2 |d| tau + tau^2 + roundings of the sums.
     const float rl = sqrtf(a.rl2);
     const float l1_i = fabsf(hi_i.x) + fabsf(hi_i.y) + fabsf(hi_i.z);
-    auto within = [&](const float4& hj, const float4& lj) -> bool {
+    auto within = [&](const float4& hj, int j) -> bool {
         const float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float tau = 2.384185791015625e-7f * (l1_i + fabsf(hj.x) + fabsf(hj.y) + fabsf(hj.z));
         const float margin = fmaf(4.f * rl, tau, fmaf(2.f * tau, tau, 9.5367431640625e-7f * a.rl2));
         if (r2 < a.rl2 - margin) return true;
         if (r2 > a.rl2 + margin) return false;
+        const float4 lj = a.lo[j];   // the lo parts only for the rare pairs near the list radius
         const float3 d = displacement(hi_i, lo_i, hj, lj, box);
         return d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
     };
@@ -224,17 +225,11 @@ __global__ void k_nbr_allpairs(int n, int n_mols, const int* __restrict__ mol_st
     for (int base = beg; base < end; base += 64) {
         const int j0 = base + lane, j1 = base + 32 + lane;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 h0 = z4, l0 = z4, h1 = z4, l1 = z4;
-        if (j0 < end) {
-            h0 = a.hi[j0];
-            l0 = a.lo[j0];
-        }
-        if (j1 < end) {
-            h1 = a.hi[j1];
-            l1 = a.lo[j1];
-        }
-        emit(j0, j0 < end && j0 != i && within(h0, l0));
-        if (base + 32 < end) emit(j1, j1 < end && j1 != i && within(h1, l1));
+        float4 h0 = z4, h1 = z4;
+        if (j0 < end) h0 = a.hi[j0];
+        if (j1 < end) h1 = a.hi[j1];
+        emit(j0, j0 < end && j0 != i && within(h0, j0));
+        if (base + 32 < end) emit(j1, j1 < end && j1 != i && within(h1, j1));
     }
     if (lane == 0) {
         a.nbr_cnt[i] = count;
