@@ -383,6 +383,29 @@ __global__ void k_nbr_cell(int n, NbrArgs a, Box box, const Grid* __restrict__ g
         }
     }
     const int cc[3] = {cx, cy, cz};
+    // r_ij < r_list from the hi parts alone (minimum image with the FP32 box)
+    // unless r^2 falls within that shortcut's error bound of r_list^2; there
+    // the split-precision displacement decides (as in k_nbr_allpairs; the
+    // image shift adds at most 2^-24 L per axis to the error)
+    const float rl = sqrtf(a.rl2);
+    const float l1_i = fabsf(hi_i.x) + fabsf(hi_i.y) + fabsf(hi_i.z) +
+                       (box.periodic ? box.Lhi[0] + box.Lhi[1] + box.Lhi[2] : 0.f);
+    auto within = [&](int j) -> bool {
+        const float4 hj = a.hi[j];
+        float dx = hj.x - hi_i.x, dy = hj.y - hi_i.y, dz = hj.z - hi_i.z;
+        if (box.periodic) {
+            dx -= rintf(dx * box.invL[0]) * box.Lhi[0];
+            dy -= rintf(dy * box.invL[1]) * box.Lhi[1];
+            dz -= rintf(dz * box.invL[2]) * box.Lhi[2];
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float tau = 2.384185791015625e-7f * (l1_i + fabsf(hj.x) + fabsf(hj.y) + fabsf(hj.z));
+        const float margin = fmaf(4.f * rl, tau, fmaf(2.f * tau, tau, 9.5367431640625e-7f * a.rl2));
+        if (r2 < a.rl2 - margin) return true;
+        if (r2 > a.rl2 + margin) return false;
+        const float3 d = displacement(hi_i, lo_i, hj, a.lo[j], box);
+        return d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
+    };
     for (int oz = lo3[2]; oz <= hi3[2]; ++oz) {
         int z = rel[2] ? cc[2] + oz : oz;
         if (rel[2]) {
@@ -409,10 +432,7 @@ __global__ void k_nbr_cell(int n, NbrArgs a, Box box, const Grid* __restrict__ g
                     int j = -1;
                     if (q < end) {
                         j = cell_atoms[q];
-                        if (j != i) {
-                            float3 d = displacement(hi_i, lo_i, a.hi[j], a.lo[j], box);
-                            ok = d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
-                        }
+                        ok = j != i && within(j);
                     }
                     unsigned mask = __ballot_sync(0xffffffffu, ok);
                     int pos = count + __popc(mask & lanemask_lt());
