@@ -454,12 +454,12 @@ def term_counts(stream):
 MEASURED_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture, per atom of the captured
     # launch (profiles/); valid only while the kernel source is the one that was captured
-    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
-               "bytes_per_atom": (559.759616e6 + 217.994496e6) / 131056},
-    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
-                 "bytes_per_atom": (360.897792e6 + 257.773824e6) / 65518},
-    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "a0f048607bdcb0f329143a906f4a86ca17a3f336",
-                        "bytes_per_atom": (300.706560e6 + 108.813568e6) / 65518},
+    "mlp_tc": {"file": "kernels_mlp_tc.cu", "sha1": "8071bda3bb789ca43fd0dbd4dc9490a34fe3d910",
+               "bytes_per_atom": (559.342592e6 + 217.979904e6) / 131056},
+    "mlp_tc@8": {"file": "kernels_mlp_tc.cu", "sha1": "8071bda3bb789ca43fd0dbd4dc9490a34fe3d910",
+                 "bytes_per_atom": (361.059584e6 + 258.157824e6) / 65518},
+    "mlp_tc_b1_ens@8": {"file": "kernels_mlp_tc.cu", "sha1": "8071bda3bb789ca43fd0dbd4dc9490a34fe3d910",
+                        "bytes_per_atom": (300.809216e6 + 108.260608e6) / 65518},
 }
 
 
