@@ -114,6 +114,8 @@ typedef struct {
  * gradients, so energies and forces are the means over the K nets (one AEV,
  * K network passes). Returns MLP_EINVAL on NULL arrays, a non-finite W1 entry
  * or n_nets out of range, MLP_ENOMEM, MLP_ECUDA. */
+/* Passage: section "OpenMM-ML" (ANI-2x: one net per element of H, C, N, O,
+ * S, F, Cl) and section "Performance of MLPs" (ensemble average). */
 MLP_API int mlp_weights_create(const mlp_weights_host *w, int n_nets, mlp_weights **out);
 MLP_API void mlp_weights_destroy(mlp_weights *w);
 
@@ -125,6 +127,8 @@ MLP_API void mlp_weights_destroy(mlp_weights *w);
  * length must be >= 2 (rc_rad + skin). precision = MLP_FP32, MLP_BF16 or
  * MLP_BF16_1PASS (see the precision enum). Device buffers
  * are sized for n atoms at creation. The weights must outlive the system. */
+/* Passage: section "Optimization Through NNPOps" (the neighbor list and the
+ * symmetry functions are built for the system's atoms, box and cutoffs). */
 MLP_API int mlp_create(const int8_t *species, const double *coords, int32_t n, const double *cell,
                const mlp_cutoffs *cut, const mlp_weights *w, int precision, mlp_system **out);
 MLP_API void mlp_destroy(mlp_system *s);
@@ -132,6 +136,8 @@ MLP_API void mlp_destroy(mlp_system *s);
 /* One evaluation from host memory: copies coords (host [n][3]; NULL = the
  * stored positions) to the device, evaluates, and copies the energy (host
  * scalar) and forces (host [n][3], may be NULL) back. Synchronous. */
+/* Passage: section "PyTorch Model Support" (positions in, potential energy
+ * out, forces as the negative energy gradient). */
 MLP_API int mlp_energy_forces(mlp_system *s, const double *coords, double *energy, float *forces);
 
 /* One evaluation from device memory, asynchronous on `stream`:
@@ -139,6 +145,7 @@ MLP_API int mlp_energy_forces(mlp_system *s, const double *coords, double *energ
  * NULL). Returns after enqueueing; the neighbor capacity check is read back
  * on the next call (or by mlp_sync), which then reports MLP_EOVERFLOW if a
  * list was truncated. */
+/* Passage: section "PyTorch Model Support", as mlp_energy_forces. */
 MLP_API int mlp_energy_forces_device(mlp_system *s, const double *d_coords, double *d_energy, float *d_forces,
                              void *stream);
 
@@ -217,6 +224,7 @@ MLP_API int mlp_debug_langevin_normals(uint64_t seed, int64_t step, int32_t n, d
 /* Forward only (autograd forward): d_energy = E(d_coords). keep_aev != 0
  * keeps the AEVs on the device for a following mlp_backward_device on the
  * same coordinates; otherwise the backward recomputes them. */
+/* Passage: section "PyTorch Model Support" (forces through backpropagation). */
 MLP_API int mlp_forward_device(mlp_system *s, const double *d_coords, double *d_energy, int keep_aev, void *stream);
 
 /* Backward (autograd backward): d_grad_coords[n][3] (FP32) =
@@ -234,6 +242,8 @@ MLP_API int mlp_sync(mlp_system *s);
 /* A batch engine for many independent open-boundary molecules of at most
  * max_atoms_per_mol atoms each (all-pairs neighbor search inside each
  * molecule), sized for max_atoms atoms and max_mols molecules in total. */
+/* Passage: section "PyTorch Model Support" (the same evaluation for many
+ * independent molecules at once). */
 MLP_API int mlp_batch_create(const mlp_weights *w, int precision, int32_t max_atoms, int32_t max_mols,
                      int32_t max_atoms_per_mol, mlp_batch **out);
 MLP_API void mlp_batch_destroy(mlp_batch *b);
@@ -281,12 +291,16 @@ MLP_API void mlp_server_opts_default(mlp_server_opts *opts);
  * batches, runs up to `streams` batches concurrently on the device, and
  * completes tickets. Device memory for all slots is reserved here, within
  * budget_bytes (MLP_ENOMEM if the slots do not fit). */
+/* Passage: none in the paper, which evaluates one system per simulation
+ * step; the serving loop runs the evaluation of section "PyTorch Model
+ * Support" for a stream of independent requests. */
 MLP_API int mlp_server_create(const mlp_weights *w, const mlp_server_opts *opts, mlp_server **out);
 MLP_API void mlp_server_destroy(mlp_server *s);
 
 /* Queues one open-boundary molecule (host species[n], coords[n][3], copied
  * before returning). Never blocks: MLP_EAGAIN when the queue is full,
  * MLP_EINVAL for n outside [1, max_atoms_per_mol] or bad input. */
+/* Passage: as mlp_server_create. */
 MLP_API int mlp_submit(mlp_server *s, int32_t n, const int8_t *species, const double *coords, mlp_ticket *out);
 
 /* Non-blocking: MLP_PENDING while in flight; MLP_OK once done, writing the
@@ -392,8 +406,26 @@ MLP_API void mlp_profile_reset(void);
  * capacity used by the device list (call with list = NULL to query it). */
 MLP_API int mlp_debug_neighbors(mlp_system *s, int32_t *counts, int32_t *list, int32_t cap);
 
-/* AEVs of the last evaluation in atom order, host FP32 G[n][1008]. */
+/* AEVs of the last evaluation in atom order, host FP32 G[n][1008]: the value
+ * the network consumes (FP32 path: the FP32 row; MLP_BF16: G_hi + G_lo;
+ * MLP_BF16_1PASS: G_hi). */
 MLP_API int mlp_debug_aev(mlp_system *s, float *G);
+
+/* The BF16 paths' stored AEV rows of the last evaluation in atom order, each
+ * BF16 value widened to FP32: G_hi[n][1008] and (MLP_BF16, may be NULL)
+ * G_lo[n][1008], the BF16 rounding of G - G_hi (zero for MLP_BF16_1PASS).
+ * MLP_EINVAL on an FP32-path system. */
+MLP_API int mlp_debug_aev_split(mlp_system *s, float *G_hi, float *G_lo);
+
+/* The force kernel alone (AEV backward, section "PyTorch Model Support"):
+ * forces[n][3] (host FP64, the kernel's FP64 sums, negated) for the caller's
+ * dEdG[n][1008] (host FP32, atom order), on the positions and neighbor list
+ * of the system's last evaluation, with the arithmetic of the system's
+ * precision (FP32 path: dE/dG read as FP32, library-accurate functions; BF16
+ * paths: dE/dG rounded to BF16 to nearest even, the fast hardware
+ * approximations). Overwrites the system's stored dE/dG and force sums; the
+ * next evaluation rebuilds its neighbor list. */
+MLP_API int mlp_debug_forces(mlp_system *s, const float *dEdG, double *forces);
 
 /* Per-atom energies e[n] (host FP32) and dE/dG[n][1008] (host FP32, may be
  * NULL) of the last evaluation that ran the network backward. */

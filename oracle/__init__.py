@@ -17,6 +17,8 @@ Parity status per function (what pins it, from tests/test_oracle.py):
   oracle_atom_energy ................ torch Linear+CELU chain, single-path network;
                                       ensemble: K copies of one net, net-by-net means
   oracle_energy_forces .............. central finite differences, zero net force/torque
+  oracle_forces_from_dEdG ........... central differences of g . G(r) for a random g; equality
+                                      with oracle_energy_forces for the network's own dE/dG
   oracle_forces_subset / local energy  equality with the full evaluation
   oracle_ml_region .................. invariance to the classical region, zero rows, finite differences
   oracle_philox4x64 ................. numpy.random.Philox (the same published generator)
@@ -83,6 +85,8 @@ def lib():
         L.oracle_energy.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), _dp]
         L.oracle_energy_forces.restype = ctypes.c_double
         L.oracle_energy_forces.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), _dp, _dp]
+        L.oracle_forces_from_dEdG.restype = None
+        L.oracle_forces_from_dEdG.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp]
         L.oracle_aev_grad.restype = None
         L.oracle_aev_grad.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(_Weights), _dp, _dp]
         L.oracle_forces_subset.restype = None
@@ -309,6 +313,19 @@ def aev_grad(species, coords, cell, w):
     c = _cell(cell)
     lib().oracle_aev_grad(n, _i(s), _d(x), None if c is None else _d(c), w.ref(), _d(e), _d(g))
     return e, g
+
+
+def forces_from_dEdG(species, coords, cell, dEdG):
+    """F[n, 3] = -sum_i dEdG[i] . dG_i/dr (the AEV backward for a given dE/dG)."""
+    x = _f64(coords)
+    s = _i32(species)
+    n = x.shape[0]
+    g = _f64(dEdG)
+    assert g.shape == (n, AEV_LEN)
+    F = np.zeros((n, 3))
+    c = _cell(cell)
+    lib().oracle_forces_from_dEdG(n, _i(s), _d(x), None if c is None else _d(c), _d(g), _d(F))
+    return F
 
 
 def forces_subset(species, coords, cell, w, idx):

@@ -422,6 +422,23 @@ double oracle_energy_forces(int n, const int *species, const double *xyz, const 
     return E;
 }
 
+/* Forces F[n][3] = -sum_i dEdG_i . dG_i/dr for a given dE/dG (dEdG[n][1008],
+ * row i belonging to atom i): the AEV backward alone, the chain rule below
+ * the network (section "PyTorch Model Support": forces by backpropagation).
+ * With dE/dG from the oracle's own network it equals the forces of
+ * oracle_energy_forces. */
+void oracle_forces_from_dEdG(int n, const int *species, const double *xyz, const double *cell,
+                             const double *dEdG, double *F)
+{
+    int *nb = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    double *grad = (double *)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
+    for (int i = 0; i < n; ++i)
+        aev_atom_backward(i, n, species, xyz, cell, dEdG + (size_t)AEV_LEN * i, nb, grad);
+    for (int c = 0; c < 3 * n; ++c) F[c] = -grad[c];
+    free(nb);
+    free(grad);
+}
+
 /* dE/dG for every atom: dEdG[n][1008], and e_atoms[n]. */
 void oracle_aev_grad(int n, const int *species, const double *xyz, const double *cell,
                      const oracle_weights *w, double *e_atoms, double *dEdG)

@@ -110,6 +110,8 @@ SIGNATURES = {
     "mlp_profile_reset": (None, []),
     "mlp_debug_neighbors": (ip, [vp, i32p, i32p, i32]),
     "mlp_debug_aev": (ip, [vp, fp]),
+    "mlp_debug_aev_split": (ip, [vp, fp, fp]),
+    "mlp_debug_forces": (ip, [vp, fp, dp]),
     "mlp_debug_atom_energies": (ip, [vp, fp, fp]),
     "mlp_debug_network": (ip, [vp, ip, i32, i8p, fp, fp, fp]),
     "mlp_langevin_create": (ip, [vp, ctypes.POINTER(LangevinParams), ctypes.POINTER(vp)]),

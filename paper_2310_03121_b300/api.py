@@ -174,6 +174,24 @@ class System:
         check(load().mlp_debug_aev(self.handle, _ptr(G, ctypes.c_float)), "mlp_debug_aev")
         return G
 
+    def debug_aev_split(self):
+        """(G_hi, G_lo) [n, 1008] float32: the BF16 rows of the last evaluation."""
+        hi = np.zeros((self.n, 1008), dtype=np.float32)
+        lo = np.zeros((self.n, 1008), dtype=np.float32)
+        check(load().mlp_debug_aev_split(self.handle, _ptr(hi, ctypes.c_float), _ptr(lo, ctypes.c_float)),
+              "mlp_debug_aev_split")
+        return hi, lo
+
+    def debug_forces(self, dEdG):
+        """The force kernel alone on the last evaluation's positions and
+        neighbors for a given dE/dG [n, 1008]: forces [n, 3] float64."""
+        g = np.ascontiguousarray(dEdG, dtype=np.float32)
+        assert g.shape == (self.n, 1008)
+        F = np.zeros((self.n, 3))
+        check(load().mlp_debug_forces(self.handle, _ptr(g, ctypes.c_float), _ptr(F, ctypes.c_double)),
+              "mlp_debug_forces")
+        return F
+
     def debug_atom_energies(self, grad=True):
         e = np.zeros(self.n, dtype=np.float32)
         g = np.zeros((self.n, 1008), dtype=np.float32) if grad else None

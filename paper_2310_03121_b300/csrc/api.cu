@@ -107,12 +107,15 @@ inline __nv_bfloat16 to_bf16(float f) { return __float2bfloat16_rn(f); }
 
 int sys_make_workspace(mlp_system* s, int nbr_cap) {
     // open systems: at most ~2 cells per atom plus slack
-    int max_cells = s->periodic ? make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin)).ncell
-                                : (s->n * 2 + 64);
+    // at most ~2 cells per atom plus slack (periodic boxes: never more cells
+    // than that either, however large the box)
+    const long long cell_cap = 2LL * s->n + 64;
+    int max_cells = s->periodic ? make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin), cell_cap).ncell
+                                : (int)cell_cap;
     int rc = workspace_create(s->ws, s->n, 1, s->precision, true, nbr_cap, max_cells, s->w->dw.n_nets);
     if (rc) return rc;
     if (s->periodic) {
-        Grid g = make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin));
+        Grid g = make_periodic_grid(s->L, (float)(s->cut.rc_rad + s->cut.skin), cell_cap);
         cudaError_t e = cudaMemcpy(s->ws.grid, &g, sizeof(Grid), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(grid)");
     }
@@ -760,13 +763,95 @@ int mlp_debug_aev(mlp_system* s, float* G) {
         cudaMemcpy(all.data(), s->ws.G32, 4 * all.size(), cudaMemcpyDeviceToHost);
         for (int i = 0; i < s->n; ++i) std::memcpy(G + (size_t)i * kAevLen, &all[(size_t)rows[i] * kAevLd], 4 * kAevLen);
     } else {
-        std::vector<__nv_bfloat16> all(R * kAevLd);
+        // the value the network consumes: G_hi + G_lo (split path) or G_hi
+        std::vector<__nv_bfloat16> all(R * kAevLd), lo;
         cudaMemcpy(all.data(), s->ws.G16, 2 * all.size(), cudaMemcpyDeviceToHost);
+        if (s->ws.G16lo) {
+            lo.resize(R * kAevLd);
+            cudaMemcpy(lo.data(), s->ws.G16lo, 2 * lo.size(), cudaMemcpyDeviceToHost);
+        }
         for (int i = 0; i < s->n; ++i)
-            for (int c = 0; c < kAevLen; ++c) G[(size_t)i * kAevLen + c] = __bfloat162float(all[(size_t)rows[i] * kAevLd + c]);
+            for (int c = 0; c < kAevLen; ++c) {
+                const size_t q = (size_t)rows[i] * kAevLd + c;
+                G[(size_t)i * kAevLen + c] = __bfloat162float(all[q]) + (lo.empty() ? 0.f : __bfloat162float(lo[q]));
+            }
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MLP_OK : cuda_error(e, "mlp_debug_aev");
+}
+
+int mlp_debug_aev_split(mlp_system* s, float* G_hi, float* G_lo) {
+    clear_error();
+    if (!s || !G_hi) return set_error(MLP_EINVAL, "NULL argument");
+    if (s->precision == MLP_FP32) return set_error(MLP_EINVAL, "the FP32 path stores no BF16 AEV rows");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    cudaStreamSynchronize(s->stream);
+    std::vector<int> rows;
+    rc = atom_rows(s, rows);
+    if (rc) return rc;
+    const size_t R = s->ws.rows_cap;
+    std::vector<__nv_bfloat16> hi(R * kAevLd), lo;
+    cudaMemcpy(hi.data(), s->ws.G16, 2 * hi.size(), cudaMemcpyDeviceToHost);
+    if (s->ws.G16lo) {
+        lo.resize(R * kAevLd);
+        cudaMemcpy(lo.data(), s->ws.G16lo, 2 * lo.size(), cudaMemcpyDeviceToHost);
+    }
+    for (int i = 0; i < s->n; ++i)
+        for (int c = 0; c < kAevLen; ++c) {
+            const size_t q = (size_t)rows[i] * kAevLd + c;
+            G_hi[(size_t)i * kAevLen + c] = __bfloat162float(hi[q]);
+            if (G_lo) G_lo[(size_t)i * kAevLen + c] = lo.empty() ? 0.f : __bfloat162float(lo[q]);
+        }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MLP_OK : cuda_error(e, "mlp_debug_aev_split");
+}
+
+int mlp_debug_forces(mlp_system* s, const float* dEdG, double* forces) {
+    clear_error();
+    if (!s || !dEdG || !forces) return set_error(MLP_EINVAL, "NULL argument");
+    int rc = sys_finish_pending(s);
+    if (rc) return rc;
+    cudaStreamSynchronize(s->stream);
+    std::vector<int> rows;
+    rc = atom_rows(s, rows);
+    if (rc) return rc;
+    Workspace& ws = s->ws;
+    const size_t R = ws.rows_cap;
+    const int n = s->n;
+    cudaError_t e;
+    if (ws.dG) {
+        std::vector<float> all(R * kAevLd, 0.f);
+        for (int i = 0; i < n; ++i) std::memcpy(&all[(size_t)rows[i] * kAevLd], dEdG + (size_t)i * kAevLen, 4 * kAevLen);
+        e = cudaMemcpy(ws.dG, all.data(), 4 * all.size(), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f));
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < kAevLen; ++c) all[(size_t)rows[i] * kAevLd + c] = to_bf16(dEdG[(size_t)i * kAevLen + c]);
+        e = cudaMemcpy(ws.dG16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(ws.grad, 0, sizeof(double) * 3 * (size_t)n);
+    if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces (inputs)");
+    AevArgs aa;
+    aa.n = n;
+    aa.hi = ws.hi;
+    aa.lo = ws.lo;
+    aa.nbr = ws.nbr;
+    aa.nbr_cnt = ws.nbr_cnt;
+    aa.cap = ws.nbr_cap;
+    aa.box = make_box(s->periodic, s->L);
+    aa.ctr = ws.ctr;
+    aa.rank = ws.rank;
+    launch_forces(s->stream, aa, ws.dG, ws.dG16, ws.grad, ws.precision != MLP_FP32);
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces");
+    std::vector<double> grad(3 * (size_t)n);
+    e = cudaMemcpy(grad.data(), ws.grad, sizeof(double) * grad.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces (copy)");
+    for (size_t q = 0; q < grad.size(); ++q) forces[q] = -grad[q];
+    s->nbr_valid = false;   // the next evaluation rebuilds everything it reads
+    s->kept = false;        // and a following backward recomputes its AEVs (the force sums were used here)
+    return MLP_OK;
 }
 
 int mlp_debug_atom_energies(mlp_system* s, float* e_out, float* dEdG) {

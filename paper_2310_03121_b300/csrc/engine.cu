@@ -6,6 +6,7 @@
 //   AEV backward (forces) -> finalize (FP64 energies, FP32 forces).
 // All device memory of an evaluation is reserved up front in a Workspace;
 // nothing is allocated per call.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -26,17 +27,34 @@ Box make_box(int periodic, const double* L) {
     return b;
 }
 
-Grid make_periodic_grid(const double* L, float r_list) {
-    Grid g{};
-    g.ncell = 1;
+Grid make_periodic_grid(const double* L, float r_list, long long max_cells) {
+    // Cells at least r_list wide: floor(L / r_list) per axis. The product is
+    // formed in 64 bits and, where it exceeds max_cells (a large box with a
+    // short cutoff), the largest axis loses cells until it fits: wider cells
+    // only add candidates to the search, never lose a neighbor.
+    long long nc[3];
     for (int a = 0; a < 3; ++a) {
-        int nc = (int)std::floor(L[a] / (double)r_list);
-        if (nc < 1) nc = 1;
-        g.nc[a] = nc;
-        g.origin[a] = 0.f;
-        g.inv_cs[a] = (float)(nc / L[a]);
-        g.ncell *= nc;
+        double f = std::floor(L[a] / (double)r_list);
+        nc[a] = f < 1.0 ? 1 : (f > 1048576.0 ? 1048576 : (long long)f);
     }
+    if (max_cells < 1) max_cells = 1;
+    auto prod = [&]() { return nc[0] * nc[1] * nc[2]; };
+    if (prod() > max_cells) {
+        const double scale = std::cbrt((double)prod() / (double)max_cells);
+        for (int a = 0; a < 3; ++a) nc[a] = std::max(1LL, (long long)std::floor((double)nc[a] / scale));
+    }
+    while (prod() > max_cells) {
+        int big = 0;
+        for (int a = 1; a < 3; ++a) if (nc[a] > nc[big]) big = a;
+        nc[big] -= 1;
+    }
+    Grid g{};
+    for (int a = 0; a < 3; ++a) {
+        g.nc[a] = (int)nc[a];
+        g.origin[a] = 0.f;
+        g.inv_cs[a] = (float)((double)nc[a] / L[a]);
+    }
+    g.ncell = (int)prod();
     return g;
 }
 

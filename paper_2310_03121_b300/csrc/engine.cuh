@@ -126,6 +126,9 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& spec, cudaS
 int check_counters(const Workspace& ws);
 
 Box make_box(int periodic, const double* L);
-Grid make_periodic_grid(const double* L, float r_list);
+// Cell grid of an orthorhombic periodic box for a search radius r_list: cells
+// at least r_list wide, at most max_cells of them (fewer, wider cells when
+// floor(L / r_list) per axis would give more).
+Grid make_periodic_grid(const double* L, float r_list, long long max_cells);
 
 }  // namespace mlp

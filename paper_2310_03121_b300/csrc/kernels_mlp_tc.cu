@@ -34,7 +34,8 @@
 // warps get up to 128 registers):
 //   warp 0       TMA producer (one lane): streams G and weight sub-chunks into
 //                shared-memory rings as soon as slots free up, running ahead
-//                across GEMMs, and prefetches the next tile's G into L2;
+//                across GEMMs (no L2 prefetch of the next tile's G: its
+//                requests held up the current tile's loads and stores);
 //   warp 1       MMA issuer (one lane): tcgen05.mma into tensor memory (512
 //                columns: two 256-column accumulator halves), tcgen05.commit
 //                to the ring-slot and accumulator barriers;

@@ -11,8 +11,9 @@
 // file-scope __device__ array of fixed size, reserved when the library is
 // loaded and held by every GPU that loads it until the process exits.
 //
-// Limits: at most kStaticMaxAtoms atoms and kStaticMaxCells cells; larger
-// inputs are rejected with MLP_EINVAL before any work is enqueued.
+// Limits: at most kStaticMaxAtoms atoms (more are rejected with MLP_EINVAL
+// before any work is enqueued) and kStaticMaxCells cells (a box or an open
+// system that would need more gets fewer, wider cells).
 //
 // The array is shared by every call in the process: each call clears the
 // parts that must start at zero (counters and cell counts) on its stream
@@ -148,8 +149,10 @@ extern "C" int mlp_neighbors_static(const double* d_coords, int32_t n, const dou
                 return set_error(MLP_EINVAL, "box length %g below 2 x cutoff", cell[a]);
             L[a] = cell[a];
         }
-        g = make_periodic_grid(L, (float)cutoff);
-        if (g.ncell > kStaticMaxCells)
+        // a box that would need more cells than the array holds gets fewer,
+        // wider cells (still exact)
+        g = make_periodic_grid(L, (float)cutoff, kStaticMaxCells);
+        if (g.ncell < 1 || g.ncell > kStaticMaxCells)
             return set_error(MLP_EINVAL, "box needs %d cells; the static array holds %d", g.ncell, kStaticMaxCells);
     }
     unsigned char* scratch = nullptr;

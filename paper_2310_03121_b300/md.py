@@ -35,8 +35,14 @@ MASSES = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
 
 
 def _min_pair_distance_ok(coords_t, cell, limit, lib):
-    """True if no pair is closer than `limit` (allocation-free neighbor search)."""
+    """True if no pair is closer than `limit` (allocation-free neighbor search
+    with a list of 4 entries per atom: the counts are the true counts even
+    where they exceed the list, which is all this check reads). Raises
+    MLPError when the search refuses the input (more atoms than its static
+    array holds), so that the guard is never skipped silently."""
     import torch
+
+    from ._lib import check
 
     n = coords_t.shape[0]
     counts = torch.zeros(n, dtype=torch.int32, device=coords_t.device)
@@ -46,8 +52,7 @@ def _min_pair_distance_ok(coords_t, cell, limit, lib):
                                   None if cl is None else cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                   float(limit), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(lst.data_ptr()),
                                   4, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    if rc != 0:
-        return True   # too large for the static search: skip the guard
+    check(rc, "mlp_neighbors_static (MD pair-distance guard)")
     return int(counts.max().item()) == 0
 
 

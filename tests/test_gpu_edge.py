@@ -107,3 +107,18 @@ def test_batch_with_extreme_molecule_sizes(P, W, OW, precision):
         assert (np.abs(E - E_ref) <= 1e-3 * np.abs(E_ref) + 1e-9).all()
         assert np.sqrt(np.mean((F - F_ref) ** 2)) <= 2e-2
     assert np.all(F[0] == 0.0) and np.all(F[-1] == 0.0)   # the lone atoms
+
+
+def test_huge_periodic_box(P, W, OW):
+    """Three copies of the 24-atom molecule far apart in a 1,300 A periodic
+    box: floor(1300 / 5.1)^3 cells would overflow a 32-bit count, so the grid
+    is capped (fewer, wider cells) and the result equals the oracle's."""
+    c = gen.make_config(0)
+    cell = np.array([1300.0, 1300.0, 1300.0])
+    sp = np.concatenate([c.species] * 3)
+    x = np.concatenate([c.coords + off for off in (300.0, 700.0, 1297.0)])   # the last copy straddles the boundary
+    E_ref, F_ref = oracle.energy_forces(sp, x, cell, OW)
+    s = P.System(W, sp, x, cell, precision="fp32")
+    E, F = s.energy_forces()
+    assert abs(E - E_ref) <= 1e-6 * abs(E_ref), (E, E_ref)
+    assert np.abs(F - F_ref).max() <= 1e-4

@@ -303,6 +303,54 @@ def test_forces_match_central_differences(W, n):
     assert np.abs(F[atoms] - f5).max() <= 1e-6 * scale
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_forces_from_dEdG_match_central_differences(periodic):
+    """The AEV backward alone: for a fixed random g (every column, positive
+    and negative), F = -d/dr sum_i g_i . G_i(r), by central differences of
+    the oracle's AEV (h = 1e-4 and 1e-5 A)."""
+    if periodic:
+        c = gen.random_molecule(40, seed=23, density=0.1, periodic=True)
+    else:
+        c = gen.random_molecule(12, seed=13, density=0.3)
+    g = np.random.default_rng(3).normal(size=(c.n, oracle.AEV_LEN))
+    F = oracle.forces_from_dEdG(c.species, c.coords, c.cell, g)
+
+    def phi(x):
+        return float((g * oracle.aev(c.species, x, c.cell)).sum())
+
+    atoms = [0, 1, c.n // 2, c.n - 1]
+    scale = np.abs(F).max()
+    fd = {}
+    for h in (1e-4, 1e-5):
+        out = np.zeros((len(atoms), 3))
+        for q, m in enumerate(atoms):
+            for a in range(3):
+                x = c.coords.copy()
+                x[m, a] += h
+                p = phi(x)
+                x[m, a] -= 2 * h
+                out[q, a] = -(p - phi(x)) / (2 * h)
+        fd[h] = out
+    assert np.abs(fd[1e-4] - fd[1e-5]).max() <= 1e-6 * scale
+    assert np.abs(F[atoms] - fd[1e-4]).max() <= 1e-6 * scale
+    if not periodic:
+        assert np.abs(F.sum(0)).max() <= 1e-10 * np.abs(F).sum()     # translation invariance of g . G
+
+
+def test_forces_from_dEdG_with_network_gradient_equal_forces(W):
+    """With dE/dG from the oracle's network, the AEV backward alone gives the
+    forces of the whole evaluation (same arithmetic, same order: equal)."""
+    for c in (gen.make_config(0), gen.random_molecule(60, seed=4, density=0.1, periodic=True)):
+        E, F = oracle.energy_forces(c.species, c.coords, c.cell, W)
+        e, g = oracle.aev_grad(c.species, c.coords, c.cell, W)
+        F2 = oracle.forces_from_dEdG(c.species, c.coords, c.cell, g)
+        assert np.array_equal(F, F2)
+        g2 = np.random.default_rng(1).normal(size=g.shape)       # and it is linear in dE/dG
+        Fa = oracle.forces_from_dEdG(c.species, c.coords, c.cell, 2.0 * g - 3.0 * g2)
+        Fb = 2.0 * F2 - 3.0 * oracle.forces_from_dEdG(c.species, c.coords, c.cell, g2)
+        assert np.abs(Fa - Fb).max() <= 1e-12 * np.abs(Fa).max()
+
+
 def test_ensemble_forces_match_central_differences():
     We = oracle.Weights(gen.make_weights(nets=3))
     c = gen.random_molecule(9, seed=5, density=0.3)
