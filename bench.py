@@ -17,7 +17,9 @@ e2e    the same stream through the C-ABI server (mlp_server_replay_clients
        median of three runs after a warm-up run; p50/p99 request latency.
 Also reported: Langevin dynamics at 2 fs (LF-Middle, graph-replayed steps)
 of the 72-atom ligand and the 672-atom ligand-in-water system in ns/day,
-one net and the 8-net ensemble; the same device-resident stream with an ensemble of
+one net and the 8-net ensemble; velocity-Verlet trajectories at 0.5 fs with
+a caller-side repulsive wall (10,000 steps of the 672-atom system: energy
+drift; 1,000 steps of the 21,080-atom box on its skin list: atom-steps/s); the same device-resident stream with an ensemble of
 --ensemble-nets nets (energy = mean of the nets, forces = mean gradient),
 Poisson-arrival latency sweep, the one-molecule-per-launch FP32 path, the
 roofline of the dominant kernel and the FP64 oracle on the host cores
@@ -405,7 +407,7 @@ def run_ours(args):
     # ---------------- Langevin dynamics (2 fs), graph-replayed steps
     if not args.no_md and rank == 0:
         result["langevin_md"] = langevin_md(P, args)
-        result["box_md"] = box_md(P, args)
+        result["vv_md"] = vv_md(P, args)
 
     # ---------------- every synthetic system at both precisions, one evaluation per call
     if not args.no_configs and rank == 0:
@@ -744,48 +746,39 @@ def per_system(P, args):
     return out
 
 
-def box_md(P, args):
-    """Langevin dynamics (LF-Middle) of the 21,080-atom periodic solvated box
-    at 0.5 fs with a 5.6 A list (0.5 A skin, rebuilt on the device when an
-    atom has moved half the skin), BF16 network: wall time per step over runs
-    of 100 graph-replayed steps, up to args.box_md_steps steps. Random-init
-    weights have no repulsive core, so the run stops at the first run that
-    reports an error (atoms collapsing past the neighbor capacity) and the
-    rate is over the completed runs."""
-    import torch
-
+def vv_md(P, args):
+    """Velocity-Verlet dynamics at 0.5 fs of the two workloads that ask for a
+    trajectory, with the caller's short-range repulsive wall (md.RepulsiveWall:
+    shifted r^-12 inside 1.0 A, the classical part a caller adds; random-init
+    weights have no repulsive core) added to the ML forces through the
+    accumulate path: the 672-atom ligand in water for args.vv_steps steps on
+    the FP32 path (total-energy drift per atom per ps), and the 21,080-atom
+    periodic box for args.box_md_steps steps on the BF16 path with its
+    persistent 5.6 A list (0.5 A skin, rebuilt every 10 steps or when an atom
+    moved half the skin): atom-steps/s. Host wall time of the whole run; the
+    host reads the energies every report interval."""
     import gen
+    from paper_2310_03121_b300 import md
 
-    c = gen.make_config(4)
     W = P.Weights(gen.make_weights())
-    masses = np.array([1.008, 12.011, 14.007, 15.999, 32.06, 18.998, 35.45])
-    m = masses[c.species][:, None]
-    v0 = np.random.default_rng(0).normal(size=c.coords.shape) * np.sqrt(8.617333262e-5 * 300.0 / (m * 103.6426965))
-    s = P.System(W, c.species, c.coords, c.cell, precision="bf16", skin=0.5)
-    L = P.Langevin(s, dt_fs=0.5, friction_per_ps=1.0, temperature_K=300.0, seed=1, use_graph=True)
-    x = torch.from_numpy(np.ascontiguousarray(c.coords)).cuda()
-    v = torch.from_numpy(np.ascontiguousarray(v0)).cuda()
-    per_run, done, walls, err = 100, 0, [], None
-    while done < args.box_md_steps:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        try:
-            L.run(x, v, done, per_run, energies=False)
-        except P.MLPError as e:
-            err = str(e)
-            break
-        walls.append(time.perf_counter() - t0)
-        done += per_run
-    L.close()
+    out = []
+    keys = ("atoms", "steps", "dt_fs", "wall_s", "atom_steps_per_s", "drift_eV_per_atom_per_ps",
+            "etot_rms_fluct_eV_per_atom", "temperature_K_last", "aborted", "repulsive_wall")
+    c = gen.make_config(1)
+    s = P.System(W, c.species, c.coords, None, precision="fp32")
+    res = md.run(s, c.species, c.coords, None, dt_fs=0.5, steps=args.vv_steps, report_every=20, guard_every=0,
+                 wall=md.RepulsiveWall(c.n))
     s.close()
+    out.append(dict({"system": "672-atom ligand in water (open), FP32 path"}, **{k: res[k] for k in keys}))
+    c = gen.make_config(4)
+    s = P.System(W, c.species, c.coords, c.cell, precision="bf16", skin=0.5)
+    res = md.run(s, c.species, c.coords, c.cell, dt_fs=0.5, steps=args.box_md_steps, report_every=50,
+                 guard_every=0, wall=md.RepulsiveWall(c.n, c.cell))
+    s.close()
+    out.append(dict({"system": "21,080-atom solvated box (periodic), BF16 path, 5.6 A skin list"},
+                    **{k: res[k] for k in keys}))
     W.close()
-    row = {"system": "21,080-atom solvated box (periodic), 0.5 fs, skin 0.5 A", "atoms": int(c.n),
-           "steps_completed": done, "stopped": err}
-    timed = walls[1:]                      # the first run captures the graph
-    if timed:
-        us = sum(timed) / (per_run * len(timed)) * 1e6
-        row.update({"us_per_step": us, "atom_steps_per_s": c.n / (us * 1e-6)})
-    return row
+    return out
 
 
 def main():
@@ -813,6 +806,7 @@ def main():
     ap.add_argument("--no-md", action="store_true", help="skip the Langevin dynamics timing")
     ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--box-md-steps", type=int, default=1000)
+    ap.add_argument("--vv-steps", type=int, default=10000, help="velocity-Verlet steps of the 672-atom system")
     ap.add_argument("--no-configs", action="store_true", help="skip the per-system timing")
     ap.add_argument("--config-reps", type=int, default=20)
     ap.add_argument("--ensemble-nets", type=int, default=8,

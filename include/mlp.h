@@ -128,7 +128,9 @@ MLP_API void mlp_weights_destroy(mlp_weights *w);
  * MLP_BF16_1PASS (see the precision enum). Device buffers
  * are sized for n atoms at creation. The weights must outlive the system. */
 /* Passage: section "Optimization Through NNPOps" (the neighbor list and the
- * symmetry functions are built for the system's atoms, box and cutoffs). */
+ * symmetry functions are built for the system's atoms, box and cutoffs).
+ * Neighbor rows hold 160 entries (256 with a skin); a host-path evaluation
+ * that finds more grows them to 256 and repeats itself. */
 MLP_API int mlp_create(const int8_t *species, const double *coords, int32_t n, const double *cell,
                const mlp_cutoffs *cut, const mlp_weights *w, int precision, mlp_system **out);
 MLP_API void mlp_destroy(mlp_system *s);

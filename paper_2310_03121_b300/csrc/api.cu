@@ -368,7 +368,10 @@ int mlp_create(const int8_t* species, const double* coords, int32_t n, const dou
     s->cut = *cut;
     s->w = w;
     s->precision = precision;
-    rc = sys_make_workspace(s, kDefaultNbrCap);
+    // a list with a skin reaches (rc + skin)^3 / rc^3 times as many neighbors
+    // and is kept for several steps while atoms move: rows of the largest
+    // capacity from the start (no regrowth in the middle of a trajectory)
+    rc = sys_make_workspace(s, cut->skin > 0.0 ? kMaxNbrCap : kDefaultNbrCap);
     if (rc) {
         mlp_destroy(s);
         return rc;
@@ -451,10 +454,10 @@ int mlp_energy_forces(mlp_system* s, const double* coords, double* energy, float
         if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
         s->pending = false;
         rc = check_counters(s->ws);
-        if (rc == MLP_EOVERFLOW && s->ws.h_ctr->nbr_overflow && s->ws.nbr_cap < 256 && attempt == 0) {
+        if (rc == MLP_EOVERFLOW && s->ws.h_ctr->nbr_overflow && s->ws.nbr_cap < kMaxNbrCap && attempt == 0) {
             // grow the neighbor rows once and redo the evaluation
             workspace_destroy(s->ws);
-            rc = sys_make_workspace(s, 256);
+            rc = sys_make_workspace(s, kMaxNbrCap);
             if (rc) return rc;
             continue;
         }
@@ -842,6 +845,8 @@ int mlp_debug_forces(mlp_system* s, const float* dEdG, double* forces) {
     aa.box = make_box(s->periodic, s->L);
     aa.ctr = ws.ctr;
     aa.rank = ws.rank;
+    aa.big_list = ws.ang_big_list;
+    aa.big_flag = ws.ang_big_flag;
     launch_forces(s->stream, aa, ws.dG, ws.dG16, ws.grad, ws.precision != MLP_FP32);
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces");

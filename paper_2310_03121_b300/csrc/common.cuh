@@ -32,7 +32,12 @@ constexpr float kEtaAng = 12.5f;
 constexpr float kZeta = 14.1f;
 constexpr float kCeluAlpha = 0.1f;
 
-constexpr int kMaxAng = 60;   // angular neighbors kept per atom (overflow flagged)
+// Angular neighbors (within 3.5 A) staged per atom by the AEV and force
+// kernels: up to kAngCap in the main launches; atoms with more are handed to
+// a second launch that stages up to kAngCapBig (more than any neighbor list
+// holds: rows have at most 256 entries).
+constexpr int kAngCap = 60;
+constexpr int kAngCapBig = 256;
 
 // Device constant tables, filled once per device by init_constants().
 struct AevConsts {
@@ -66,11 +71,12 @@ struct Grid {
 struct Counters {
     int species[8];        // atoms per element
     int nbr_overflow;      // largest neighbor count seen above capacity (0 = fine)
-    int ang_overflow;      // largest radial/angular count above the staging limits (0 = fine)
+    int ang_overflow;      // largest angular neighbor count above kAngCapBig (0 = fine)
     int bad_species;       // bad input: 1 element code outside [0, 7), 2 molecule offsets, 4 ML-region index
     int rebuild;           // 1 if this evaluation rebuilds the neighbor list
     int net_error;         // tensor-core network kernel gave up on a bounded wait (0 = fine; else a code)
-    int pad[3];
+    int ang_big;           // atoms with more than kAngCap angular neighbors (listed for the second launch)
+    int pad[2];
     // bounding box of an open system as order-preserving unsigned keys of
     // max(x) and max(-x), so that an all-zero reset is the identity
     unsigned bbox_max_key[3];

@@ -98,6 +98,8 @@ void plan_workspace(Plan& P, Workspace& ws) {
         P.add(&ws.dG16, R * kAevLd);
         if (ws.nets > 1) P.add(&ws.g1ens, R * (size_t)ws.nets * kH1);
     }
+    P.add(&ws.ang_big_list, n);
+    P.add(&ws.ang_big_flag, n);
     P.add(&ws.tc_err, 4);
     P.add(&ws.err_sticky, 4);
     if (ws.precision == 0) {
@@ -204,6 +206,8 @@ int enqueue_eval(Workspace& ws, const DevWeights& w, const EvalSpec& sp, cudaStr
     aa.box = make_box(batch ? 0 : sp.periodic, sp.L);
     aa.ctr = ws.ctr;
     aa.rank = ws.rank;
+    aa.big_list = ws.ang_big_list;
+    aa.big_flag = ws.ang_big_flag;
 
     if (!sp.reuse_aev) {
         ce = cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), st);
@@ -271,8 +275,8 @@ int check_counters(const Workspace& ws) {
         return set_error(-7, "neighbor list overflow: an atom has %d neighbors (capacity %d)", c.nbr_overflow,
                          ws.nbr_cap);
     if (c.ang_overflow)
-        return set_error(-7, "too many neighbors inside the AEV cutoffs (%d; limits 160 radial / %d angular)",
-                         c.ang_overflow, kMaxAng);
+        return set_error(-7, "too many neighbors inside the angular cutoff (%d; limit %d)", c.ang_overflow,
+                         kAngCapBig);
     if (c.net_error)
         return set_error(-5, "tensor-core network kernel gave up on a bounded wait (code %#x)", c.net_error);
     return 0;

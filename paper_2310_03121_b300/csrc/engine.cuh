@@ -34,6 +34,7 @@ void profile_reset();
 
 constexpr int kMaxNets = 8;
 constexpr int kDefaultNbrCap = 160;
+constexpr int kMaxNbrCap = 256;   // rows grow to this once; lists with a skin start here
 
 struct DevWeights {
     int n_nets = 1;
@@ -72,6 +73,8 @@ struct Workspace {
     Grid* grid = nullptr;
     int *cell_of_atom = nullptr, *cell_rank = nullptr, *cell_count = nullptr, *cell_start = nullptr,
         *cell_atoms = nullptr;
+    int* ang_big_list = nullptr;           // atoms with more than kAngCap angular neighbors
+    unsigned char* ang_big_flag = nullptr;  // per atom: 1 if listed there
     int* tc_err = nullptr;
     int* err_sticky = nullptr;   // error flags of all evaluations since the host last cleared them
     Counters* h_ctr = nullptr;   // pinned host copy of the counters of the last evaluation

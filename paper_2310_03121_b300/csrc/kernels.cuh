@@ -74,6 +74,11 @@ struct AevArgs {
     Box box;
     Counters* ctr;
     const int* rank;
+    // atoms with more than kAngCap angular neighbors: listed by the AEV's main
+    // launch (big_list[0 .. ctr->ang_big), big_flag[i] = 1) and done by its
+    // second launch; the force kernels read the same list and flags
+    int* big_list;
+    unsigned char* big_flag;
 };
 void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast);
 void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,

@@ -119,57 +119,77 @@ struct M<true> {    // hardware approximations with subnormals flushed (BF16-net
     static __device__ __forceinline__ float dv(float a, float b) { return a * rcp(b); }
 };
 
-// Angular sub-list of one atom (neighbors within 3.5 A).
+// Angular sub-list of one atom (neighbors within 3.5 A), CAP slots.
+template <int CAP>
 struct AngStage {
-    float4 u[kMaxAng];     // unit vector d / r, and r
-    float invr[kMaxAng];
-    float fc[kMaxAng];     // fc(r; 3.5)
-    float dfc[kMaxAng];    // d fc / dr
-    int sp[kMaxAng];       // element
-    int idx[kMaxAng];      // atom index
+    float4 u[CAP];     // unit vector d / r, and r
+    float invr[CAP];
+    float fc[CAP];     // fc(r; 3.5)
+    float dfc[CAP];    // d fc / dr
+    int sp[CAP];       // element
+    int idx[CAP];      // atom index
 };
 
-constexpr int kPairRow = 34;
+// Angular pairs are processed in super-chunks of kSC pairs: one pair per
+// lane computes its 8 section factors and 4 distance factors into rows of
+// kFacRow floats (the rows of different sections start on different banks:
+// 34 mod 32 = 2, and two consecutive pairs of a row load as one 8-byte word),
+// then lane (a, z) sums column 8 a + z of every element-pair block of the
+// super-chunk. 32 pairs per super-chunk (measured 4% faster than 64: the
+// smaller stage lets 32 instead of 26 one-warp blocks share an SM).
+constexpr int kSC = 32;
+constexpr int kFacRow = kSC + 2;
 
 // Forward scratch of one warp (after its angular stage).
+template <int CAP>
 struct AevScratch {
     float accR[4 * kRadLen];    // radial accumulators [element][quarter][shift]: a warp's
                                 // quarters (8 lanes, 2 shifts each) take one neighbor each;
                                 // the two quarters of a half-warp use disjoint banks
-    // per pair q (one per lane): 2 fc fc P_z for the 8 sections (pfT[z][q])
-    // and the 4 distance Gaussians (rfT[a][q]); rows of 34 floats, so that
-    // the writing lanes (consecutive q) and the reading lanes (8 or 4 rows,
-    // one address per row) hit distinct banks and two consecutive pairs of a
-    // row load as one 8-byte word
-    float pfT[kAngZ * kPairRow];
-    float rfT[kAngA * kPairRow];
-    int ord[64];                // sorted (by element) position -> stage slot
-    int off[kNPairs + 1];       // first pair of each element pair in pair order
-    int pdesc[kNPairs];         // element groups of the pair: g1 | c1 << 8 | g2 << 16 | c2 << 24
+    float pfT[kAngZ * kFacRow]; // 2 fc_j fc_k P_z of the super-chunk's pairs, section-major
+    float rfT[kAngA * kFacRow]; // the 4 distance Gaussians, shift-major
+    int ord[CAP];               // sorted (by element) position -> stage slot
+    int blk[3 * kNPairs];       // present element-pair blocks, compacted: first pair, descriptor, pair index
 };
 // per-warp regions start on 16-byte boundaries (the stage holds float4)
-constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
-constexpr size_t kAevSmemPerWarp = round16(sizeof(AngStage) + sizeof(AevScratch));
-static_assert(sizeof(AngStage) % 16 == 0, "AngStage must keep the per-warp regions 16-byte aligned");
-// dE/dG staged with the angular block in rows of 33 floats (one per element
-// pair) so that lanes reading the same column of different rows hit
-// different banks
-constexpr int kGsAngStride = 33;
-// the radial block in rows of 17 floats per element, so that lanes on
-// neighbors of different elements read different banks
-constexpr int kGsRadStride = 17;
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+template <int CAP>
+__host__ __device__ constexpr size_t aev_smem_per_warp() { return round16(sizeof(AngStage<CAP>) + sizeof(AevScratch<CAP>)); }
+static_assert(sizeof(AngStage<kAngCap>) % 16 == 0 && sizeof(AngStage<kAngCapBig>) % 16 == 0,
+              "AngStage must keep the per-warp regions 16-byte aligned");
+// dE/dG staged for the backward as FP32: the radial block in rows of 16
+// floats per element, the angular block in rows of 32 floats per element
+// pair, read as 16-byte groups of four columns. Group g of row q is stored
+// at group g ^ (q & 7) (angular) or g ^ (q & 3) (radial), so that lanes
+// reading the same group of rows of different element pairs (elements) hit
+// different banks without padding the rows.
+constexpr int kGsRadStride = 16;
+constexpr int kGsAngStride = 32;
 constexpr int kGsRad = kNSpecies * kGsRadStride;
 constexpr int kGsFloats = kGsRad + kNPairs * kGsAngStride;
-constexpr size_t kForceSmemPerWarp = round16(sizeof(AngStage) + (kGsFloats + 3 * kMaxAng) * sizeof(float));
-static_assert(kAevSmemPerWarp % 16 == 0 && kForceSmemPerWarp % 16 == 0, "per-warp shared regions must be 16-byte aligned");
+__device__ __forceinline__ int gs_rad(int s, int g) { return kGsRadStride * s + 4 * (g ^ (s & 3)); }
+__device__ __forceinline__ int gs_ang(int p, int g) { return kGsRad + kGsAngStride * p + 4 * (g ^ (p & 7)); }
+template <int CAP>
+__host__ __device__ constexpr size_t force_smem_per_warp() { return round16(sizeof(AngStage<CAP>) + (kGsFloats + 3 * CAP) * sizeof(float)); }
+static_assert(aev_smem_per_warp<kAngCap>() % 16 == 0 && force_smem_per_warp<kAngCap>() % 16 == 0 &&
+              force_smem_per_warp<kAngCapBig>() % 16 == 0, "per-warp shared regions must be 16-byte aligned");
 static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AEV row start on 16 bytes");
-static_assert(offsetof(AevScratch, pfT) % 8 == 0 && offsetof(AevScratch, rfT) % 8 == 0 && kPairRow % 2 == 0,
-              "pair rows load two floats at a time");
-static_assert(offsetof(AevScratch, accR) % 8 == 0, "radial accumulators are read two at a time");
+static_assert(offsetof(AevScratch<kAngCap>, pfT) % 8 == 0 && offsetof(AevScratch<kAngCap>, rfT) % 8 == 0 &&
+              kFacRow % 2 == 0, "factor rows load two floats at a time");
+static_assert(offsetof(AevScratch<kAngCap>, accR) % 8 == 0, "radial accumulators are read two at a time");
+static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsRadStride == 16 && kGsAngStride == 32,
+              "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row)");
+static_assert(2 * force_smem_per_warp<kAngCap>() + 1024 <= 233472 / 15,
+              "15 blocks of two force warps fit an SM (each block also reserves 1 KB)");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
     return m;
 }
 
@@ -241,16 +261,15 @@ __device__ __forceinline__ int load_neighbors2(const AevArgs& a, const int* row,
     return cnt;
 }
 
-// Appends this chunk's angular neighbors to the stage; returns the new count.
-// pA_out: this lane's slot in the stage (or -1: not an angular neighbor or
-// past the staging limit).
-template <bool FAST>
-__device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage& s, const AevArgs& a,
-                                             int* pA_out = nullptr) {
+// Appends this chunk's angular neighbors to the stage; returns the new count
+// (which may exceed CAP: only the first CAP are staged). pA_out: this lane's
+// slot in the stage (or -1: not an angular neighbor or past the stage).
+template <bool FAST, int CAP>
+__device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage<CAP>& s, int* pA_out = nullptr) {
     const unsigned bA = __ballot_sync(kFull, nl.inA);
     const int pA = mA + __popc(bA & lanemask_lt());
-    if (pA_out) *pA_out = (nl.inA && pA < kMaxAng) ? pA : -1;
-    if (nl.inA && pA < kMaxAng) {
+    if (pA_out) *pA_out = (nl.inA && pA < CAP) ? pA : -1;
+    if (nl.inA && pA < CAP) {
         const float ir = M<FAST>::rcp(nl.r);
         s.u[pA] = make_float4(nl.d.x * ir, nl.d.y * ir, nl.d.z * ir, nl.r);
         s.invr[pA] = ir;
@@ -259,9 +278,7 @@ __device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage
         s.sp[pA] = nl.sp;
         s.idx[pA] = nl.j;
     }
-    const int m = mA + __popc(bA);
-    if (m > kMaxAng && (threadIdx.x & 31) == 0) atomicMax(&a.ctr->ang_overflow, m);
-    return m;
+    return mA + __popc(bA);
 }
 
 // Unordered pairs of the m angular neighbors, enumerated by rotation: for
@@ -296,6 +313,22 @@ struct PairIt {
     }
 };
 
+// floor(l / c) for 0 <= l and 1 <= c. (l + 1/2) / c lies at least 1 / (2 c)
+// from an integer; the approximate reciprocal and the product (relative
+// error <= 2^-22 together) move it by at most l 2^-22 / c, which is below
+// 1 / (2 c) for l < 2^21 — exact without a check for the main kernels
+// (l < 60 * 59 / 2). The second launch stages up to 256 neighbors
+// (l < 2^15); one correction step there makes it exact as well.
+template <bool CHECK>
+__device__ __forceinline__ int small_div(int l, int c) {
+    int q = (int)(((float)l + 0.5f) * M<true>::rcp((float)c));
+    if (CHECK) {
+        if (q * c > l) --q;
+        else if ((q + 1) * c <= l) ++q;
+    }
+    return q;
+}
+
 // One AEV value into the output row: FP32, or BF16 and (with out_lo) the
 // BF16 rounding of the remainder (G = G_hi + G_lo to ~16 bits) for the
 // split-precision network.
@@ -321,15 +354,46 @@ __device__ __forceinline__ void zero_cols(OutT* out, OutT* out_lo, int c0, int c
     }
 }
 
-template <bool FAST, typename OutT>
-__global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
-                                                      int* __restrict__ row_atom) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kAevWarps + w;
-    if (i >= a.n) return;
-    AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kAevSmemPerWarp);
-    AevScratch& X = *reinterpret_cast<AevScratch*>(smem + w * kAevSmemPerWarp + sizeof(AngStage));
+// Orders the m staged neighbors by element: ord[sorted position] = stage
+// slot (stable within an element); lane e < 7 gets the size (cnt_e) and
+// first sorted position (g_e) of element e's group.
+template <int CAP>
+__device__ __forceinline__ void sort_by_element(const AngStage<CAP>& s, int m, int* ord, int lane, int& cnt_e,
+                                                int& g_e) {
+    constexpr int NCH = (CAP + 31) / 32;
+    int spv[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) spv[c] = c * 32 + lane < m ? s.sp[c * 32 + lane] : -1;
+    const unsigned lt = lanemask_lt();
+    int base = 0;
+    cnt_e = 0;
+    g_e = 0;
+    for (int e = 0; e < kNSpecies; ++e) {
+        int ce = 0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            if (c * 32 < m) {   // warp-uniform
+                const unsigned b = __ballot_sync(kFull, spv[c] == e);
+                if (spv[c] == e) ord[base + ce + __popc(b & lt)] = c * 32 + lane;
+                ce += __popc(b);
+            }
+        }
+        if (lane == e) {
+            cnt_e = ce;
+            g_e = base;
+        }
+        base += ce;
+    }
+}
+
+// AEV row of atom i. Returns false (nothing written) when the atom has more
+// than CAP angular neighbors.
+template <bool FAST, typename OutT, int CAP>
+__device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
+                                         int* __restrict__ row_atom, int i, unsigned char* wsmem) {
+    const int lane = threadIdx.x & 31;
+    AngStage<CAP>& s = *reinterpret_cast<AngStage<CAP>*>(wsmem);
+    AevScratch<CAP>& X = *reinterpret_cast<AevScratch<CAP>*>(wsmem + sizeof(AngStage<CAP>));
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
     const int* row = a.nbr + (size_t)i * a.cap;
     NbrLane nl0, nl1;
@@ -360,42 +424,28 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
                 *acc2 = v;
             }
         }
-        mA = stage_angular<FAST>(nl, mA, s, a);
+        mA = stage_angular<FAST, CAP>(nl, mA, s);
     };
     if (cnt > 0) chunk(nl0, 0);
     if (cnt > 32) chunk(nl1, 32);
     for (int base = 64; base < cnt; base += 32) chunk(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i), base);
-    if (mA > kMaxAng) mA = 0;   // reported as an error by the host; keep every index in range
+    if (mA > CAP) return false;   // warp-uniform
     __syncwarp();
     const int si = species_of(hi_i);
     const int rw = row_base(a.ctr->species, si) + a.rank[i];
     OutT* out = G + (size_t)rw * kAevLd;
     OutT* out_lo = G_lo ? G_lo + (size_t)rw * kAevLd : nullptr;
 
-    // ---- angular. The sub-list is ordered by element (ord), and the pairs
-    // are enumerated element pair by element pair (p = 0 .. 27), so that a
-    // lane (a, z) sums its column of one 32-column block in a register over
-    // a run of pairs and writes the finished block once; no accumulator
-    // array, fixed order (deterministic).
-    const int sp0 = lane < mA ? s.sp[lane] : -1, sp1 = lane + 32 < mA ? s.sp[lane + 32] : -1;
-    int cnt_e = 0, g_e = 0;   // lane e < 7: size and first sorted position of element e's group
+    // ---- angular. The sub-list is ordered by element (ord); the pairs are
+    // enumerated element pair by element pair (the present blocks p, in
+    // order), so that lane (a, z) sums its column of one 32-column block in a
+    // register over the block's pairs and writes the block once: no
+    // accumulator array, fixed order (deterministic).
+    int cnt_e, g_e;   // lane e < 7: size and first sorted position of element e's group
+    sort_by_element<CAP>(s, mA, X.ord, lane, cnt_e, g_e);
+    int my_off, my_end, my_desc, my_p, np, P;
     {
-        const unsigned lt = lanemask_lt();
-        int base = 0;
-        for (int e = 0; e < kNSpecies; ++e) {
-            const unsigned b0 = __ballot_sync(kFull, sp0 == e), b1 = __ballot_sync(kFull, sp1 == e);
-            const int c0 = __popc(b0), c = c0 + __popc(b1);
-            if (sp0 == e) X.ord[base + __popc(b0 & lt)] = lane;
-            if (sp1 == e) X.ord[base + c0 + __popc(b1 & lt)] = lane + 32;
-            if (lane == e) {
-                cnt_e = c;
-                g_e = base;
-            }
-            base += c;
-        }
-    }
-    {
-        // lane p < 28: element pair (s1 <= s2) in pair_index order, its pair count and first pair
+        // lane p < 28: element pair (s1 <= s2) in pair_index order and its pair count
         int s1 = 0, s2 = 0, l = lane;
         for (int e = 0; e < kNSpecies; ++e) {
             const int len = kNSpecies - e;
@@ -414,89 +464,89 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
             const int t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
         }
-        if (lane < kNPairs) {
-            X.off[lane] = incl - n;
-            X.pdesc[lane] = g1 | (c1 << 8) | (g2 << 16) | (c2 << 24);
+        P = __shfl_sync(kFull, incl, kNPairs - 1);
+        // compact the present blocks: block q of np holds first pair, descriptor
+        // (group starts g1, g2 and the divisor of its pair decoding: c2 for two
+        // groups, c1 for one), element pair index
+        const unsigned present = __ballot_sync(kFull, n > 0);
+        np = __popc(present);
+        if (n > 0) {
+            const int q = __popc(present & lanemask_lt());
+            X.blk[q] = incl - n;
+            X.blk[kNPairs + q] = g1 | (g2 << 8) | ((s1 < s2 ? c2 : c1) << 16);
+            X.blk[2 * kNPairs + q] = lane;
         }
-        if (lane == kNPairs - 1) X.off[kNPairs] = incl;
+        __syncwarp();
+        my_off = lane < np ? X.blk[lane] : P;
+        my_desc = lane < np ? X.blk[kNPairs + lane] : 0;
+        my_p = lane < np ? X.blk[2 * kNPairs + lane] : kNPairs;
+        my_end = __shfl_down_sync(kFull, my_off, 1);
+        if (lane == 31) my_end = P;
     }
-    __syncwarp();
     {
-        const int P = X.off[kNPairs];
         const int z = lane & 7, aa = lane >> 3;
+        const float* pz = X.pfT + z * kFacRow;
+        const float* ra = X.rfT + aa * kFacRow;
         float acc = 0.f;
-        int cur_p = -1, next_p = 0, p = 0;
-        auto flush = [&]() {
-            if (cur_p < 0) return;
-            if (next_p < cur_p) zero_cols(out, out_lo, kRadLen + 32 * next_p, kRadLen + 32 * cur_p, lane);
-            put_g(out, out_lo, kRadLen + 32 * cur_p + lane, acc);
-            next_p = cur_p + 1;
-        };
-        for (int base = 0; base < P; base += 32) {
-            const int e = base + lane;
-            const int nv = min(32, P - base);
-            int myp = kNPairs;
-            if (e < P) {
-                while (e >= X.off[p + 1]) ++p;
-                myp = p;
-                const int l = e - X.off[p];
-                const int dsc = X.pdesc[p];
-                const int g1 = dsc & 255, c1 = (dsc >> 8) & 255, g2 = (dsc >> 16) & 255, c2 = (dsc >> 24) & 255;
-                int jj, kk;
-                if (g1 != g2) {   // two groups: l = ja * c2 + kb
-                    // (l + 1/2) / c2 lies at least 1 / (2 c2) from an integer, far beyond
-                    // the approximate reciprocal's error; the two checks keep it exact anyway
-                    int ja = (int)(((float)l + 0.5f) * M<true>::rcp((float)c2));
-                    if (ja * c2 > l) --ja;
-                    if ((ja + 1) * c2 <= l) ++ja;
-                    jj = g1 + ja;
-                    kk = g2 + (l - ja * c2);
-                } else {          // one group of c1: row-major pairs (ja < kb), row ja starts at ja (2 c1 - ja - 1) / 2
-                    const int t = 2 * c1 - 1;
-                    int ja = (int)(0.5f * ((float)t - M<true>::sq((float)(t * t - 8 * l))));
-                    ja = max(0, min(ja, c1 - 2));
-                    while (ja > 0 && ja * (t - ja) / 2 > l) --ja;
-                    while ((ja + 1) * (t - ja - 1) / 2 <= l) ++ja;
-                    jj = g1 + ja;
-                    kk = g1 + (l - ja * (t - ja) / 2) + ja + 1;
-                }
-                const int J = X.ord[jj], K = X.ord[kk];
-                const float4 uj = s.u[J], uk = s.u[K];
-                const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
-                const float sn = M<FAST>::sq(1.f - c * c);
-                const float f2 = 2.f * s.fc[J] * s.fc[K];
-                // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
-                const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
+        int bi = 0, next_p = 0;
+        for (int sb = 0; sb < P; sb += kSC) {
+            const int se = min(P, sb + kSC);
+            for (int base = sb; base < se; base += 32) {
+                // block of pair e = base + lane: blocks starting before base, plus
+                // those starting inside this chunk at or before the lane
+                const unsigned before = __ballot_sync(kFull, my_off < base);
+                const unsigned starts = __reduce_or_sync(
+                    kFull, (lane < np && my_off >= base && my_off < base + 32) ? (1u << (my_off - base)) : 0u);
+                const int b = max(0, __popc(before) - 1 + __popc(starts & lanemask_le()));
+                const int off_b = __shfl_sync(kFull, my_off, b);
+                const int dsc = __shfl_sync(kFull, my_desc, b);
+                const int e = base + lane;
+                if (e < se) {
+                    const int l = e - off_b;
+                    const int g1 = dsc & 255, g2 = (dsc >> 8) & 255, cdiv = dsc >> 16;
+                    const int q = small_div<(CAP > 64)>(l, cdiv);
+                    const int r = l - q * cdiv;
+                    int jj, kk;
+                    if (g1 != g2) {   // two groups: pair (q, r) of the rectangle
+                        jj = g1 + q;
+                        kk = g2 + r;
+                    } else {          // one group of cdiv: rotation q + 1, position r
+                        const int x = r + q + 1;
+                        jj = g1 + r;
+                        kk = g1 + (x >= cdiv ? x - cdiv : x);
+                    }
+                    const int J = X.ord[jj], K = X.ord[kk];
+                    const float4 uj = s.u[J], uk = s.u[K];
+                    const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
+                    const float sn = M<FAST>::sq(1.f - c * c);
+                    const float f2 = 2.f * s.fc[J] * s.fc[K];
+                    // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
+                    const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
+                    const int col = e - sb;
+                    // sections z and 7 - z share sin: theta_(7-z) = pi - theta_z
 #pragma unroll
-                for (int zz = 0; zz < kAngZ; ++zz) {
-                    const float b = fmaf(c, c_aev.hcos_z[zz], fmaf(sn, c_aev.hsin_z[zz], 0.5f));
-                    X.pfT[zz * kPairRow + lane] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b), lf2))
-                                               : f2 * M<false>::pw(b, kZeta);
-                }
-                const float rbar = 0.5f * (uj.w + uk.w);
+                    for (int zz = 0; zz < kAngZ / 2; ++zz) {
+                        const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f);
+                        const float b0 = fmaf(c, c_aev.hcos_z[zz], y);
+                        const float b1 = fmaf(-c, c_aev.hcos_z[zz], y);
+                        X.pfT[zz * kFacRow + col] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b0), lf2))
+                                                         : f2 * M<false>::pw(b0, kZeta);
+                        X.pfT[(kAngZ - 1 - zz) * kFacRow + col] =
+                            FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b1), lf2)) : f2 * M<false>::pw(b1, kZeta);
+                    }
+                    const float rbar = 0.5f * (uj.w + uk.w);
 #pragma unroll
-                for (int q = 0; q < kAngA; ++q) {
-                    const float dr = rbar - c_aev.shf_a[q];
-                    X.rfT[q * kPairRow + lane] = M<FAST>::gauss(kEtaAng, dr);
+                    for (int q4 = 0; q4 < kAngA; ++q4)
+                        X.rfT[q4 * kFacRow + col] = M<FAST>::gauss(kEtaAng, rbar - c_aev.shf_a[q4]);
                 }
             }
-            const int prevp = __shfl_up_sync(kFull, myp, 1);
-            unsigned heads = __ballot_sync(kFull, e < P && (lane == 0 || prevp != myp));
             __syncwarp();
-            while (heads) {   // runs of one element pair inside these 32 pairs
-                const int q0 = __ffs(heads) - 1;
-                heads &= heads - 1;
-                const int q1 = heads ? __ffs(heads) - 1 : nv;
-                const int pq = __shfl_sync(kFull, myp, q0);
-                if (pq != cur_p) {
-                    flush();
-                    cur_p = pq;
-                    acc = 0.f;
-                }
-                // the run's pairs in order, two per 8-byte load where aligned
-                const float* pz = X.pfT + z * kPairRow;
-                const float* ra = X.rfT + aa * kPairRow;
-                int q = q0;
+            // the blocks of this super-chunk, in order; the last one may continue
+            // into the next super-chunk (its sum stays in acc)
+            while (bi < np) {
+                const int b0 = __shfl_sync(kFull, my_off, bi), b1 = __shfl_sync(kFull, my_end, bi);
+                int q = max(b0, sb) - sb;
+                const int q1 = min(b1, se) - sb;
                 if (q & 1) {
                     acc = fmaf(pz[q], ra[q], acc);
                     ++q;
@@ -509,32 +559,80 @@ __global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restr
                     acc = fmaf(p2.y, r2.y, acc);
                 }
                 if (q < q1) acc = fmaf(pz[q], ra[q], acc);
+                if (b1 > se) break;
+                const int p = __shfl_sync(kFull, my_p, bi);
+                if (next_p < p) zero_cols(out, out_lo, kRadLen + 32 * next_p, kRadLen + 32 * p, lane);
+                put_g(out, out_lo, kRadLen + 32 * p + lane, acc);
+                next_p = p + 1;
+                acc = 0.f;
+                ++bi;
             }
-            __syncwarp();
+            __syncwarp();   // the next super-chunk overwrites the factors
         }
-        flush();
         // the absent blocks after the last present one, and the row's padding
         zero_cols(out, out_lo, kRadLen + 32 * next_p, kAevLd, lane);
     }
     // radial block (four quarters, added in a fixed order)
     for (int c = lane; c < kRadLen; c += 32) {
-        const int a = 4 * kRadShifts * (c >> 4) + (c & 15);
+        const int ra4 = 4 * kRadShifts * (c >> 4) + (c & 15);
         put_g(out, out_lo, c,
-              (X.accR[a] + X.accR[a + kRadShifts]) + (X.accR[a + 2 * kRadShifts] + X.accR[a + 3 * kRadShifts]));
+              (X.accR[ra4] + X.accR[ra4 + kRadShifts]) + (X.accR[ra4 + 2 * kRadShifts] + X.accR[ra4 + 3 * kRadShifts]));
     }
     if (lane == 0) row_atom[rw] = i;
+    return true;
+}
+
+// Main AEV launch: one warp per atom, kAngCap staged angular neighbors; an
+// atom with more is listed for k_aev_big (its flag is set, nothing written).
+template <bool FAST, typename OutT>
+__global__ void __launch_bounds__(kAevWarps * 32) k_aev(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
+                                                      int* __restrict__ row_atom) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kAevWarps + w;
+    if (i >= a.n) return;
+    const bool done = aev_atom<FAST, OutT, kAngCap>(a, G, G_lo, row_atom, i, smem + w * aev_smem_per_warp<kAngCap>());
+    if (lane == 0) {
+        a.big_flag[i] = done ? 0 : 1;
+        if (!done) a.big_list[atomicAdd(&a.ctr->ang_big, 1)] = i;
+    }
+}
+
+// Second AEV launch: the listed atoms (usually none), kAngCapBig staged
+// angular neighbors, one warp per atom, a fixed grid striding over the list.
+template <bool FAST, typename OutT>
+__global__ void __launch_bounds__(32) k_aev_big(AevArgs a, OutT* __restrict__ G, OutT* __restrict__ G_lo,
+                                              int* __restrict__ row_atom) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = a.ctr->ang_big;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const int i = a.big_list[t];
+        if (!aev_atom<FAST, OutT, kAngCapBig>(a, G, G_lo, row_atom, i, smem) && (threadIdx.x & 31) == 0)
+            atomicMax(&a.ctr->ang_overflow, kAngCapBig + 1);
+        __syncwarp();
+    }
 }
 
 // d/dr of sum_k g_k 0.25 exp(-eta (r - R_k)^2) fc(r): the radial part of the
-// backward for one neighbor (g = the 16 dE/dG entries of its element).
+// backward for one neighbor (the 16 dE/dG entries of its element sp, staged
+// in shared memory).
 template <bool FAST>
-__device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, float dfc) {
+__device__ __forceinline__ float radial_dEdr(const float* gs, int sp, float r, float fc, float dfc) {
+    float gv[kRadShifts];
+#pragma unroll
+    for (int q = 0; q < kRadShifts / 4; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(gs + gs_rad(sp, q));
+        gv[4 * q] = v.x;
+        gv[4 * q + 1] = v.y;
+        gv[4 * q + 2] = v.z;
+        gv[4 * q + 3] = v.w;
+    }
     float s = 0.f;
     if constexpr (!FAST) {
 #pragma unroll
         for (int k = 0; k < kRadShifts; ++k) {
             const float dk = r - c_aev.shf_r[k];
-            s += g[k] * M<false>::ex(-kEtaRad * dk * dk) * (-2.f * kEtaRad * dk * fc + dfc);
+            s += gv[k] * M<false>::ex(-kEtaRad * dk * dk) * (-2.f * kEtaRad * dk * fc + dfc);
         }
     } else {
         // fast path: the 16 Gaussians as hardware exponentials, fully unrolled
@@ -544,7 +642,7 @@ __device__ __forceinline__ float radial_dEdr(const float* g, float r, float fc, 
 #pragma unroll
         for (int k = 0; k < kRadShifts; ++k) {
             const float dk = r - c_aev.shf_r[k];
-            s = fmaf(g[k] * M<true>::ex2(-kEtaRad * 1.4426950408889634f * dk * dk), -2.f * kEtaRad * dk * fc + dfc, s);
+            s = fmaf(gv[k] * M<true>::ex2(-kEtaRad * 1.4426950408889634f * dk * dk), -2.f * kEtaRad * dk * fc + dfc, s);
         }
     }
     return 0.25f * s;
@@ -566,15 +664,16 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* p, float (&v)[8]) {
     }
 }
 
-template <bool FAST, typename TG>
-__global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
-                                                         double* __restrict__ grad) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kForceWarps + w;
-    if (i >= a.n) return;
-    AngStage& s = *reinterpret_cast<AngStage*>(smem + w * kForceSmemPerWarp);
-    float* gs = reinterpret_cast<float*>(smem + w * kForceSmemPerWarp + sizeof(AngStage));
+// Forces of atom i's AEV terms (the AEV backward for one atom): gradients on
+// i and on its neighbors into the FP64 sums grad. Returns false (nothing
+// added) when the atom has more than CAP angular neighbors: the AEV's main
+// launch has listed such an atom for the second launches.
+template <bool FAST, typename TG, int CAP>
+__device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restrict__ dG, double* __restrict__ grad,
+                                           int i, unsigned char* wsmem) {
+    const int lane = threadIdx.x & 31;
+    AngStage<CAP>& s = *reinterpret_cast<AngStage<CAP>*>(wsmem);
+    float* gs = reinterpret_cast<float*>(wsmem + sizeof(AngStage<CAP>));
     float* fslot = gs + kGsFloats;
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
     const int si = species_of(hi_i);
@@ -600,29 +699,45 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
         for (int q = 0; q < 4; ++q) {
             const int c = 8 * lane + 256 * q;
             if (c < kAevLen) {
-                const int dst = c < kRadLen ? kGsRadStride * (c >> 4) + (c & 15)
-                                            : kGsRad + kGsAngStride * ((c - kRadLen) >> 5) + ((c - kRadLen) & 31);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) gs[dst + e] = v[q][e];
+                // columns c .. c + 7: groups g0 and g0 + 1 of one row
+                const bool rad = c < kRadLen;
+                const int rowq = rad ? c >> 4 : (c - kRadLen) >> 5;
+                const int g0 = rad ? (c & 15) >> 2 : ((c - kRadLen) & 31) >> 2;
+                *reinterpret_cast<float4*>(gs + (rad ? gs_rad(rowq, g0) : gs_ang(rowq, g0))) =
+                    make_float4(v[q][0], v[q][1], v[q][2], v[q][3]);
+                *reinterpret_cast<float4*>(gs + (rad ? gs_rad(rowq, g0 + 1) : gs_ang(rowq, g0 + 1))) =
+                    make_float4(v[q][4], v[q][5], v[q][6], v[q][7]);
             }
         }
     }
-    for (int c = lane; c < 3 * kMaxAng; c += 32) fslot[c] = 0.f;
+    for (int c = lane; c < 3 * CAP; c += 32) fslot[c] = 0.f;
+    __syncwarp();
+
+    // The angular neighbors are staged first; nothing is added to grad before
+    // the atom is known to fit the stage.
+    int mA = 0;
+    if (cnt > 0) mA = stage_angular<FAST, CAP>(nl0, mA, s);
+    if (cnt > 32) mA = stage_angular<FAST, CAP>(nl1, mA, s);
+    for (int base = 64; base < cnt; base += 32)
+        mA = stage_angular<FAST, CAP>(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i), mA, s);
+    if (mA > CAP) return false;   // warp-uniform
     __syncwarp();
 
     float fix = 0.f, fiy = 0.f, fiz = 0.f;   // dE/dr_i partial sums of this lane
-    int mA = 0;
     // radial: one neighbor per lane. The gradient on an angular neighbor goes
     // to its (still private) shared-memory slot, which the angular terms add
     // to and which is flushed once; other neighbors go straight to the FP64 sums.
+    int mR = 0;
     auto chunk = [&](const NbrLane& nl) {
-        int pA;
-        mA = stage_angular<FAST>(nl, mA, s, a, &pA);
+        // the lane's slot in the stage: angular neighbors were staged in list order
+        const unsigned bA = __ballot_sync(kFull, nl.inA);
+        const int pA = nl.inA ? mR + __popc(bA & lanemask_lt()) : -1;
+        mR += __popc(bA);
         if (nl.inR) {
             const float x = nl.r * (1.f / kRcRad);
             const float fc = 0.5f * M<FAST>::cpi(x) + 0.5f;
             const float dfc = -0.5f * (3.14159265358979f / kRcRad) * M<FAST>::spi(x);
-            const float sc = radial_dEdr<FAST>(gs + nl.sp * kGsRadStride, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
+            const float sc = radial_dEdr<FAST>(gs, nl.sp, nl.r, fc, dfc) * M<FAST>::rcp(nl.r);
             const float gx = sc * nl.d.x, gy = sc * nl.d.y, gz = sc * nl.d.z;
             if (pA >= 0) {
                 fslot[3 * pA] = gx;
@@ -641,8 +756,6 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
     if (cnt > 0) chunk(nl0);
     if (cnt > 32) chunk(nl1);
     for (int base = 64; base < cnt; base += 32) chunk(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i));
-    const int mS = min(mA, kMaxAng);   // staged slots (flushed even on overflow)
-    if (mA > kMaxAng) mA = 0;
     __syncwarp();
 
     // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers
@@ -669,7 +782,20 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
                     R[aa] = M<FAST>::gauss(kEtaAng, dr);
                     dR[aa] = -2.f * kEtaAng * dr * R[aa];
                 }
-                const float* gp = gs + kGsRad + kGsAngStride * p;
+                // U_z = sum_a g[a][z] R_a and V_z = sum_a g[a][z] dR_a, the row of
+                // dE/dG read as two 4-column groups per shift
+                float U[kAngZ], V[kAngZ];
+#pragma unroll
+                for (int aa = 0; aa < kAngA; ++aa) {
+                    const float4 g0 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa));
+                    const float4 g1 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa + 1));
+                    const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+                    for (int z = 0; z < kAngZ; ++z) {
+                        U[z] = aa == 0 ? gg[z] * R[0] : fmaf(gg[z], R[aa], U[z]);
+                        V[z] = aa == 0 ? gg[z] * dR[0] : fmaf(gg[z], dR[aa], V[z]);
+                    }
+                }
                 float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
                 for (int z = 0; z < kAngZ; ++z) {
@@ -687,16 +813,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
                         Pz = 2.f * M<false>::pw(b, kZeta);
                         dPdc = 0.5f * kZeta * Pz * sm * M<false>::rcp(b) * isn;
                     }
-                    float S1 = 0.f, S2 = 0.f;
-#pragma unroll
-                    for (int aa = 0; aa < kAngA; ++aa) {
-                        const float gg = gp[8 * aa + z];
-                        S1 = fmaf(gg, R[aa], S1);
-                        S2 = fmaf(gg, dR[aa], S2);
-                    }
-                    Sc = fmaf(dPdc, S1, Sc);
-                    T1 = fmaf(Pz, S1, T1);
-                    T2 = fmaf(Pz, S2, T2);
+                    Sc = fmaf(dPdc, U[z], Sc);
+                    T1 = fmaf(Pz, U[z], T1);
+                    T2 = fmaf(Pz, V[z], T2);
                 }
                 const float f = fj * fk;
                 Sc *= f;
@@ -735,11 +854,38 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG
         atomicAdd(&grad[3 * (size_t)i + 1], (double)fiy);
         atomicAdd(&grad[3 * (size_t)i + 2], (double)fiz);
     }
-    for (int q = lane; q < mS; q += 32) {
+    for (int q = lane; q < mA; q += 32) {
         const int jj = s.idx[q];
         atomicAdd(&grad[3 * (size_t)jj], (double)fslot[3 * q]);
         atomicAdd(&grad[3 * (size_t)jj + 1], (double)fslot[3 * q + 1]);
         atomicAdd(&grad[3 * (size_t)jj + 2], (double)fslot[3 * q + 2]);
+    }
+    return true;
+}
+
+// Main force launch: one warp per atom; an atom with more than kAngCap
+// angular neighbors is left to the second launch (the AEV listed it).
+template <bool FAST, typename TG>
+__global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
+                                                         double* __restrict__ grad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = threadIdx.x >> 5;
+    const int i = blockIdx.x * kForceWarps + w;
+    if (i >= a.n) return;
+    if (!force_atom<FAST, TG, kAngCap>(a, dG, grad, i, smem + w * force_smem_per_warp<kAngCap>()) &&
+        (threadIdx.x & 31) == 0 && !a.big_flag[i])
+        atomicMax(&a.ctr->ang_overflow, kAngCapBig + 1);   // not listed by the AEV: a mismatch, reported
+}
+
+// Second force launch: the atoms the AEV listed (usually none).
+template <bool FAST, typename TG>
+__global__ void __launch_bounds__(32) k_forces_big(AevArgs a, const TG* __restrict__ dG, double* __restrict__ grad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nb = a.ctr->ang_big;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        if (!force_atom<FAST, TG, kAngCapBig>(a, dG, grad, a.big_list[t], smem) && (threadIdx.x & 31) == 0)
+            atomicMax(&a.ctr->ang_overflow, kAngCapBig + 1);
+        __syncwarp();
     }
 }
 
@@ -748,47 +894,61 @@ void set_smem(K kernel, size_t bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Grid of the second launches (listed atoms, usually none): they stride over
+// the list, so a few blocks per SM suffice.
+constexpr int kBigGrid = 296;
+
+template <bool FAST, typename OutT>
+void launch_aev_t(cudaStream_t st, const AevArgs& a, OutT* G, OutT* G_lo, int* row_atom) {
+    const size_t sm = kAevWarps * aev_smem_per_warp<kAngCap>();
+    const size_t smb = aev_smem_per_warp<kAngCapBig>();
+    once_per_device((const void*)k_aev<FAST, OutT>, [&] {
+        set_smem(k_aev<FAST, OutT>, sm);
+        set_smem(k_aev_big<FAST, OutT>, smb);
+    });
+    const int gs = (a.n + kAevWarps - 1) / kAevWarps;
+    MLP_LAUNCH("aev", st, k_aev<FAST, OutT><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
+    MLP_LAUNCH("aev_big", st, k_aev_big<FAST, OutT><<<kBigGrid, 32, smb, st>>>(a, G, G_lo, row_atom));
+}
+
+template <bool FAST, typename TG>
+void launch_forces_t(cudaStream_t st, const AevArgs& a, const TG* dG, double* grad) {
+    const size_t sm = kForceWarps * force_smem_per_warp<kAngCap>();
+    const size_t smb = force_smem_per_warp<kAngCapBig>();
+    once_per_device((const void*)k_forces<FAST, TG>, [&] {
+        set_smem(k_forces<FAST, TG>, sm);
+        set_smem(k_forces_big<FAST, TG>, smb);
+    });
+    const int gs = (a.n + kForceWarps - 1) / kForceWarps;
+    MLP_LAUNCH("forces", st, k_forces<FAST, TG><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
+    MLP_LAUNCH("forces_big", st, k_forces_big<FAST, TG><<<kBigGrid, 32, smb, st>>>(a, dG, grad));
+}
+
 }  // namespace
 
 void launch_aev_f32(cudaStream_t st, const AevArgs& a, float* G, int* row_atom, bool fast) {
-    const size_t sm = kAevWarps * kAevSmemPerWarp;
-    const int gs = (a.n + kAevWarps - 1) / kAevWarps;
-    if (fast) {
-        once_per_device((const void*)k_aev<true, float>, [&] { set_smem(k_aev<true, float>, sm); });
-        MLP_LAUNCH("aev", st, k_aev<true, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
-    } else {
-        once_per_device((const void*)k_aev<false, float>, [&] { set_smem(k_aev<false, float>, sm); });
-        MLP_LAUNCH("aev", st, k_aev<false, float><<<gs, kAevWarps * 32, sm, st>>>(a, G, nullptr, row_atom));
-    }
+    if (fast)
+        launch_aev_t<true, float>(st, a, G, nullptr, row_atom);
+    else
+        launch_aev_t<false, float>(st, a, G, nullptr, row_atom);
 }
 
 void launch_aev_bf16(cudaStream_t st, const AevArgs& a, __nv_bfloat16* G, __nv_bfloat16* G_lo, int* row_atom,
                      bool fast) {
-    const size_t sm = kAevWarps * kAevSmemPerWarp;
-    const int gs = (a.n + kAevWarps - 1) / kAevWarps;
-    if (fast) {
-        once_per_device((const void*)k_aev<true, __nv_bfloat16>, [&] { set_smem(k_aev<true, __nv_bfloat16>, sm); });
-        MLP_LAUNCH("aev", st, k_aev<true, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
-    } else {
-        once_per_device((const void*)k_aev<false, __nv_bfloat16>, [&] { set_smem(k_aev<false, __nv_bfloat16>, sm); });
-        MLP_LAUNCH("aev", st, k_aev<false, __nv_bfloat16><<<gs, kAevWarps * 32, sm, st>>>(a, G, G_lo, row_atom));
-    }
+    if (fast)
+        launch_aev_t<true, __nv_bfloat16>(st, a, G, G_lo, row_atom);
+    else
+        launch_aev_t<false, __nv_bfloat16>(st, a, G, G_lo, row_atom);
 }
 
 void launch_forces(cudaStream_t st, const AevArgs& a, const float* dG, const __nv_bfloat16* dG16, double* grad,
                    bool fast) {
-    const size_t sm = kForceWarps * kForceSmemPerWarp;
-    const int gs = (a.n + kForceWarps - 1) / kForceWarps;
-    if (dG16) {
-        once_per_device((const void*)k_forces<true, __nv_bfloat16>, [&] { set_smem(k_forces<true, __nv_bfloat16>, sm); });
-        MLP_LAUNCH("forces", st, k_forces<true, __nv_bfloat16><<<gs, kForceWarps * 32, sm, st>>>(a, dG16, grad));
-    } else if (fast) {
-        once_per_device((const void*)k_forces<true, float>, [&] { set_smem(k_forces<true, float>, sm); });
-        MLP_LAUNCH("forces", st, k_forces<true, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
-    } else {
-        once_per_device((const void*)k_forces<false, float>, [&] { set_smem(k_forces<false, float>, sm); });
-        MLP_LAUNCH("forces", st, k_forces<false, float><<<gs, kForceWarps * 32, sm, st>>>(a, dG, grad));
-    }
+    if (dG16)
+        launch_forces_t<true, __nv_bfloat16>(st, a, dG16, grad);
+    else if (fast)
+        launch_forces_t<true, float>(st, a, dG, grad);
+    else
+        launch_forces_t<false, float>(st, a, dG, grad);
 }
 
 }  // namespace mlp

@@ -2,15 +2,23 @@
 
 With random-init weights the potential has no repulsive core: after some
 hundreds of femtoseconds atoms fall into attractive regions and pairs
-collapse. The harness therefore guards the trajectory (closest pair below
-0.5 A, or a neighbor-capacity error from the library) and reports the steps
-completed, the energy drift over the stable window and the throughput.
+collapse. A caller that runs dynamics therefore adds a short-range
+repulsion, as a classical force field's non-bonded term would
+(RepulsiveWall: a shifted r^-12 wall inside sigma with bounded curvature,
+zero with its force at sigma and beyond). It is the caller's term, outside
+the ML potential: its forces are written first and the library adds the ML
+forces onto them (mlp_energy_forces_subset_device with accumulate, the
+ML/MM path). Its pairs come from the library's allocation-free neighbor
+search (mlp_neighbors_static). Without the wall the harness guards the
+trajectory (closest pair below 0.5 A, or a neighbor-capacity error from the
+library) and reports the steps completed.
 
 Not part of the evaluation itself: a driver that integrates Newton's
 equations with the library's forces, to check energy conservation (the
-672-atom ligand-in-water system) and to time a persistent system with a
-skin neighbor list (the 21,080-atom periodic box: list radius 5.1 + 0.5 A,
-rebuilt every 10 steps or when an atom moved more than half the skin).
+672-atom ligand-in-water system, 10,000 steps of 0.5 fs) and to time a
+persistent system with a skin neighbor list (the 21,080-atom periodic box:
+list radius 5.1 + 0.5 A, rebuilt every 10 steps or when an atom moved more
+than half the skin; 1,000 steps of 0.5 fs).
 
 Units: A, fs, amu, eV. Acceleration F/m in eV/(A amu) = 9.6485e-3 A/fs^2;
 kinetic energy 0.5 m v^2 (amu A^2/fs^2) = 103.6427 eV per unit.
@@ -56,9 +64,76 @@ def _min_pair_distance_ok(coords_t, cell, limit, lib):
     return int(counts.max().item()) == 0
 
 
+class RepulsiveWall:
+    """The caller's short-range repulsion, summed over pairs closer than
+    sigma (A): U(r) = eps [(sigma / r)^12 - 1 + 12 (r / sigma - 1)] (eV),
+    zero with its derivative at sigma, and below r_soft continued linearly
+    (constant force, so its curvature stays bounded and a 0.5 fs step stays
+    stable when a hot atom hits it; the r^-12 wall alone made the 21,080-atom
+    box blow up). The random-init network's energy keeps falling as atoms
+    crowd (AEV entries grow with the number of close neighbors), so the wall
+    must start before the collapse: sigma 1.0 A, eps 0.2 eV, r_soft 0.85 A
+    held the 672-atom system for 10,000 steps and the box for 1,000. Pairs
+    within sigma come from mlp_neighbors_static (up to `cap` per atom; more
+    is reported, never silently dropped from the sum)."""
+
+    def __init__(self, n, cell=None, sigma=1.0, eps=0.2, cap=16, r_soft=0.85):
+        import torch
+
+        self.n, self.sigma, self.eps, self.cap = n, float(sigma), float(eps), cap
+        self.r_soft = float(r_soft)   # below it the wall continues linearly (bounded curvature)
+        self.cell = None if cell is None else np.ascontiguousarray(cell, dtype=np.float64)
+        dev = torch.device("cuda")
+        self.counts = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.list = torch.zeros((n, cap), dtype=torch.int32, device=dev)
+        self.rows = torch.arange(n, device=dev)[:, None].expand(n, cap)
+        self.slot = torch.arange(cap, device=dev, dtype=torch.int32)[None, :]
+        self.L = None if cell is None else torch.as_tensor(self.cell, device=dev)
+        self.max_seen = torch.zeros((), dtype=torch.int32, device=dev)   # largest count since creation
+
+    def energy_forces(self, x, F):
+        """Writes the wall's forces (float32) into F [n, 3]; returns its energy
+        as a float64 device tensor [1]."""
+        import torch
+
+        from ._lib import check, load
+
+        lib = load()
+        cl = None if self.cell is None else self.cell.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        check(lib.mlp_neighbors_static(ctypes.c_void_p(x.data_ptr()), self.n, cl, self.sigma,
+                                       ctypes.c_void_p(self.counts.data_ptr()), ctypes.c_void_p(self.list.data_ptr()),
+                                       self.cap, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+              "mlp_neighbors_static (repulsive wall)")
+        torch.maximum(self.max_seen, self.counts.max(), out=self.max_seen)
+        valid = self.slot < self.counts[:, None]
+        i = self.rows[valid]
+        j = self.list[valid].long()
+        d = x[j] - x[i]
+        if self.L is not None:
+            d = d - self.L * torch.round(d / self.L)
+        r = d.norm(dim=1).clamp_min(1e-3)
+        rr = r.clamp_min(self.r_soft) if self.r_soft > 0.0 else r
+        q12 = (self.sigma / rr) ** 12
+        inside = r < self.sigma
+        u = torch.where(inside, self.eps * (q12 - 1.0 + 12.0 * (rr / self.sigma - 1.0)), torch.zeros_like(r))
+        dudr = torch.where(inside, self.eps * 12.0 * (1.0 / self.sigma - q12 / rr), torch.zeros_like(r))
+        if self.r_soft > 0.0:
+            u = u + torch.where(r < rr, dudr * (r - rr), torch.zeros_like(r))
+        f = (dudr / r)[:, None] * d          # force on i from the pair (i, j): -dU/dr along -d/r
+        F.zero_()
+        F.index_add_(0, i, f.to(F.dtype))
+        return (0.5 * u.sum()).reshape(1)     # each pair is listed from both ends
+
+    def overflow(self):
+        """True if any call so far found more pairs of an atom than the list holds."""
+        return int(self.max_seen.item()) > self.cap
+
+
 def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=300.0, seed=0, report_every=10,
-        guard_every=1000, min_pair=0.5):
-    """Integrates `steps` velocity-Verlet steps; returns a dict of results."""
+        guard_every=1000, min_pair=0.5, wall=None):
+    """Integrates `steps` velocity-Verlet steps; returns a dict of results.
+    wall: a RepulsiveWall (the caller's repulsion, added to the ML forces),
+    or None (the ML potential alone, with the collapse guard)."""
     import torch
 
     from . import _lib
@@ -75,7 +150,18 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
     E = torch.zeros(1, dtype=torch.float64, device=dev)
     F = torch.zeros((len(species), 3), dtype=torch.float32, device=dev)
     lib = _lib.load()
-    system.energy_forces_device(x, E, F)
+    index = torch.arange(len(species), dtype=torch.int32, device=dev)
+
+    def forces():
+        """Potential energy (device [1]) and total forces into F."""
+        if wall is None:
+            system.energy_forces_device(x, E, F)
+            return E
+        E_w = wall.energy_forces(x, F)
+        system.energy_forces_subset_device(x, index, forces_full=F, energy=E, accumulate=True)
+        return E + E_w
+
+    Epot = forces()
     a = F.double() * (ACC / m)
     t_series, e_pot, e_kin = [], [], []
     aborted = None
@@ -88,7 +174,7 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
         v.add_(a, alpha=0.5 * dt_fs)
         x.add_(v, alpha=dt_fs)
         try:
-            system.energy_forces_device(x, E, F)
+            Epot = forces()
         except MLPError as e:          # e.g. neighbor capacity exceeded after a collapse
             aborted = f"step {step}: {e}"
             step -= 1
@@ -98,13 +184,18 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
         if step % report_every == 0:
             ke = 0.5 * KE * float((m * v * v).sum().item())
             t_series.append(step * dt_fs)
-            e_pot.append(float(E.item()))
+            e_pot.append(float(Epot.item()))
             e_kin.append(ke)
+            if wall is not None and wall.overflow():
+                aborted = f"by step {step}: more than {wall.cap} pairs of an atom inside the wall"
+                break
         if guard_every and step % guard_every == 0 and not _min_pair_distance_ok(x, cell, min_pair, lib):
             aborted = f"pair closer than {min_pair} A at step {step}"
             break
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    wall_s = time.perf_counter() - t0
+    if aborted is None and wall is not None and wall.overflow():
+        aborted = f"by step {step}: more than {wall.cap} pairs of an atom inside the wall"
     try:
         system.sync()
     except MLPError as e:
@@ -116,12 +207,14 @@ def run(system, species, coords, cell=None, dt_fs=0.5, steps=1000, temperature=3
     et = np.array(e_pot) + np.array(e_kin)
     slope = float(np.polyfit(tt, et, 1)[0]) if len(tt) > 2 else float("nan")   # eV / fs
     done = step if aborted is None else step
-    return {"atoms": n, "steps": done, "dt_fs": dt_fs, "wall_s": wall, "atom_steps_per_s": n * done / wall,
+    return {"atoms": n, "steps": done, "dt_fs": dt_fs, "wall_s": wall_s, "atom_steps_per_s": n * done / wall_s,
             "drift_eV_per_atom_per_ps": slope * 1000.0 / n,
             "etot_rms_fluct_eV_per_atom": float(np.std(et - np.polyval(np.polyfit(tt, et, 1), tt)) / n)
             if len(tt) > 2 else None,
             "etot_first": float(et[0]) if len(et) else None, "etot_last": float(et[-1]) if len(et) else None,
-            "temperature_K_last": float(2 * e_kin[-1] / (3 * n * KB)) if e_kin else None, "aborted": aborted}
+            "temperature_K_last": float(2 * e_kin[-1] / (3 * n * KB)) if e_kin else None, "aborted": aborted,
+            "repulsive_wall": None if wall is None else {"sigma_A": wall.sigma, "eps_eV": wall.eps,
+                                                         "r_soft_A": wall.r_soft}}
 
 
 def main():
@@ -145,7 +238,8 @@ def main():
         steps = args.steps or 1000
         prec = args.precision or "bf16"
         s = System(W, c.species, c.coords, c.cell, precision=prec, skin=0.5)
-    res = run(s, c.species, c.coords, c.cell, dt_fs=args.dt, steps=steps)
+    res = run(s, c.species, c.coords, c.cell, dt_fs=args.dt, steps=steps, guard_every=0,
+              wall=RepulsiveWall(c.n, c.cell))
     res.update({"workload": c.name, "precision": prec})
     print(json.dumps(res))
 
