@@ -21,7 +21,9 @@ one net and the 8-net ensemble; velocity-Verlet trajectories at 0.5 fs with
 a caller-side repulsive wall (10,000 steps of the 672-atom system: energy
 drift; 1,000 steps of the 21,080-atom box on its skin list: atom-steps/s); the same device-resident stream with an ensemble of
 --ensemble-nets nets (energy = mean of the nets, forces = mean gradient),
-Poisson-arrival latency sweep, the one-molecule-per-launch FP32 path, the
+Poisson-arrival latency sweep of the server and, with the same arrivals, of
+the one-molecule-per-launch FP32 path (one host queue), that path back to
+back, the
 roofline of the dominant kernel and the FP64 oracle on the host cores
 (cpu_baseline). --nets K makes the ensemble the headline model instead.
 
@@ -400,9 +402,11 @@ def run_ours(args):
             result["latency_sweep"] = sweep(srv, stream, args)
         srv.close()
 
-    # ---------------- plain FP32, one molecule per launch
+    # ---------------- plain FP32, one molecule per launch: back to back, and open-loop
     if not args.no_plain and rank == 0:
         result["plain_fp32"] = plain_fp32(P, W, stream, args)
+        if not args.no_sweep:
+            result["latency_sweep_plain_fp32"] = plain_sweep(P, W, stream, args)
 
     # ---------------- Langevin dynamics (2 fs), graph-replayed steps
     if not args.no_md and rank == 0:
@@ -629,6 +633,47 @@ def sweep(srv, stream, args):
     return out
 
 
+def plain_sweep(P, W, stream, args):
+    """The one-molecule-per-call FP32 path under the served sweep's open-loop
+    Poisson arrivals (the same seeded arrival times): one host queue, one
+    worker that takes requests in arrival order and runs each synchronously
+    (mlp_batch_run, host buffers, FP32 network), idling until the next
+    arrival when the queue is empty; latency = completion - arrival. At most
+    args.plain_sweep_requests requests per rate (the first ones of the
+    served sweep's sequence). Above its capacity (requests per second of
+    service time) the queue, and with it the latency, grows without bound
+    for as long as requests keep arriving."""
+    b = P.Batch(W, precision="fp32", max_atoms=256, max_mols=1, max_atoms_per_mol=256)
+    rng = np.random.default_rng(7)
+    out = []
+    for lam in (1000, 2000, 5000, 10000, 20000, 50000):
+        n_served = int(min(stream.count, max(200, lam * args.sweep_seconds)))
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=n_served))    # the served sweep's arrivals
+        n = min(n_served, args.plain_sweep_requests)
+        lat = np.empty(n)
+        busy = 0.0
+        atoms = 0
+        t0 = time.perf_counter()
+        for m in range(n):
+            due = t0 + arr[m]
+            while time.perf_counter() < due:
+                pass
+            a, z = int(stream.mol_start[m]), int(stream.mol_start[m + 1])
+            t1 = time.perf_counter()
+            b.run(np.array([0, z - a], dtype=np.int32), stream.species[a:z], stream.coords[a:z])
+            t2 = time.perf_counter()
+            busy += t2 - t1
+            lat[m] = t2 - due
+            atoms += z - a
+        wall = time.perf_counter() - t0
+        cap = n / busy
+        out.append({"rate_req_s": lam, "requests": n, "served_req_s": n / wall, "atoms_per_s": atoms / wall,
+                    "capacity_req_s": cap, "saturated": bool(lam > cap),
+                    "p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3})
+    b.close()
+    return out
+
+
 def plain_fp32(P, W, stream, args):
     """One molecule per launch sequence, FP32 network, synchronous host calls."""
     b = P.Batch(W, precision="fp32", max_atoms=256, max_mols=1, max_atoms_per_mol=256)
@@ -794,6 +839,8 @@ def main():
     ap.add_argument("--sweep-seconds", type=float, default=1.0)
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--plain-seconds", type=float, default=3.0)
+    ap.add_argument("--plain-sweep-requests", type=int, default=2000,
+                    help="requests per arrival rate of the plain path's open-loop sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-clients", type=int, default=1, help="client threads of the e2e replay")

@@ -895,8 +895,8 @@ void set_smem(K kernel, size_t bytes) {
 }
 
 // Grid of the second launches (listed atoms, usually none): they stride over
-// the list, so a few blocks per SM suffice.
-constexpr int kBigGrid = 296;
+// the list; a small grid keeps an empty launch cheap (it only reads the count).
+constexpr int kBigGrid = 32;
 
 template <bool FAST, typename OutT>
 void launch_aev_t(cudaStream_t st, const AevArgs& a, OutT* G, OutT* G_lo, int* row_atom) {
