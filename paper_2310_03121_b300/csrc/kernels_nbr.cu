@@ -19,6 +19,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <algorithm>
+
 namespace mlp {
 
 namespace {
@@ -26,6 +28,11 @@ namespace {
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
     return m;
 }
 
@@ -289,39 +296,50 @@ __global__ void k_cell_count(int n, const float4* __restrict__ hi, const Grid* _
     cell_rank[i] = atomicAdd(&cell_count[c], 1);
 }
 
-// Exclusive scan of the cell counts (one block of 1024 threads).
-__global__ void k_cell_scan(const Grid* __restrict__ g, const int* __restrict__ cell_count,
+// Exclusive scan of the cell counts: one block of 1024 threads, each thread
+// summing kScanPer consecutive cells per round (16,384 cells a round).
+constexpr int kScanPer = 16;
+__global__ void __launch_bounds__(1024) k_cell_scan(const Grid* __restrict__ g, const int* __restrict__ cell_count,
                             int* __restrict__ cell_start, const Counters* __restrict__ ctr) {
     if (!ctr->rebuild) return;
     __shared__ int warp_sums[32];
     __shared__ int carry;
-    int ncell = g->ncell;
+    const int ncell = g->ncell;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int base = 0; base < ncell; base += 1024) {
-        int c = base + threadIdx.x;
-        int v = c < ncell ? cell_count[c] : 0;
-        int x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < ncell; base += kScanPer * 1024) {
+        const int c0 = base + kScanPer * threadIdx.x;
+        int v[kScanPer], t = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            v[k] = c0 + k < ncell ? cell_count[c0 + k] : 0;
+            t += v[k];
+        }
+        int x = t;
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_sums[w] = x;
         __syncthreads();
         if (w == 0) {
-            int s = warp_sums[lane];
+            int sm = warp_sums[lane];
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
+                const int y = __shfl_up_sync(0xffffffffu, sm, o);
+                if (lane >= o) sm += y;
             }
-            warp_sums[lane] = s;
+            warp_sums[lane] = sm;
         }
         __syncthreads();
-        int incl = x + (w > 0 ? warp_sums[w - 1] : 0) + carry;
-        if (c < ncell) cell_start[c] = incl - v;
+        int run = x - t + (w > 0 ? warp_sums[w - 1] : 0) + carry;   // exclusive start of this thread's cells
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            if (c0 + k < ncell) cell_start[c0 + k] = run;
+            run += v[k];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = incl;
+        if (threadIdx.x == 1023) carry = run;
         __syncthreads();
     }
     if (threadIdx.x == 0) cell_start[ncell] = carry;
@@ -335,23 +353,60 @@ __global__ void k_cell_scatter(int n, const int* __restrict__ cell_of_atom, cons
     cell_atoms[cell_start[cell_of_atom[i]] + cell_rank[i]] = i;
 }
 
-// Insertion sort of each cell's atoms by index, so that the neighbor order
-// does not depend on the order of the counting atomics.
+// Each cell's atoms in index order, so that the neighbor order does not
+// depend on the order of the counting atomics: one warp per cell; an atom's
+// place is the number of atoms of the cell with a smaller index (cells of up
+// to 256 atoms, read once into registers; larger ones, which only degenerate
+// inputs make, are sorted by one lane).
+constexpr int kSortChunks = 8;
+__device__ __forceinline__ void sort_cell(int a, int m, int* __restrict__ cell_atoms, int lane) {
+    if (m <= 1) return;
+    if (m > 32 * kSortChunks) {
+        if (lane == 0)
+            for (int p = a + 1; p < a + m; ++p) {
+                const int v = cell_atoms[p];
+                int q = p - 1;
+                while (q >= a && cell_atoms[q] > v) {
+                    cell_atoms[q + 1] = cell_atoms[q];
+                    --q;
+                }
+                cell_atoms[q + 1] = v;
+            }
+        return;
+    }
+    int v[kSortChunks], rank[kSortChunks];
+#pragma unroll
+    for (int k = 0; k < kSortChunks; ++k) {
+        v[k] = 32 * k + lane < m ? cell_atoms[a + 32 * k + lane] : 0x7fffffff;
+        rank[k] = 0;
+    }
+    const int nch = (m + 31) >> 5;
+#pragma unroll
+    for (int k2 = 0; k2 < kSortChunks; ++k2) {
+        if (k2 >= nch) break;   // warp-uniform
+        for (int u = 0; u < 32; ++u) {
+            const int w = __shfl_sync(0xffffffffu, v[k2], u);
+#pragma unroll
+            for (int k = 0; k < kSortChunks; ++k)
+                if (k < nch) rank[k] += w < v[k] ? 1 : 0;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kSortChunks; ++k)
+        if (32 * k + lane < m) cell_atoms[a + rank[k]] = v[k];
+}
+
 __global__ void k_cell_sort(const Grid* __restrict__ g, const int* __restrict__ cell_start,
                             int* __restrict__ cell_atoms, const Counters* __restrict__ ctr) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!ctr->rebuild || c >= g->ncell) return;
-    int a = cell_start[c], b = cell_start[c + 1];
-    for (int p = a + 1; p < b; ++p) {
-        int v = cell_atoms[p];
-        int q = p - 1;
-        while (q >= a && cell_atoms[q] > v) {
-            cell_atoms[q + 1] = cell_atoms[q];
-            --q;
-        }
-        cell_atoms[q + 1] = v;
-    }
+    const int lane = threadIdx.x & 31;
+    if (!ctr->rebuild) return;
+    const int ncell = g->ncell, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nw)   // warp-uniform
+        sort_cell(cell_start[c], cell_start[c + 1] - cell_start[c], cell_atoms, lane);
 }
+
+constexpr int kNbrCellWarps = 8;   // warps (atoms) per block of k_nbr_cell
 
 __global__ void k_nbr_cell(int n, NbrArgs a, Box box, const Grid* __restrict__ g,
                            const int* __restrict__ cell_of_atom, const int* __restrict__ cell_start,
@@ -406,41 +461,65 @@ __global__ void k_nbr_cell(int n, NbrArgs a, Box box, const Grid* __restrict__ g
         const float3 d = displacement(hi_i, lo_i, hj, a.lo[j], box);
         return d.x * d.x + d.y * d.y + d.z * d.z < a.rl2;
     };
-    for (int oz = lo3[2]; oz <= hi3[2]; ++oz) {
-        int z = rel[2] ? cc[2] + oz : oz;
-        if (rel[2]) {
-            if (box.periodic) z = (z + nc2) % nc2;
-            else if (z < 0 || z >= nc2) continue;
-        }
-        for (int oy = lo3[1]; oy <= hi3[1]; ++oy) {
-            int y = rel[1] ? cc[1] + oy : oy;
-            if (rel[1]) {
-                if (box.periodic) y = (y + nc1) % nc1;
-                else if (y < 0 || y >= nc1) continue;
-            }
-            for (int ox = lo3[0]; ox <= hi3[0]; ++ox) {
-                int x = rel[0] ? cc[0] + ox : ox;
-                if (rel[0]) {
-                    if (box.periodic) x = (x + nc0) % nc0;
-                    else if (x < 0 || x >= nc0) continue;
-                }
-                int cell = (z * nc1 + y) * nc0 + x;
-                int beg = cell_start[cell], end = cell_start[cell + 1];
-                for (int base = beg; base < end; base += 32) {
-                    int q = base + lane;
-                    bool ok = false;
-                    int j = -1;
-                    if (q < end) {
-                        j = cell_atoms[q];
-                        ok = j != i && within(j);
-                    }
-                    unsigned mask = __ballot_sync(0xffffffffu, ok);
-                    int pos = count + __popc(mask & lanemask_lt());
-                    if (ok && pos < a.cap) row[pos] = j;
-                    count += __popc(mask);
-                }
+    // The (at most 27) cells to visit, in (z, y, x) order: lane v takes visit
+    // v and loads its cell's range, so all ranges take one memory round trip;
+    // the non-empty ones are compacted (lane k < ne: the k-th, first candidate
+    // position coff, first entry cbeg in cell_atoms). Candidates are then
+    // taken 32 at a time in the same order as visiting the cells one by one
+    // (cells in (z, y, x) order, atoms in index order within a cell).
+    const int nv0 = hi3[0] - lo3[0] + 1, nv1 = hi3[1] - lo3[1] + 1, nv2 = hi3[2] - lo3[2] + 1;
+    int beg = 0, len = 0;
+    if (lane < nv0 * nv1 * nv2) {
+        const int o[3] = {lo3[0] + lane % nv0, lo3[1] + (lane / nv0) % nv1, lo3[2] + lane / (nv0 * nv1)};
+        int v[3];
+        bool inside = true;
+        for (int ax = 0; ax < 3; ++ax) {
+            v[ax] = rel[ax] ? cc[ax] + o[ax] : o[ax];
+            if (rel[ax]) {
+                if (box.periodic) v[ax] = (v[ax] + ncs[ax]) % ncs[ax];
+                else if (v[ax] < 0 || v[ax] >= ncs[ax]) inside = false;
             }
         }
+        if (inside) {
+            const int cell = (v[2] * nc1 + v[1]) * nc0 + v[0];
+            beg = cell_start[cell];
+            len = cell_start[cell + 1] - beg;
+        }
+    }
+    const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
+    const int ne = __popc(nonempty);
+    int total = len;   // inclusive prefix over the visits
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, total, o);
+        if (lane >= o) total += t;
+    }
+    const int off = total - len;
+    total = __shfl_sync(0xffffffffu, total, 31);
+    // compact: lane k < ne gets the k-th non-empty visit's (off, beg)
+    __shared__ int2 visit_sm[kNbrCellWarps][32];
+    int2* vs = visit_sm[threadIdx.x >> 5];
+    if (len > 0) vs[__popc(nonempty & lanemask_lt())] = make_int2(off, beg);
+    __syncwarp();
+    const int2 cv = lane < ne ? vs[lane] : make_int2(total, 0);
+    const int coff = cv.x, cbeg = cv.y;
+    for (int base = 0; base < total; base += 32) {
+        // candidate q = base + lane: the non-empty visit holding it
+        const unsigned before = __ballot_sync(0xffffffffu, lane < ne && coff < base);
+        const unsigned starts = __reduce_or_sync(
+            0xffffffffu, (lane < ne && coff >= base && coff < base + 32) ? (1u << (coff - base)) : 0u);
+        const int b = max(0, __popc(before) - 1 + __popc(starts & lanemask_le()));
+        const int off_b = __shfl_sync(0xffffffffu, coff, b), beg_b = __shfl_sync(0xffffffffu, cbeg, b);
+        const int q = base + lane;
+        bool ok = false;
+        int j = -1;
+        if (q < total) {
+            j = cell_atoms[beg_b + (q - off_b)];
+            ok = j != i && within(j);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        int pos = count + __popc(mask & lanemask_lt());
+        if (ok && pos < a.cap) row[pos] = j;
+        count += __popc(mask);
     }
     if (lane == 0) {
         a.nbr_cnt[i] = count;
@@ -485,18 +564,18 @@ void launch_cell_build(cudaStream_t st, int n, const float4* hi, const Grid* g, 
     MLP_LAUNCH("cell_scan", st, k_cell_scan<<<1, 1024, 0, st>>>(g, cell_count, cell_start, ctr));
     MLP_LAUNCH("cell_scatter", st,
                k_cell_scatter<<<gs, bs, 0, st>>>(n, cell_of_atom, cell_rank, cell_start, cell_atoms, ctr));
-    MLP_LAUNCH("cell_sort", st,
-               k_cell_sort<<<(max_cells + 255) / 256, 256, 0, st>>>(g, cell_start, cell_atoms, ctr));
+    // a warp per cell, at most 16 blocks of 8 warps per SM (cells are taken grid-stride)
+    const int sort_blocks = (int)std::min<long long>(((long long)max_cells * 32 + 255) / 256, 148LL * 16);
+    MLP_LAUNCH("cell_sort", st, k_cell_sort<<<sort_blocks, 256, 0, st>>>(g, cell_start, cell_atoms, ctr));
 }
 
 void launch_nbr_cell(cudaStream_t st, int n, const NbrArgs& a, const Box& box, const Grid* g,
                      const int* cell_of_atom, const int* cell_start, const int* cell_atoms, Counters* ctr,
                      float4* ref) {
-    int warps_per_block = 8;
-    int gs = (n + warps_per_block - 1) / warps_per_block;
+    int gs = (n + kNbrCellWarps - 1) / kNbrCellWarps;
     MLP_LAUNCH("neighbors_cell", st,
-               k_nbr_cell<<<gs, 32 * warps_per_block, 0, st>>>(n, a, box, g, cell_of_atom, cell_start, cell_atoms,
-                                                               ctr, ref));
+               k_nbr_cell<<<gs, 32 * kNbrCellWarps, 0, st>>>(n, a, box, g, cell_of_atom, cell_start, cell_atoms,
+                                                             ctr, ref));
 }
 
 }  // namespace mlp

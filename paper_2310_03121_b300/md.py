@@ -86,7 +86,6 @@ class RepulsiveWall:
         dev = torch.device("cuda")
         self.counts = torch.zeros(n, dtype=torch.int32, device=dev)
         self.list = torch.zeros((n, cap), dtype=torch.int32, device=dev)
-        self.rows = torch.arange(n, device=dev)[:, None].expand(n, cap)
         self.slot = torch.arange(cap, device=dev, dtype=torch.int32)[None, :]
         self.L = None if cell is None else torch.as_tensor(self.cell, device=dev)
         self.max_seen = torch.zeros((), dtype=torch.int32, device=dev)   # largest count since creation
@@ -105,24 +104,28 @@ class RepulsiveWall:
                                        self.cap, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
               "mlp_neighbors_static (repulsive wall)")
         torch.maximum(self.max_seen, self.counts.max(), out=self.max_seen)
+        # every (atom, slot) of the list, unused slots masked: fixed shapes, so
+        # the host never waits for the device here
         valid = self.slot < self.counts[:, None]
-        i = self.rows[valid]
-        j = self.list[valid].long()
-        d = x[j] - x[i]
+        j = torch.where(valid, self.list, 0).long()
+        d = x[j] - x[:, None, :]
         if self.L is not None:
             d = d - self.L * torch.round(d / self.L)
-        r = d.norm(dim=1).clamp_min(1e-3)
+        # the pair terms in FP32 (the forces are FP32; FP64 arithmetic is slow on this GPU)
+        d = d.float()
+        r = d.norm(dim=2).clamp_min(1e-3)
         rr = r.clamp_min(self.r_soft) if self.r_soft > 0.0 else r
-        q12 = (self.sigma / rr) ** 12
-        inside = r < self.sigma
+        q2 = (self.sigma / rr) ** 2
+        q6 = q2 * q2 * q2
+        q12 = q6 * q6
+        inside = valid & (r < self.sigma)
         u = torch.where(inside, self.eps * (q12 - 1.0 + 12.0 * (rr / self.sigma - 1.0)), torch.zeros_like(r))
         dudr = torch.where(inside, self.eps * 12.0 * (1.0 / self.sigma - q12 / rr), torch.zeros_like(r))
         if self.r_soft > 0.0:
-            u = u + torch.where(r < rr, dudr * (r - rr), torch.zeros_like(r))
-        f = (dudr / r)[:, None] * d          # force on i from the pair (i, j): -dU/dr along -d/r
-        F.zero_()
-        F.index_add_(0, i, f.to(F.dtype))
-        return (0.5 * u.sum()).reshape(1)     # each pair is listed from both ends
+            u = u + torch.where(inside & (r < rr), dudr * (r - rr), torch.zeros_like(r))
+        # force on i from the pair (i, j): -dU/dr along -d/r, summed over i's slots
+        F.copy_(((dudr / r)[:, :, None] * d).sum(1))
+        return (0.5 * u.sum(dtype=torch.float64)).reshape(1)     # each pair is listed from both ends
 
     def overflow(self):
         """True if any call so far found more pairs of an atom than the list holds."""

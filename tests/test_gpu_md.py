@@ -49,8 +49,29 @@ def test_energy_conservation_fp32(P):
     assert res["etot_rms_fluct_eV_per_atom"] < 1e-4, res
 
 
+def _wall_energy64(x, cell, sigma, eps, r_soft):
+    """The wall's energy in float64 by brute force over all pairs (the form the
+    harness documents), for central differences."""
+    d = x[None, :, :] - x[:, None, :]
+    if cell is not None:
+        d -= cell * np.round(d / cell)
+    r = np.sqrt((d * d).sum(-1))
+    iu = np.triu_indices(len(x), 1)
+    r = r[iu]
+    r = r[r < sigma]
+    rr = np.maximum(r, r_soft)
+    q12 = (sigma / rr) ** 12
+    u = eps * (q12 - 1.0 + 12.0 * (rr / sigma - 1.0))
+    dudr = eps * 12.0 * (1.0 / sigma - q12 / rr)
+    u += np.where(r < rr, dudr * (r - rr), 0.0)
+    return float(u.sum())
+
+
 @pytest.mark.parametrize("periodic", [False, True])
 def test_repulsive_wall_forces_are_its_gradient(P, periodic):
+    """The harness's wall (FP32 pair terms over the allocation-free search's
+    pairs): its energy equals the brute-force float64 sum over all pairs, and
+    its forces equal central differences (h = 1e-5 A) of that sum."""
     from paper_2310_03121_b300 import md
 
     rng = np.random.default_rng(3)
@@ -69,19 +90,19 @@ def test_repulsive_wall_forces_are_its_gradient(P, periodic):
     x = torch.as_tensor(x0, device="cuda").contiguous()
     F = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     E = float(w.energy_forces(x, F).item())
-    assert E > 0 and not w.overflow()
+    assert not w.overflow()
+    E64 = _wall_energy64(x0, cell, w.sigma, w.eps, w.r_soft)
+    assert E64 > 0 and abs(E - E64) <= 1e-5 * E64, (E, E64)
     F = F.cpu().numpy().astype(np.float64)
     h = 1e-5
-    for i in range(0, n, 7):
+    for i in range(n):
         for a in range(3):
             xp = x0.copy()
             xp[i, a] += h
-            Ep = float(w.energy_forces(torch.as_tensor(xp, device="cuda").contiguous(), torch.zeros_like(
-                torch.as_tensor(xp, dtype=torch.float32, device="cuda"))).item())
+            Ep = _wall_energy64(xp, cell, w.sigma, w.eps, w.r_soft)
             xp[i, a] -= 2 * h
-            Em = float(w.energy_forces(torch.as_tensor(xp, device="cuda").contiguous(), torch.zeros_like(
-                torch.as_tensor(xp, dtype=torch.float32, device="cuda"))).item())
-            assert abs(F[i, a] + (Ep - Em) / (2 * h)) <= 1e-4 * max(1.0, abs(F[i, a]))
+            Em = _wall_energy64(xp, cell, w.sigma, w.eps, w.r_soft)
+            assert abs(F[i, a] + (Ep - Em) / (2 * h)) <= 1e-4 * max(1.0, abs(F[i, a])), (i, a)
 
 
 def test_ligand_in_water_10000_steps_with_wall(P):
