@@ -71,6 +71,7 @@ int sys_finish_pending(mlp_system* s) {
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(error flags)");
     if (sticky) {
         cudaMemset(s->ws.err_sticky, 0, sizeof(int));
+        cudaStreamSynchronize(nullptr);   // cleared before the system's (non-blocking) stream runs again
         if (sticky & 4)
             return set_error(MLP_EINVAL, "bad input (element code or ML-region index) in an earlier evaluation");
         if (sticky & 8) return set_error(MLP_ECUDA, "tensor-core network kernel error in an earlier evaluation");
@@ -823,17 +824,21 @@ int mlp_debug_forces(mlp_system* s, const float* dEdG, double* forces) {
     const size_t R = ws.rows_cap;
     const int n = s->n;
     cudaError_t e;
+    // inputs and the zeroed force sums go in on the system's own stream (a
+    // non-blocking stream: the legacy stream's work would not order with it)
+    std::vector<float> all32;
+    std::vector<__nv_bfloat16> all16;
     if (ws.dG) {
-        std::vector<float> all(R * kAevLd, 0.f);
-        for (int i = 0; i < n; ++i) std::memcpy(&all[(size_t)rows[i] * kAevLd], dEdG + (size_t)i * kAevLen, 4 * kAevLen);
-        e = cudaMemcpy(ws.dG, all.data(), 4 * all.size(), cudaMemcpyHostToDevice);
+        all32.assign(R * kAevLd, 0.f);
+        for (int i = 0; i < n; ++i) std::memcpy(&all32[(size_t)rows[i] * kAevLd], dEdG + (size_t)i * kAevLen, 4 * kAevLen);
+        e = cudaMemcpyAsync(ws.dG, all32.data(), 4 * all32.size(), cudaMemcpyHostToDevice, s->stream);
     } else {
-        std::vector<__nv_bfloat16> all(R * kAevLd, to_bf16(0.f));
+        all16.assign(R * kAevLd, to_bf16(0.f));
         for (int i = 0; i < n; ++i)
-            for (int c = 0; c < kAevLen; ++c) all[(size_t)rows[i] * kAevLd + c] = to_bf16(dEdG[(size_t)i * kAevLen + c]);
-        e = cudaMemcpy(ws.dG16, all.data(), 2 * all.size(), cudaMemcpyHostToDevice);
+            for (int c = 0; c < kAevLen; ++c) all16[(size_t)rows[i] * kAevLd + c] = to_bf16(dEdG[(size_t)i * kAevLen + c]);
+        e = cudaMemcpyAsync(ws.dG16, all16.data(), 2 * all16.size(), cudaMemcpyHostToDevice, s->stream);
     }
-    if (e == cudaSuccess) e = cudaMemset(ws.grad, 0, sizeof(double) * 3 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.grad, 0, sizeof(double) * 3 * (size_t)n, s->stream);
     if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces (inputs)");
     AevArgs aa;
     aa.n = n;
@@ -851,7 +856,8 @@ int mlp_debug_forces(mlp_system* s, const float* dEdG, double* forces) {
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces");
     std::vector<double> grad(3 * (size_t)n);
-    e = cudaMemcpy(grad.data(), ws.grad, sizeof(double) * grad.size(), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(grad.data(), ws.grad, sizeof(double) * grad.size(), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_error(e, "mlp_debug_forces (copy)");
     for (size_t q = 0; q < grad.size(); ++q) forces[q] = -grad[q];
     s->nbr_valid = false;   // the next evaluation rebuilds everything it reads

@@ -713,26 +713,26 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
     for (int c = lane; c < 3 * CAP; c += 32) fslot[c] = 0.f;
     __syncwarp();
 
-    // The angular neighbors are staged first; nothing is added to grad before
-    // the atom is known to fit the stage.
-    int mA = 0;
-    if (cnt > 0) mA = stage_angular<FAST, CAP>(nl0, mA, s);
-    if (cnt > 32) mA = stage_angular<FAST, CAP>(nl1, mA, s);
-    for (int base = 64; base < cnt; base += 32)
-        mA = stage_angular<FAST, CAP>(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i), mA, s);
-    if (mA > CAP) return false;   // warp-uniform
-    __syncwarp();
+    // The angular neighbor count decides first whether the atom fits the
+    // stage (nothing is added to grad before): from the first two chunks'
+    // ballots, plus a counting pass over any further chunks (atoms with more
+    // than 64 list entries).
+    {
+        int m = __popc(__ballot_sync(kFull, nl0.inA)) + __popc(__ballot_sync(kFull, nl1.inA));
+        for (int base = 64; base < cnt; base += 32)
+            m += __popc(__ballot_sync(kFull, load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i).inA));
+        if (m > CAP) return false;   // warp-uniform
+    }
 
     float fix = 0.f, fiy = 0.f, fiz = 0.f;   // dE/dr_i partial sums of this lane
-    // radial: one neighbor per lane. The gradient on an angular neighbor goes
-    // to its (still private) shared-memory slot, which the angular terms add
-    // to and which is flushed once; other neighbors go straight to the FP64 sums.
-    int mR = 0;
+    int mA = 0;
+    // radial: one neighbor per lane, staging the angular neighbors as it goes.
+    // The gradient on an angular neighbor goes to its (still private)
+    // shared-memory slot, which the angular terms add to and which is flushed
+    // once; other neighbors go straight to the FP64 sums.
     auto chunk = [&](const NbrLane& nl) {
-        // the lane's slot in the stage: angular neighbors were staged in list order
-        const unsigned bA = __ballot_sync(kFull, nl.inA);
-        const int pA = nl.inA ? mR + __popc(bA & lanemask_lt()) : -1;
-        mR += __popc(bA);
+        int pA;
+        mA = stage_angular<FAST, CAP>(nl, mA, s, &pA);
         if (nl.inR) {
             const float x = nl.r * (1.f / kRcRad);
             const float fc = 0.5f * M<FAST>::cpi(x) + 0.5f;
