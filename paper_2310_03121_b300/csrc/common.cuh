@@ -47,6 +47,7 @@ struct AevConsts {
     float sin_z[kAngZ];
     float hcos_z[kAngZ];   // cos_z / 2, sin_z / 2: 1 + cos(theta - theta_z) over 2 in two FMAs
     float hsin_z[kAngZ];
+    float kzcos_z[kAngZ];  // (zeta / 2) cos_z: the section factors' derivative (force kernel)
 };
 
 // Orthorhombic box: L (float), split L = Lhi + Llo, 1/L; periodic = 0 for open.

@@ -50,6 +50,7 @@ void init_constants_for_current_device() {
             h.sin_z[z] = (float)sin(Z);
             h.hcos_z[z] = (float)(0.5 * cos(Z));
             h.hsin_z[z] = (float)(0.5 * sin(Z));
+            h.kzcos_z[z] = (float)(0.5 * 14.1 * cos(Z));   // zeta = 14.1
         }
         cudaMemcpyToSymbol(c_aev, &h, sizeof(h));
     });
@@ -770,53 +771,60 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
                 const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
                 const float c = 0.95f * cos0;
                 const float sn = M<FAST>::sq(1.f - c * c);
-                const float isn = M<FAST>::rcp(sn);
-                const float hz_isn = 0.5f * kZeta * isn;
+                // With Q_z = 2 b_z^(zeta - 1): P_z = 2 b_z^zeta = Q_z b_z and
+                // dP_z/dc = (zeta / 2) Q_z sin(theta - theta_z) / sin theta
+                //         = Q_z (K_z - B sin theta_z), K_z = (zeta / 2) cos theta_z,
+                // B = (zeta / 2) c / sin theta (sin theta / sin theta cancels), no
+                // reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z).
+                const float B = 0.5f * kZeta * c * M<FAST>::rcp(sn);
                 const float rbar = 0.5f * (uj.w + uk.w);
                 const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
                 const int p = pair_index(s.sp[j], s.sp[kk]);
-                float R[kAngA], dR[kAngA];
+                float P[kAngZ], D[kAngZ];
 #pragma unroll
-                for (int aa = 0; aa < kAngA; ++aa) {
-                    const float dr = rbar - c_aev.shf_a[aa];
-                    R[aa] = M<FAST>::gauss(kEtaAng, dr);
-                    dR[aa] = -2.f * kEtaAng * dr * R[aa];
+                for (int zz = 0; zz < kAngZ / 2; ++zz) {
+                    // sections zz and 7 - zz: theta_(7-zz) = pi - theta_zz (cos flips, sin stays)
+                    const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f), x = c * c_aev.hcos_z[zz];
+                    const float b0 = y + x, b1 = y - x;
+                    float Q0, Q1;
+                    if (FAST) {
+                        Q0 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b0), 1.f));
+                        Q1 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b1), 1.f));
+                    } else {
+                        Q0 = 2.f * M<false>::pw(b0, kZeta - 1.f);
+                        Q1 = 2.f * M<false>::pw(b1, kZeta - 1.f);
+                    }
+                    const float t = B * c_aev.sin_z[zz];
+                    P[zz] = Q0 * b0;
+                    P[kAngZ - 1 - zz] = Q1 * b1;
+                    D[zz] = Q0 * (c_aev.kzcos_z[zz] - t);
+                    D[kAngZ - 1 - zz] = -Q1 * (c_aev.kzcos_z[zz] + t);
                 }
-                // U_z = sum_a g[a][z] R_a and V_z = sum_a g[a][z] dR_a, the row of
-                // dE/dG read as two 4-column groups per shift
-                float U[kAngZ], V[kAngZ];
+                // Contracted over the sections first: W_a = sum_z g[a][z] P_z and
+                // Wd_a = sum_z g[a][z] dP_z/dc (the pair's dE/dG row read as two
+                // 4-column groups per shift); then T1 = sum_a W_a R_a, Sc = sum_a
+                // Wd_a R_a, T2 = sum_a W_a dR_a/drbar with dR_a/drbar = -2 eta
+                // (rbar - A_a) R_a.
+                float Sc = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
                 for (int aa = 0; aa < kAngA; ++aa) {
                     const float4 g0 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa));
                     const float4 g1 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa + 1));
                     const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                    float W = 0.f, Wd = 0.f;
 #pragma unroll
                     for (int z = 0; z < kAngZ; ++z) {
-                        U[z] = aa == 0 ? gg[z] * R[0] : fmaf(gg[z], R[aa], U[z]);
-                        V[z] = aa == 0 ? gg[z] * dR[0] : fmaf(gg[z], dR[aa], V[z]);
+                        W = fmaf(gg[z], P[z], W);
+                        Wd = fmaf(gg[z], D[z], Wd);
                     }
+                    const float dr = rbar - c_aev.shf_a[aa];
+                    const float Ra = M<FAST>::gauss(kEtaAng, dr);
+                    const float WR = W * Ra;
+                    T1 += WR;
+                    T2 = fmaf(WR, dr, T2);
+                    Sc = fmaf(Wd, Ra, Sc);
                 }
-                float Sc = 0.f, T1 = 0.f, T2 = 0.f;
-#pragma unroll
-                for (int z = 0; z < kAngZ; ++z) {
-                    // b = (1 + cos(theta - theta_z)) / 2, sm = sin(theta - theta_z)
-                    const float b = fmaf(c, c_aev.hcos_z[z], fmaf(sn, c_aev.hsin_z[z], 0.5f));
-                    const float sm = fmaf(sn, c_aev.cos_z[z], -c * c_aev.sin_z[z]);
-                    float Pz, dPdc;
-                    if (FAST) {
-                        // Q = 2 b^(zeta - 1): Pz = 2 b^zeta = Q b and dPz/dc = (zeta / 2) Q sm / sin,
-                        // no reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z)
-                        const float Q = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b), 1.f));
-                        Pz = Q * b;
-                        dPdc = hz_isn * Q * sm;
-                    } else {
-                        Pz = 2.f * M<false>::pw(b, kZeta);
-                        dPdc = 0.5f * kZeta * Pz * sm * M<false>::rcp(b) * isn;
-                    }
-                    Sc = fmaf(dPdc, U[z], Sc);
-                    T1 = fmaf(Pz, U[z], T1);
-                    T2 = fmaf(Pz, V[z], T2);
-                }
+                T2 *= -2.f * kEtaAng;
                 const float f = fj * fk;
                 Sc *= f;
                 const float Srj = 0.5f * f * T2 + dfj * fk * T1;
