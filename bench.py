@@ -95,7 +95,8 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []   # (host time received, csv line)
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -106,10 +107,22 @@ class Clocks:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a while to start: wait (bounded) for its first sample,
+        # so that the samples cover the timed region that follows
+        t_end = time.monotonic() + 10.0
+        while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.monotonic(), ln.strip()))
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -122,7 +135,13 @@ class Clocks:
         time.sleep(0.05)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # the samples taken during the timed region (one sampling period of slack
+        # at its end), else all of them
+        lines = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            inside = [x for x in self.lines if self.t0 <= x[0] <= self.t1 + 0.06]
+            lines = inside or self.lines
+        for _, ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -135,7 +154,8 @@ class Clocks:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": 50,
+                "timed_region_s": (self.t1 - self.t0) if self.t0 is not None and self.t1 is not None else None}
 
 
 def measured_peaks():
@@ -282,6 +302,7 @@ def measure_device(P, W, stream, args, prec, dev, ws, local, steps, warmup, prof
     launches0 = P.launch_count()
     clk = Clocks(local)
     clk.start()
+    clk.begin()
     times = []
     for i in range(steps):
         flush.zero_()                      # L2 flush between timed steps (outside the events)
@@ -292,6 +313,7 @@ def measure_device(P, W, stream, args, prec, dev, ws, local, steps, warmup, prof
             b.sync()
         times.append(s_ev.elapsed_time(e_ev))
     barrier()
+    clk.end()
     clocks = clk.stop()
     launches = P.launch_count() - launches0
     # per-kernel durations: the same step on one stream (so that an event pair

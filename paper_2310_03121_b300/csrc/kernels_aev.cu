@@ -15,20 +15,22 @@
 //     (displacement, distance, element, cutoff value in registers); only the
 //     neighbors within 3.5 A are staged in shared memory, as unit vector,
 //     distance, 1/r and cutoff values (the angular sub-list);
-//   * radial (forward): lane = (half, k), 16 shift lanes x 2 neighbors taken
-//     from the lanes that loaded them by shuffles; each lane owns its own
-//     accumulator column per element -> no atomics, fixed order;
+//   * radial (forward): four neighbors per step, taken from the lanes that
+//     loaded them by shuffles, a quarter-warp each with two shifts per lane;
+//     each lane owns its accumulator columns per element and quarter -> no
+//     atomics, fixed order;
 //   * angular: pairs are taken 32 at a time: one pair per lane computes its
 //     8 angle factors and 4 distance factors into shared memory, then lane
 //     (a, z) adds the products, pair by pair, to its own column 32 p + 8 a + z
 //     (conflict-free, fixed order -> deterministic).
 // The backward recomputes the terms with their derivatives and contracts
-// them with dE/dG (staged in shared memory): radial one neighbor per lane
-// (16 unrolled exponentials), angular one pair per lane with its 4 distance and 8 angle factors in registers (the angular
-// block of dE/dG is staged in rows of 33 floats per element pair so that
-// lanes reading the same column of different pair rows do not share a bank). Gradients on
-// neighbors go to FP64 global sums (radial: per neighbor; angular:
-// accumulated per angular neighbor in shared memory first).
+// them with dE/dG (staged in shared memory as FP32, XOR-swizzled rows):
+// radial one neighbor per lane (16 unrolled exponentials), angular one pair
+// per lane with its 4 distance and 8 angle factors in registers. Gradients
+// on neighbors go to FP64 global sums: radial ones per neighbor; angular
+// ones summed per angular neighbor first (in the registers of the lane that
+// owns the neighbor when an atom has at most 32 of them, else in shared
+// memory) and added once.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -133,13 +135,14 @@ struct AngStage {
 
 // Angular pairs are processed in super-chunks of kSC pairs: one pair per
 // lane computes its 8 section factors and 4 distance factors into rows of
-// kFacRow floats (the rows of different sections start on different banks:
-// 34 mod 32 = 2, and two consecutive pairs of a row load as one 8-byte word),
-// then lane (a, z) sums column 8 a + z of every element-pair block of the
-// super-chunk. 32 pairs per super-chunk (measured 4% faster than 64: the
-// smaller stage lets 32 instead of 26 one-warp blocks share an SM).
+// kFacRow floats (rows start 16-byte aligned, on banks 4 apart: the eight
+// lanes of a quarter-warp reading four consecutive pairs of eight section
+// rows cover all 32 banks), then lane (a, z) sums column 8 a + z of every
+// element-pair block of the super-chunk. 32 pairs per super-chunk (measured
+// 4% faster than 64: the smaller stage lets 32 instead of 26 one-warp blocks
+// share an SM).
 constexpr int kSC = 32;
-constexpr int kFacRow = kSC + 2;
+constexpr int kFacRow = kSC + 4;
 
 // Forward scratch of one warp (after its angular stage).
 template <int CAP>
@@ -175,8 +178,9 @@ __host__ __device__ constexpr size_t force_smem_per_warp() { return round16(size
 static_assert(aev_smem_per_warp<kAngCap>() % 16 == 0 && force_smem_per_warp<kAngCap>() % 16 == 0 &&
               force_smem_per_warp<kAngCapBig>() % 16 == 0, "per-warp shared regions must be 16-byte aligned");
 static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AEV row start on 16 bytes");
-static_assert(offsetof(AevScratch<kAngCap>, pfT) % 8 == 0 && offsetof(AevScratch<kAngCap>, rfT) % 8 == 0 &&
-              kFacRow % 2 == 0, "factor rows load two floats at a time");
+static_assert(offsetof(AevScratch<kAngCap>, pfT) % 16 == 0 && offsetof(AevScratch<kAngCap>, rfT) % 16 == 0 &&
+              offsetof(AevScratch<kAngCapBig>, pfT) % 16 == 0 && offsetof(AevScratch<kAngCapBig>, rfT) % 16 == 0 &&
+              kFacRow % 4 == 0 && kSC == 32, "factor rows load four floats at a time; one pair per lane");
 static_assert(offsetof(AevScratch<kAngCap>, accR) % 8 == 0, "radial accumulators are read two at a time");
 static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsRadStride == 16 && kGsAngStride == 32,
               "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row)");
@@ -488,90 +492,90 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
         const int z = lane & 7, aa = lane >> 3;
         const float* pz = X.pfT + z * kFacRow;
         const float* ra = X.rfT + aa * kFacRow;
+        // The angular columns start as zeros (absent blocks stay zero); each
+        // present block's 32 columns are written once, when its last pair has
+        // been added.
+        zero_cols(out, out_lo, kRadLen, kAevLd, lane);
+        __syncwarp();
         float acc = 0.f;
-        int bi = 0, next_p = 0;
         for (int sb = 0; sb < P; sb += kSC) {
-            const int se = min(P, sb + kSC);
-            for (int base = sb; base < se; base += 32) {
-                // block of pair e = base + lane: blocks starting before base, plus
-                // those starting inside this chunk at or before the lane
-                const unsigned before = __ballot_sync(kFull, my_off < base);
-                const unsigned starts = __reduce_or_sync(
-                    kFull, (lane < np && my_off >= base && my_off < base + 32) ? (1u << (my_off - base)) : 0u);
-                const int b = max(0, __popc(before) - 1 + __popc(starts & lanemask_le()));
-                const int off_b = __shfl_sync(kFull, my_off, b);
-                const int dsc = __shfl_sync(kFull, my_desc, b);
-                const int e = base + lane;
-                if (e < se) {
-                    const int l = e - off_b;
-                    const int g1 = dsc & 255, g2 = (dsc >> 8) & 255, cdiv = dsc >> 16;
-                    const int q = small_div<(CAP > 64)>(l, cdiv);
-                    const int r = l - q * cdiv;
-                    int jj, kk;
-                    if (g1 != g2) {   // two groups: pair (q, r) of the rectangle
-                        jj = g1 + q;
-                        kk = g2 + r;
-                    } else {          // one group of cdiv: rotation q + 1, position r
-                        const int x = r + q + 1;
-                        jj = g1 + r;
-                        kk = g1 + (x >= cdiv ? x - cdiv : x);
-                    }
-                    const int J = X.ord[jj], K = X.ord[kk];
-                    const float4 uj = s.u[J], uk = s.u[K];
-                    const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
-                    const float sn = M<FAST>::sq(1.f - c * c);
-                    const float f2 = 2.f * s.fc[J] * s.fc[K];
-                    // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
-                    const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
-                    const int col = e - sb;
-                    // sections z and 7 - z share sin: theta_(7-z) = pi - theta_z
-#pragma unroll
-                    for (int zz = 0; zz < kAngZ / 2; ++zz) {
-                        const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f);
-                        const float b0 = fmaf(c, c_aev.hcos_z[zz], y);
-                        const float b1 = fmaf(-c, c_aev.hcos_z[zz], y);
-                        X.pfT[zz * kFacRow + col] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b0), lf2))
-                                                         : f2 * M<false>::pw(b0, kZeta);
-                        X.pfT[(kAngZ - 1 - zz) * kFacRow + col] =
-                            FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b1), lf2)) : f2 * M<false>::pw(b1, kZeta);
-                    }
-                    const float rbar = 0.5f * (uj.w + uk.w);
-#pragma unroll
-                    for (int q4 = 0; q4 < kAngA; ++q4)
-                        X.rfT[q4 * kFacRow + col] = M<FAST>::gauss(kEtaAng, rbar - c_aev.shf_a[q4]);
+            const int n = min(kSC, P - sb);
+            // block of pair e = sb + lane: blocks starting before sb, plus those
+            // starting inside this super-chunk at or before the lane
+            const unsigned before = __ballot_sync(kFull, my_off < sb);
+            const unsigned starts = __reduce_or_sync(
+                kFull, (lane < np && my_off >= sb && my_off < sb + 32) ? (1u << (my_off - sb)) : 0u);
+            const int b = max(0, __popc(before) - 1 + __popc(starts & lanemask_le()));
+            const int off_b = __shfl_sync(kFull, my_off, b);
+            const int end_b = __shfl_sync(kFull, my_end, b);
+            const int dsc = __shfl_sync(kFull, my_desc, b);
+            const int p_b = __shfl_sync(kFull, my_p, b);
+            const int e = sb + lane;
+            bool last = false;   // pair e is the last of its block
+            if (lane < n) {
+                const int l = e - off_b;
+                const int g1 = dsc & 255, g2 = (dsc >> 8) & 255, cdiv = dsc >> 16;
+                const int q = small_div<(CAP > 64)>(l, cdiv);
+                const int r = l - q * cdiv;
+                int jj, kk;
+                if (g1 != g2) {   // two groups: pair (q, r) of the rectangle
+                    jj = g1 + q;
+                    kk = g2 + r;
+                } else {          // one group of cdiv: rotation q + 1, position r
+                    const int x = r + q + 1;
+                    jj = g1 + r;
+                    kk = g1 + (x >= cdiv ? x - cdiv : x);
                 }
+                const int J = X.ord[jj], K = X.ord[kk];
+                const float4 uj = s.u[J], uk = s.u[K];
+                const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
+                const float sn = M<FAST>::sq(1.f - c * c);
+                const float f2 = 2.f * s.fc[J] * s.fc[K];
+                // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
+                const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
+                // sections z and 7 - z share sin: theta_(7-z) = pi - theta_z
+#pragma unroll
+                for (int zz = 0; zz < kAngZ / 2; ++zz) {
+                    const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f);
+                    const float b0 = fmaf(c, c_aev.hcos_z[zz], y);
+                    const float b1 = fmaf(-c, c_aev.hcos_z[zz], y);
+                    X.pfT[zz * kFacRow + lane] = FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b0), lf2))
+                                                      : f2 * M<false>::pw(b0, kZeta);
+                    X.pfT[(kAngZ - 1 - zz) * kFacRow + lane] =
+                        FAST ? M<true>::ex2(fmaf(kZeta, M<true>::lg2(b1), lf2)) : f2 * M<false>::pw(b1, kZeta);
+                }
+                const float rbar = 0.5f * (uj.w + uk.w);
+#pragma unroll
+                for (int q4 = 0; q4 < kAngA; ++q4)
+                    X.rfT[q4 * kFacRow + lane] = M<FAST>::gauss(kEtaAng, rbar - c_aev.shf_a[q4]);
+                last = e + 1 == end_b;
             }
+            const unsigned ends = __ballot_sync(kFull, last);
             __syncwarp();
-            // the blocks of this super-chunk, in order; the last one may continue
-            // into the next super-chunk (its sum stays in acc)
-            while (bi < np) {
-                const int b0 = __shfl_sync(kFull, my_off, bi), b1 = __shfl_sync(kFull, my_end, bi);
-                int q = max(b0, sb) - sb;
-                const int q1 = min(b1, se) - sb;
-                if (q & 1) {
-                    acc = fmaf(pz[q], ra[q], acc);
-                    ++q;
+            // Lane (a, z) adds the super-chunk's products in pair order, four
+            // pairs per pair of 16-byte loads; at a block's last pair the sum
+            // goes to the block's column and restarts (the last block may
+            // continue into the next super-chunk; its sum stays in acc).
+            // Factors past n are stale, but no block ends there: what they add
+            // is never written.
+#pragma unroll
+            for (int q = 0; q < kSC; q += 4) {
+                if (q >= n) break;   // warp-uniform
+                const float4 p4 = *reinterpret_cast<const float4*>(pz + q);
+                const float4 r4 = *reinterpret_cast<const float4*>(ra + q);
+                const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    acc = fmaf(pv[t], rv[t], acc);
+                    if (ends & (1u << (q + t))) {   // warp-uniform
+                        const int pp = __shfl_sync(kFull, p_b, q + t);
+                        put_g(out, out_lo, kRadLen + 32 * pp + lane, acc);
+                        acc = 0.f;
+                    }
                 }
-#pragma unroll 2
-                for (; q + 1 < q1; q += 2) {
-                    const float2 p2 = *reinterpret_cast<const float2*>(pz + q);
-                    const float2 r2 = *reinterpret_cast<const float2*>(ra + q);
-                    acc = fmaf(p2.x, r2.x, acc);
-                    acc = fmaf(p2.y, r2.y, acc);
-                }
-                if (q < q1) acc = fmaf(pz[q], ra[q], acc);
-                if (b1 > se) break;
-                const int p = __shfl_sync(kFull, my_p, bi);
-                if (next_p < p) zero_cols(out, out_lo, kRadLen + 32 * next_p, kRadLen + 32 * p, lane);
-                put_g(out, out_lo, kRadLen + 32 * p + lane, acc);
-                next_p = p + 1;
-                acc = 0.f;
-                ++bi;
             }
             __syncwarp();   // the next super-chunk overwrites the factors
         }
-        // the absent blocks after the last present one, and the row's padding
-        zero_cols(out, out_lo, kRadLen + 32 * next_p, kAevLd, lane);
     }
     // radial block (four quarters, added in a fixed order)
     for (int c = lane; c < kRadLen; c += 32) {
@@ -711,7 +715,6 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
             }
         }
     }
-    for (int c = lane; c < 3 * CAP; c += 32) fslot[c] = 0.f;
     __syncwarp();
 
     // The angular neighbor count decides first whether the atom fits the
@@ -728,9 +731,10 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
     float fix = 0.f, fiy = 0.f, fiz = 0.f;   // dE/dr_i partial sums of this lane
     int mA = 0;
     // radial: one neighbor per lane, staging the angular neighbors as it goes.
-    // The gradient on an angular neighbor goes to its (still private)
-    // shared-memory slot, which the angular terms add to and which is flushed
-    // once; other neighbors go straight to the FP64 sums.
+    // The gradient on an angular neighbor goes to its shared-memory slot
+    // (every staged slot is written here: r < 3.5 A implies r < 5.1 A), added
+    // to its angular gradient and flushed once; other neighbors go straight
+    // to the FP64 sums.
     auto chunk = [&](const NbrLane& nl) {
         int pA;
         mA = stage_angular<FAST, CAP>(nl, mA, s, &pA);
@@ -759,98 +763,152 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
     for (int base = 64; base < cnt; base += 32) chunk(load_neighbor<FAST>(a, row, base + lane, cnt, hi_i, lo_i));
     __syncwarp();
 
-    // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers
-    {
+    // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers.
+    // pair_grad: the pair's gradients on j and k (and minus their sum on i).
+    auto pair_grad = [&](int j, int kk, float3& gj, float3& gk) {
+        const float4 uj = s.u[j], uk = s.u[kk];
+        const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+        const float c = 0.95f * cos0;
+        const float sn = M<FAST>::sq(1.f - c * c);
+        // With Q_z = 2 b_z^(zeta - 1): P_z = 2 b_z^zeta = Q_z b_z and
+        // dP_z/dc = (zeta / 2) Q_z sin(theta - theta_z) / sin theta
+        //         = Q_z (K_z - B sin theta_z), K_z = (zeta / 2) cos theta_z,
+        // B = (zeta / 2) c / sin theta (sin theta / sin theta cancels), no
+        // reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z).
+        const float B = 0.5f * kZeta * c * M<FAST>::rcp(sn);
+        const float rbar = 0.5f * (uj.w + uk.w);
+        const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
+        const int p = pair_index(s.sp[j], s.sp[kk]);
+        float P[kAngZ], D[kAngZ];
+#pragma unroll
+        for (int zz = 0; zz < kAngZ / 2; ++zz) {
+            // sections zz and 7 - zz: theta_(7-zz) = pi - theta_zz (cos flips, sin stays)
+            const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f), x = c * c_aev.hcos_z[zz];
+            const float b0 = y + x, b1 = y - x;
+            float Q0, Q1;
+            if (FAST) {
+                Q0 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b0), 1.f));
+                Q1 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b1), 1.f));
+            } else {
+                Q0 = 2.f * M<false>::pw(b0, kZeta - 1.f);
+                Q1 = 2.f * M<false>::pw(b1, kZeta - 1.f);
+            }
+            const float t = B * c_aev.sin_z[zz];
+            P[zz] = Q0 * b0;
+            P[kAngZ - 1 - zz] = Q1 * b1;
+            D[zz] = Q0 * (c_aev.kzcos_z[zz] - t);
+            D[kAngZ - 1 - zz] = -Q1 * (c_aev.kzcos_z[zz] + t);
+        }
+        // Contracted over the sections first: W_a = sum_z g[a][z] P_z and
+        // Wd_a = sum_z g[a][z] dP_z/dc (the pair's dE/dG row read as two
+        // 4-column groups per shift); then T1 = sum_a W_a R_a, Sc = sum_a
+        // Wd_a R_a, T2 = sum_a W_a dR_a/drbar with dR_a/drbar = -2 eta
+        // (rbar - A_a) R_a.
+        float Sc = 0.f, T1 = 0.f, T2 = 0.f;
+#pragma unroll
+        for (int aa = 0; aa < kAngA; ++aa) {
+            const float4 g0 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa));
+            const float4 g1 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa + 1));
+            const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            float W = 0.f, Wd = 0.f;
+#pragma unroll
+            for (int z = 0; z < kAngZ; ++z) {
+                W = fmaf(gg[z], P[z], W);
+                Wd = fmaf(gg[z], D[z], Wd);
+            }
+            const float dr = rbar - c_aev.shf_a[aa];
+            const float Ra = M<FAST>::gauss(kEtaAng, dr);
+            const float WR = W * Ra;
+            T1 += WR;
+            T2 = fmaf(WR, dr, T2);
+            Sc = fmaf(Wd, Ra, Sc);
+        }
+        T2 *= -2.f * kEtaAng;
+        const float f = fj * fk;
+        Sc *= f;
+        const float Srj = 0.5f * f * T2 + dfj * fk * T1;
+        const float Srk = 0.5f * f * T2 + fj * dfk * T1;
+        // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k
+        const float aj = 0.95f * Sc * s.invr[j], ak = 0.95f * Sc * s.invr[kk];
+        const float gjx = aj * (uk.x - cos0 * uj.x) + Srj * uj.x;
+        const float gjy = aj * (uk.y - cos0 * uj.y) + Srj * uj.y;
+        const float gjz = aj * (uk.z - cos0 * uj.z) + Srj * uj.z;
+        const float gkx = ak * (uj.x - cos0 * uk.x) + Srk * uk.x;
+        const float gky = ak * (uj.y - cos0 * uk.y) + Srk * uk.y;
+        const float gkz = ak * (uj.z - cos0 * uk.z) + Srk * uk.z;
+        gj = make_float3(gjx, gjy, gjz);
+        gk = make_float3(gkx, gky, gkz);
+        fix -= gjx + gkx;
+        fiy -= gjy + gky;
+        fiz -= gjz + gkz;
+    };
+    if (mA <= 32) {   // warp-uniform
+        // Slot owners, no shared-memory atomics: lane l = r m + j of group
+        // r < g = 32 / m owns slot j. Group r takes rotations t = r + 1,
+        // g + r + 1, ... (pairs (j, (j + t) mod m); for even m the last
+        // rotation, t = m / 2, only for j < m / 2: every pair once). The
+        // gradient on j stays in the lane's registers; the one on k goes to
+        // k's owner in the same group (same t) by a shuffle. The groups' sums
+        // of a slot are added into group 0 at the end (fixed order).
+        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+        if (mA >= 2) {
+            const int g = 32 / mA, r = lane / mA, j = lane - r * mA;
+            const int tf = (mA - 1) >> 1, T = (mA & 1) ? tf : tf + 1;
+            for (int rho = 0; rho < T; rho += g) {
+                const int t = rho + r + 1;
+                const bool act = r < g && (t <= tf || (t == T && j < (mA >> 1)));
+                float3 gj = make_float3(0.f, 0.f, 0.f), gk = gj;
+                if (act) {
+                    const int kk = j + t >= mA ? j + t - mA : j + t;
+                    pair_grad(j, kk, gj, gk);
+                }
+                // the owner of slot j receives from the lane whose k is j (its j is j - t)
+                const int src = r * mA + (j >= t ? j - t : j - t + mA);
+                Fx += gj.x + __shfl_sync(kFull, gk.x, src);
+                Fy += gj.y + __shfl_sync(kFull, gk.y, src);
+                Fz += gj.z + __shfl_sync(kFull, gk.z, src);
+            }
+            const float ox = Fx, oy = Fy, oz = Fz;
+            for (int q = 1; q < g; ++q) {
+                Fx += __shfl_sync(kFull, ox, lane + q * mA);
+                Fy += __shfl_sync(kFull, oy, lane + q * mA);
+                Fz += __shfl_sync(kFull, oz, lane + q * mA);
+            }
+        }
+        if (lane < mA) {   // slot lane: its angular sum plus its radial gradient
+            const int jj = s.idx[lane];
+            atomicAdd(&grad[3 * (size_t)jj], (double)(fslot[3 * lane] + Fx));
+            atomicAdd(&grad[3 * (size_t)jj + 1], (double)(fslot[3 * lane + 1] + Fy));
+            atomicAdd(&grad[3 * (size_t)jj + 2], (double)(fslot[3 * lane + 2] + Fz));
+        }
+    } else {
+        // more than 32 slots: pairs packed 32 per pass in rotation order, the
+        // gradients added to the slots in shared memory, flushed once
         const int P = mA * (mA - 1) / 2;
         PairIt it;
         it.init(mA, lane);
         for (int base = 0; base < P; base += 32) {
             if (base + lane < P) {
                 const int j = it.j, kk = it.k();
-                const float4 uj = s.u[j], uk = s.u[kk];
-                const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-                const float c = 0.95f * cos0;
-                const float sn = M<FAST>::sq(1.f - c * c);
-                // With Q_z = 2 b_z^(zeta - 1): P_z = 2 b_z^zeta = Q_z b_z and
-                // dP_z/dc = (zeta / 2) Q_z sin(theta - theta_z) / sin theta
-                //         = Q_z (K_z - B sin theta_z), K_z = (zeta / 2) cos theta_z,
-                // B = (zeta / 2) c / sin theta (sin theta / sin theta cancels), no
-                // reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z).
-                const float B = 0.5f * kZeta * c * M<FAST>::rcp(sn);
-                const float rbar = 0.5f * (uj.w + uk.w);
-                const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
-                const int p = pair_index(s.sp[j], s.sp[kk]);
-                float P[kAngZ], D[kAngZ];
-#pragma unroll
-                for (int zz = 0; zz < kAngZ / 2; ++zz) {
-                    // sections zz and 7 - zz: theta_(7-zz) = pi - theta_zz (cos flips, sin stays)
-                    const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f), x = c * c_aev.hcos_z[zz];
-                    const float b0 = y + x, b1 = y - x;
-                    float Q0, Q1;
-                    if (FAST) {
-                        Q0 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b0), 1.f));
-                        Q1 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b1), 1.f));
-                    } else {
-                        Q0 = 2.f * M<false>::pw(b0, kZeta - 1.f);
-                        Q1 = 2.f * M<false>::pw(b1, kZeta - 1.f);
-                    }
-                    const float t = B * c_aev.sin_z[zz];
-                    P[zz] = Q0 * b0;
-                    P[kAngZ - 1 - zz] = Q1 * b1;
-                    D[zz] = Q0 * (c_aev.kzcos_z[zz] - t);
-                    D[kAngZ - 1 - zz] = -Q1 * (c_aev.kzcos_z[zz] + t);
-                }
-                // Contracted over the sections first: W_a = sum_z g[a][z] P_z and
-                // Wd_a = sum_z g[a][z] dP_z/dc (the pair's dE/dG row read as two
-                // 4-column groups per shift); then T1 = sum_a W_a R_a, Sc = sum_a
-                // Wd_a R_a, T2 = sum_a W_a dR_a/drbar with dR_a/drbar = -2 eta
-                // (rbar - A_a) R_a.
-                float Sc = 0.f, T1 = 0.f, T2 = 0.f;
-#pragma unroll
-                for (int aa = 0; aa < kAngA; ++aa) {
-                    const float4 g0 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa));
-                    const float4 g1 = *reinterpret_cast<const float4*>(gs + gs_ang(p, 2 * aa + 1));
-                    const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-                    float W = 0.f, Wd = 0.f;
-#pragma unroll
-                    for (int z = 0; z < kAngZ; ++z) {
-                        W = fmaf(gg[z], P[z], W);
-                        Wd = fmaf(gg[z], D[z], Wd);
-                    }
-                    const float dr = rbar - c_aev.shf_a[aa];
-                    const float Ra = M<FAST>::gauss(kEtaAng, dr);
-                    const float WR = W * Ra;
-                    T1 += WR;
-                    T2 = fmaf(WR, dr, T2);
-                    Sc = fmaf(Wd, Ra, Sc);
-                }
-                T2 *= -2.f * kEtaAng;
-                const float f = fj * fk;
-                Sc *= f;
-                const float Srj = 0.5f * f * T2 + dfj * fk * T1;
-                const float Srk = 0.5f * f * T2 + fj * dfk * T1;
-                // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k
-                const float aj = 0.95f * Sc * s.invr[j], ak = 0.95f * Sc * s.invr[kk];
-                const float gjx = aj * (uk.x - cos0 * uj.x) + Srj * uj.x;
-                const float gjy = aj * (uk.y - cos0 * uj.y) + Srj * uj.y;
-                const float gjz = aj * (uk.z - cos0 * uj.z) + Srj * uj.z;
-                const float gkx = ak * (uj.x - cos0 * uk.x) + Srk * uk.x;
-                const float gky = ak * (uj.y - cos0 * uk.y) + Srk * uk.y;
-                const float gkz = ak * (uj.z - cos0 * uk.z) + Srk * uk.z;
-                atomicAdd(&fslot[3 * j], gjx);
-                atomicAdd(&fslot[3 * j + 1], gjy);
-                atomicAdd(&fslot[3 * j + 2], gjz);
-                atomicAdd(&fslot[3 * kk], gkx);
-                atomicAdd(&fslot[3 * kk + 1], gky);
-                atomicAdd(&fslot[3 * kk + 2], gkz);
-                fix -= gjx + gkx;
-                fiy -= gjy + gky;
-                fiz -= gjz + gkz;
+                float3 gj, gk;
+                pair_grad(j, kk, gj, gk);
+                atomicAdd(&fslot[3 * j], gj.x);
+                atomicAdd(&fslot[3 * j + 1], gj.y);
+                atomicAdd(&fslot[3 * j + 2], gj.z);
+                atomicAdd(&fslot[3 * kk], gk.x);
+                atomicAdd(&fslot[3 * kk + 1], gk.y);
+                atomicAdd(&fslot[3 * kk + 2], gk.z);
             }
             it.advance(32);
         }
+        __syncwarp();
+        for (int q = lane; q < mA; q += 32) {
+            const int jj = s.idx[q];
+            atomicAdd(&grad[3 * (size_t)jj], (double)fslot[3 * q]);
+            atomicAdd(&grad[3 * (size_t)jj + 1], (double)fslot[3 * q + 1]);
+            atomicAdd(&grad[3 * (size_t)jj + 2], (double)fslot[3 * q + 2]);
+        }
     }
-    __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fix += __shfl_xor_sync(kFull, fix, o);
@@ -861,12 +919,6 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         atomicAdd(&grad[3 * (size_t)i], (double)fix);
         atomicAdd(&grad[3 * (size_t)i + 1], (double)fiy);
         atomicAdd(&grad[3 * (size_t)i + 2], (double)fiz);
-    }
-    for (int q = lane; q < mA; q += 32) {
-        const int jj = s.idx[q];
-        atomicAdd(&grad[3 * (size_t)jj], (double)fslot[3 * q]);
-        atomicAdd(&grad[3 * (size_t)jj + 1], (double)fslot[3 * q + 1]);
-        atomicAdd(&grad[3 * (size_t)jj + 2], (double)fslot[3 * q + 2]);
     }
     return true;
 }
