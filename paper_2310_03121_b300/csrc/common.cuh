@@ -33,10 +33,11 @@ constexpr float kZeta = 14.1f;
 constexpr float kCeluAlpha = 0.1f;
 
 // Angular neighbors (within 3.5 A) staged per atom by the AEV and force
-// kernels: up to kAngCap in the main launches; atoms with more are handed to
-// a second launch that stages up to kAngCapBig (more than any neighbor list
-// holds: rows have at most 256 entries).
-constexpr int kAngCap = 60;
+// kernels: up to kAngCap in the main launches (the force kernel's fast path,
+// one slot owner per lane, takes atoms with up to 32); atoms with more are
+// handed to a second launch that stages up to kAngCapBig (more than any
+// neighbor list holds: rows have at most 256 entries).
+constexpr int kAngCap = 48;
 constexpr int kAngCapBig = 256;
 
 // Device constant tables, filled once per device by init_constants().
@@ -69,8 +70,8 @@ struct Grid {
 };
 
 // Counters reset at the start of every evaluation.
-struct Counters {
-    int species[8];        // atoms per element
+struct alignas(16) Counters {
+    int species[8];        // atoms per element (read as two 16-byte words)
     int nbr_overflow;      // largest neighbor count seen above capacity (0 = fine)
     int ang_overflow;      // largest angular neighbor count above kAngCapBig (0 = fine)
     int bad_species;       // bad input: 1 element code outside [0, 7), 2 molecule offsets, 4 ML-region index
@@ -96,6 +97,20 @@ __device__ __forceinline__ int padded_rows(int c) { return ((c + kTileRows - 1) 
 __device__ __forceinline__ int row_base(const int* counts, int s) {
     int b = 0;
     for (int q = 0; q < s; ++q) b += padded_rows(counts[q]);
+    return b;
+}
+// The same for a kernel that loads the element counts as two 16-byte words
+// together with the atom's own data (one memory round trip instead of two:
+// the prefix over the elements below s is formed in registers).
+__device__ __forceinline__ void load_counts(const Counters* ctr, int4& c0, int4& c1) {
+    c0 = reinterpret_cast<const int4*>(ctr->species)[0];
+    c1 = reinterpret_cast<const int4*>(ctr->species)[1];
+}
+__device__ __forceinline__ int row_base(const int4& c0, const int4& c1, int s) {
+    const int c[kNSpecies] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
+    int b = 0;
+#pragma unroll
+    for (int q = 0; q < kNSpecies; ++q) b += q < s ? padded_rows(c[q]) : 0;
     return b;
 }
 

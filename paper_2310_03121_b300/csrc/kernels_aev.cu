@@ -33,6 +33,8 @@
 // memory) and added once.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -161,18 +163,18 @@ template <int CAP>
 __host__ __device__ constexpr size_t aev_smem_per_warp() { return round16(sizeof(AngStage<CAP>) + sizeof(AevScratch<CAP>)); }
 static_assert(sizeof(AngStage<kAngCap>) % 16 == 0 && sizeof(AngStage<kAngCapBig>) % 16 == 0,
               "AngStage must keep the per-warp regions 16-byte aligned");
-// dE/dG staged for the backward as FP32: the radial block in rows of 16
-// floats per element, the angular block in rows of 32 floats per element
-// pair, read as 16-byte groups of four columns. Group g of row q is stored
-// at group g ^ (q & 7) (angular) or g ^ (q & 3) (radial), so that lanes
-// reading the same group of rows of different element pairs (elements) hit
-// different banks without padding the rows.
+// dE/dG staged for the backward as FP32, read as 16-byte groups of four
+// columns: the radial block in rows of 16 floats per element, group g of row
+// q stored at group g ^ (q & 3); the angular block in rows of 36 floats per
+// element pair (32 columns and 4 of padding: rows start 4 banks apart), so
+// that lanes reading the same group of rows of different element pairs hit
+// different banks and every group sits at a fixed offset from its row.
 constexpr int kGsRadStride = 16;
-constexpr int kGsAngStride = 32;
+constexpr int kGsAngStride = 36;
 constexpr int kGsRad = kNSpecies * kGsRadStride;
 constexpr int kGsFloats = kGsRad + kNPairs * kGsAngStride;
 __device__ __forceinline__ int gs_rad(int s, int g) { return kGsRadStride * s + 4 * (g ^ (s & 3)); }
-__device__ __forceinline__ int gs_ang(int p, int g) { return kGsRad + kGsAngStride * p + 4 * (g ^ (p & 7)); }
+__device__ __forceinline__ int gs_ang(int p, int g) { return kGsRad + kGsAngStride * p + 4 * g; }
 template <int CAP>
 __host__ __device__ constexpr size_t force_smem_per_warp() { return round16(sizeof(AngStage<CAP>) + (kGsFloats + 3 * CAP) * sizeof(float)); }
 static_assert(aev_smem_per_warp<kAngCap>() % 16 == 0 && force_smem_per_warp<kAngCap>() % 16 == 0 &&
@@ -182,10 +184,12 @@ static_assert(offsetof(AevScratch<kAngCap>, pfT) % 16 == 0 && offsetof(AevScratc
               offsetof(AevScratch<kAngCapBig>, pfT) % 16 == 0 && offsetof(AevScratch<kAngCapBig>, rfT) % 16 == 0 &&
               kFacRow % 4 == 0 && kSC == 32, "factor rows load four floats at a time; one pair per lane");
 static_assert(offsetof(AevScratch<kAngCap>, accR) % 8 == 0, "radial accumulators are read two at a time");
-static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsRadStride == 16 && kGsAngStride == 32,
-              "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row)");
-static_assert(2 * force_smem_per_warp<kAngCap>() + 1024 <= 233472 / 15,
-              "15 blocks of two force warps fit an SM (each block also reserves 1 KB)");
+static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsRadStride == 16 &&
+              kGsAngStride % 4 == 0 && (kGsAngStride / 4) % 2 == 1,
+              "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row); angular rows "
+              "start an odd number of 4-bank groups apart");
+static_assert(2 * force_smem_per_warp<kAngCap>() + 1024 <= 233472 / 16,
+              "16 blocks of two force warps fit an SM (each block also reserves 1 KB)");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -400,6 +404,9 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
     AngStage<CAP>& s = *reinterpret_cast<AngStage<CAP>*>(wsmem);
     AevScratch<CAP>& X = *reinterpret_cast<AevScratch<CAP>*>(wsmem + sizeof(AngStage<CAP>));
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
+    int4 cs0, cs1;
+    load_counts(a.ctr, cs0, cs1);
+    const int rank_i = a.rank[i];
     const int* row = a.nbr + (size_t)i * a.cap;
     NbrLane nl0, nl1;
     const int cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
@@ -437,7 +444,7 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
     if (mA > CAP) return false;   // warp-uniform
     __syncwarp();
     const int si = species_of(hi_i);
-    const int rw = row_base(a.ctr->species, si) + a.rank[i];
+    const int rw = row_base(cs0, cs1, si) + rank_i;
     OutT* out = G + (size_t)rw * kAevLd;
     OutT* out_lo = G_lo ? G_lo + (size_t)rw * kAevLd : nullptr;
 
@@ -553,24 +560,30 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
             const unsigned ends = __ballot_sync(kFull, last);
             __syncwarp();
             // Lane (a, z) adds the super-chunk's products in pair order, four
-            // pairs per pair of 16-byte loads; at a block's last pair the sum
-            // goes to the block's column and restarts (the last block may
-            // continue into the next super-chunk; its sum stays in acc).
-            // Factors past n are stale, but no block ends there: what they add
-            // is never written.
+            // pairs per pair of 16-byte loads (a quad with no block end as one
+            // pairwise sum: one dependent add per quad); at a block's last
+            // pair the sum goes to the block's column and restarts (the last
+            // block may continue into the next super-chunk; its sum stays in
+            // acc). Factors past n are stale, but no block ends there: what
+            // they add is never written.
 #pragma unroll
             for (int q = 0; q < kSC; q += 4) {
                 if (q >= n) break;   // warp-uniform
                 const float4 p4 = *reinterpret_cast<const float4*>(pz + q);
                 const float4 r4 = *reinterpret_cast<const float4*>(ra + q);
-                const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+                const float xv[4] = {p4.x * r4.x, p4.y * r4.y, p4.z * r4.z, p4.w * r4.w};
+                const unsigned e4 = (ends >> q) & 15u;
+                if (e4 == 0u) {   // warp-uniform
+                    acc += (xv[0] + xv[1]) + (xv[2] + xv[3]);
+                } else {
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    acc = fmaf(pv[t], rv[t], acc);
-                    if (ends & (1u << (q + t))) {   // warp-uniform
-                        const int pp = __shfl_sync(kFull, p_b, q + t);
-                        put_g(out, out_lo, kRadLen + 32 * pp + lane, acc);
-                        acc = 0.f;
+                    for (int t = 0; t < 4; ++t) {
+                        acc += xv[t];
+                        if (e4 & (1u << t)) {   // warp-uniform
+                            const int pp = __shfl_sync(kFull, p_b, q + t);
+                            put_g(out, out_lo, kRadLen + 32 * pp + lane, acc);
+                            acc = 0.f;
+                        }
                     }
                 }
             }
@@ -681,8 +694,10 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
     float* gs = reinterpret_cast<float*>(wsmem + sizeof(AngStage<CAP>));
     float* fslot = gs + kGsFloats;
     const float4 hi_i = a.hi[i], lo_i = a.lo[i];
+    int4 cs0, cs1;
+    load_counts(a.ctr, cs0, cs1);
     const int si = species_of(hi_i);
-    const int rw = row_base(a.ctr->species, si) + a.rank[i];
+    const int rw = row_base(cs0, cs1, si) + a.rank[i];
     const TG* grow = dG + (size_t)rw * kAevLd;
     // 8 columns per lane and load (16 B of BF16 or 32 B of FP32); the 8 stay
     // inside one radial block or one 32-column angular row. All of a lane's
@@ -842,7 +857,7 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         fiy -= gjy + gky;
         fiz -= gjz + gkz;
     };
-    if (mA <= 32) {   // warp-uniform
+    if (CAP <= 64 && mA <= 32) {   // warp-uniform
         // Slot owners, no shared-memory atomics: lane l = r m + j of group
         // r < g = 32 / m owns slot j. Group r takes rotations t = r + 1,
         // g + r + 1, ... (pairs (j, (j + t) mod m); for even m the last
@@ -882,8 +897,9 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
             atomicAdd(&grad[3 * (size_t)jj + 2], (double)(fslot[3 * lane + 2] + Fz));
         }
     } else {
-        // more than 32 slots: pairs packed 32 per pass in rotation order, the
-        // gradients added to the slots in shared memory, flushed once
+        // more than 32 slots (rare in the main launch; every atom of the
+        // second): pairs packed 32 per pass in rotation order, the gradients
+        // added to the slots in shared memory (atomics), flushed once
         const int P = mA * (mA - 1) / 2;
         PairIt it;
         it.init(mA, lane);
@@ -925,8 +941,10 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
 
 // Main force launch: one warp per atom; an atom with more than kAngCap
 // angular neighbors is left to the second launch (the AEV listed it).
+// The BF16 instance (the served path) is held to 64 registers: 16 blocks of
+// two warps per SM; the FP32 instances would spill there (12 blocks: <= 85).
 template <bool FAST, typename TG>
-__global__ void __launch_bounds__(kForceWarps * 32) k_forces(AevArgs a, const TG* __restrict__ dG,
+__global__ void __launch_bounds__(kForceWarps * 32, std::is_same<TG, __nv_bfloat16>::value ? 16 : 12) k_forces(AevArgs a, const TG* __restrict__ dG,
                                                          double* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5;
