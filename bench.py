@@ -530,9 +530,9 @@ HBM_BYTES_PER_ATOM = {"stage": 85, "neighbors_allpairs": 124, "neighbors_cell": 
 # the BF16 path (profiles/k_aev_served_bf16.md, profiles/k_forces_served_bf16.md);
 # reported only while kernels_aev.cu is the source that was captured.
 MEASURED_ISSUE = {
-    "file": "kernels_aev.cu", "sha1": "16174e7c1e33126d8cb4e7f0b21f3788c068ec8d",
-    "aev": {"issue_active": 0.811, "xu_pipe": 0.194, "fma_pipe": 0.299},
-    "forces": {"issue_active": 0.678, "xu_pipe": 0.146, "fma_pipe": 0.307},
+    "file": "kernels_aev.cu", "sha1": "0d3c71ce9793eb7412f4e5154861c3ee4e02aba9",
+    "aev": {"issue_active": 0.751, "xu_pipe": 0.212, "fma_pipe": 0.249},
+    "forces": {"issue_active": 0.778, "xu_pipe": 0.208, "fma_pipe": 0.419},
 }
 
 
@@ -859,7 +859,7 @@ def vv_md(P, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
