@@ -857,14 +857,19 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         fiy -= gjy + gky;
         fiz -= gjz + gkz;
     };
-    if (CAP <= 64 && mA <= 32) {   // warp-uniform
+    if (CAP <= 64 && (mA <= 16 || (mA >= 21 && mA <= 32))) {   // warp-uniform
         // Slot owners, no shared-memory atomics: lane l = r m + j of group
         // r < g = 32 / m owns slot j. Group r takes rotations t = r + 1,
         // g + r + 1, ... (pairs (j, (j + t) mod m); for even m the last
         // rotation, t = m / 2, only for j < m / 2: every pair once). The
         // gradient on j stays in the lane's registers; the one on k goes to
         // k's owner in the same group (same t) by a shuffle. The groups' sums
-        // of a slot are added into group 0 at the end (fixed order).
+        // of a slot are added into group 0 at the end (fixed order). For 17
+        // to 20 slots one group leaves 12 to 15 lanes idle and takes m / 2
+        // passes against ~m^2 / 64 packed ones: there the packed order with
+        // shared atomics below measured faster (forces per served-stream
+        // step: 3.03 ms with owners up to 32 slots, 2.98 with 17..20 packed,
+        // 3.01 with 17..23, 3.04 with 17..27).
         float Fx = 0.f, Fy = 0.f, Fz = 0.f;
         if (mA >= 2) {
             const int g = 32 / mA, r = lane / mA, j = lane - r * mA;
@@ -897,9 +902,10 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
             atomicAdd(&grad[3 * (size_t)jj + 2], (double)(fslot[3 * lane + 2] + Fz));
         }
     } else {
-        // more than 32 slots (rare in the main launch; every atom of the
-        // second): pairs packed 32 per pass in rotation order, the gradients
-        // added to the slots in shared memory (atomics), flushed once
+        // 17 to 20 or more than 32 slots (the latter rare in the main
+        // launch; every atom of the second): pairs packed 32 per pass in
+        // rotation order, the gradients added to the slots in shared memory
+        // (atomics), flushed once
         const int P = mA * (mA - 1) / 2;
         PairIt it;
         it.init(mA, lane);
