@@ -2,7 +2,7 @@
 
 An atom with more neighbors inside the 5.1 A list than a system's rows hold
 (160 by default) makes the system grow its rows to 256 once and redo the
-evaluation: the result matches the oracle. An atom with more than 32
+evaluation: the result matches the oracle. An atom with more than 48
 neighbors inside the 3.5 A angular cutoff is done by the AEV's and the force
 kernel's second launches (up to 256 angular neighbors, more than a row
 holds): crowded atoms alone, mixed with ordinary ones, in a batch, at both
@@ -59,7 +59,7 @@ def test_rows_grow_for_a_crowded_atom(P, wts):
 
 
 def _ball(n=80, radius=2.4, seed=4):
-    """n atoms inside a 2.4 A ball: most have more than 32 angular neighbors."""
+    """n atoms inside a 2.4 A ball: most have more than 48 angular neighbors."""
     rng = np.random.default_rng(seed)
     ball = rng.normal(size=(n, 3))
     ball *= (radius * rng.uniform(size=(n, 1)) ** (1 / 3)) / np.linalg.norm(ball, axis=1, keepdims=True)
