@@ -183,7 +183,8 @@ static_assert(kRadLen % 8 == 0 && kAevLd % 8 == 0, "element-pair blocks of an AE
 static_assert(offsetof(AevScratch<kAngCap>, pfT) % 16 == 0 && offsetof(AevScratch<kAngCap>, rfT) % 16 == 0 &&
               offsetof(AevScratch<kAngCapBig>, pfT) % 16 == 0 && offsetof(AevScratch<kAngCapBig>, rfT) % 16 == 0 &&
               kFacRow % 4 == 0 && kSC == 32, "factor rows load four floats at a time; one pair per lane");
-static_assert(offsetof(AevScratch<kAngCap>, accR) % 8 == 0, "radial accumulators are read two at a time");
+static_assert(offsetof(AevScratch<kAngCap>, accR) % 16 == 0 && sizeof(AngStage<kAngCap>) % 16 == 0 && kRadLen % 4 == 0,
+              "radial accumulators are zeroed and read four at a time");
 static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsRadStride == 16 &&
               kGsAngStride % 4 == 0 && (kGsAngStride / 4) % 2 == 1,
               "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row); angular rows "
@@ -348,6 +349,22 @@ __device__ __forceinline__ void put_g(__nv_bfloat16* out, __nv_bfloat16* out_lo,
     if (out_lo) out_lo[c] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Four consecutive AEV values (c a multiple of 4) in one 16-byte (FP32) or
+// two 8-byte (BF16 hi, lo) stores; the same roundings as put_g.
+__device__ __forceinline__ void put_g4(float* out, float*, int c, float4 v) { *reinterpret_cast<float4*>(out + c) = v; }
+__device__ __forceinline__ void put_g4(__nv_bfloat16* out, __nv_bfloat16* out_lo, int c, float4 v) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<uint2*>(out + c) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    if (out_lo) {
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+        *reinterpret_cast<uint2*>(out_lo + c) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+    }
+}
+
 // Zeros columns [c0, c1) of an AEV row (and of its lo row) with 16-byte
 // stores; c0 and c1 are multiples of 16 bytes' worth of columns (every
 // element-pair block starts on one: 112 + 32 p columns).
@@ -362,6 +379,20 @@ __device__ __forceinline__ void zero_cols(OutT* out, OutT* out_lo, int c0, int c
         if (dl) dl[q] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
+
+// Element pair p (pair_index order: (0,0), (0,1), .., (0,6), (1,1), ..) as
+// s1 | s2 << 4, eight pairs of 8 bits per 64-bit word (compile-time table).
+__host__ __device__ constexpr unsigned long long pair_code_word(int w) {
+    unsigned long long v = 0;
+    int p = 0;
+    for (int a = 0; a < kNSpecies; ++a)
+        for (int b = a; b < kNSpecies; ++b, ++p)
+            if (p / 8 == w) v |= (unsigned long long)(a | (b << 4)) << (8 * (p % 8));
+    return v;
+}
+static_assert(kNPairs == 28 && (pair_code_word(0) >> 56 & 0xff) == (1 | (1 << 4)) &&
+                  (pair_code_word(1) >> 8 & 0xff) == (1 | (3 << 4)) && (pair_code_word(3) >> 24 & 0xff) == (6 | (6 << 4)),
+              "element-pair table in pair_index order: pair 7 is (1, 1), pair 9 is (1, 3), pair 27 is (6, 6)");
 
 // Orders the m staged neighbors by element: ord[sorted position] = stage
 // slot (stable within an element); lane e < 7 gets the size (cnt_e) and
@@ -410,7 +441,7 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
     const int* row = a.nbr + (size_t)i * a.cap;
     NbrLane nl0, nl1;
     const int cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
-    for (int c = lane; c < 4 * kRadLen; c += 32) X.accR[c] = 0.f;
+    for (int c = lane; c < kRadLen; c += 32) reinterpret_cast<float4*>(X.accR)[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
 
     // radial: four neighbors per step, a quarter-warp each, shifts 2 k2 and 2 k2 + 1 per lane
@@ -458,15 +489,13 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
     int my_off, my_end, my_desc, my_p, np, P;
     {
         // lane p < 28: element pair (s1 <= s2) in pair_index order and its pair count
-        int s1 = 0, s2 = 0, l = lane;
-        for (int e = 0; e < kNSpecies; ++e) {
-            const int len = kNSpecies - e;
-            if (l >= 0 && l < len) {
-                s1 = e;
-                s2 = e + l;
-            }
-            l -= len;
-        }
+        const int pl = lane < kNPairs ? lane : 0;
+        const unsigned long long pw = (pl >> 3) == 0   ? pair_code_word(0)
+                                      : (pl >> 3) == 1 ? pair_code_word(1)
+                                      : (pl >> 3) == 2 ? pair_code_word(2)
+                                                       : pair_code_word(3);
+        const int pcode = (int)((pw >> (8 * (pl & 7))) & 0xffu);
+        const int s1 = pcode & 15, s2 = pcode >> 4;
         const int c1 = __shfl_sync(kFull, cnt_e, s1), c2 = __shfl_sync(kFull, cnt_e, s2);
         const int g1 = __shfl_sync(kFull, g_e, s1), g2 = __shfl_sync(kFull, g_e, s2);
         const int n = lane < kNPairs ? (s1 < s2 ? c1 * c2 : c1 * (c1 - 1) / 2) : 0;
@@ -590,11 +619,13 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
             __syncwarp();   // the next super-chunk overwrites the factors
         }
     }
-    // radial block (four quarters, added in a fixed order)
-    for (int c = lane; c < kRadLen; c += 32) {
-        const int ra4 = 4 * kRadShifts * (c >> 4) + (c & 15);
-        put_g(out, out_lo, c,
-              (X.accR[ra4] + X.accR[ra4 + kRadShifts]) + (X.accR[ra4 + 2 * kRadShifts] + X.accR[ra4 + 3 * kRadShifts]));
+    // radial block (four quarters, added in a fixed order), four columns per lane
+    if (lane < kRadLen / 4) {
+        const float4* a4 = reinterpret_cast<const float4*>(X.accR + 4 * kRadShifts * (lane >> 2) + 4 * (lane & 3));
+        const float4 q0 = a4[0], q1 = a4[kRadShifts / 4], q2 = a4[2 * kRadShifts / 4], q3 = a4[3 * kRadShifts / 4];
+        put_g4(out, out_lo, 4 * lane,
+               make_float4((q0.x + q1.x) + (q2.x + q3.x), (q0.y + q1.y) + (q2.y + q3.y), (q0.z + q1.z) + (q2.z + q3.z),
+                           (q0.w + q1.w) + (q2.w + q3.w)));
     }
     if (lane == 0) row_atom[rw] = i;
     return true;
