@@ -128,10 +128,7 @@ struct M<true> {    // hardware approximations with subnormals flushed (BF16-net
 template <int CAP>
 struct AngStage {
     float4 u[CAP];     // unit vector d / r, and r
-    float invr[CAP];
-    float fc[CAP];     // fc(r; 3.5)
-    float dfc[CAP];    // d fc / dr
-    int sp[CAP];       // element
+    float4 w[CAP];     // 1 / r, fc(r; 3.5), d fc / dr, element (int bits): one 16-byte load
     int idx[CAP];      // atom index
 };
 
@@ -282,10 +279,9 @@ __device__ __forceinline__ int stage_angular(const NbrLane& nl, int mA, AngStage
     if (nl.inA && pA < CAP) {
         const float ir = M<FAST>::rcp(nl.r);
         s.u[pA] = make_float4(nl.d.x * ir, nl.d.y * ir, nl.d.z * ir, nl.r);
-        s.invr[pA] = ir;
-        s.fc[pA] = 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcAng)) + 0.5f;
-        s.dfc[pA] = -0.5f * (3.14159265358979f / kRcAng) * M<FAST>::spi(nl.r * (1.f / kRcAng));
-        s.sp[pA] = nl.sp;
+        s.w[pA] = make_float4(ir, 0.5f * M<FAST>::cpi(nl.r * (1.f / kRcAng)) + 0.5f,
+                              -0.5f * (3.14159265358979f / kRcAng) * M<FAST>::spi(nl.r * (1.f / kRcAng)),
+                              __int_as_float(nl.sp));
         s.idx[pA] = nl.j;
     }
     return mA + __popc(bA);
@@ -403,7 +399,7 @@ __device__ __forceinline__ void sort_by_element(const AngStage<CAP>& s, int m, i
     constexpr int NCH = (CAP + 31) / 32;
     int spv[NCH];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) spv[c] = c * 32 + lane < m ? s.sp[c * 32 + lane] : -1;
+    for (int c = 0; c < NCH; ++c) spv[c] = c * 32 + lane < m ? __float_as_int(s.w[c * 32 + lane].w) : -1;
     const unsigned lt = lanemask_lt();
     int base = 0;
     cnt_e = 0;
@@ -563,10 +559,10 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
                     kk = g1 + (x >= cdiv ? x - cdiv : x);
                 }
                 const int J = X.ord[jj], K = X.ord[kk];
-                const float4 uj = s.u[J], uk = s.u[K];
+                const float4 uj = s.u[J], uk = s.u[K], wj = s.w[J], wk = s.w[K];
                 const float c = 0.95f * (uj.x * uk.x + uj.y * uk.y + uj.z * uk.z);
                 const float sn = M<FAST>::sq(1.f - c * c);
-                const float f2 = 2.f * s.fc[J] * s.fc[K];
+                const float f2 = 2.f * wj.y * wk.y;
                 // fast path: f2 b^zeta = 2^(zeta log2 b + log2 f2), one multiply fewer per section
                 const float lf2 = FAST ? M<true>::lg2(f2) : 0.f;
                 // sections z and 7 - z share sin: theta_(7-z) = pi - theta_z
@@ -746,18 +742,26 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         }
         // the first 64 neighbors' loads overlap the dE/dG row's
         cnt = load_neighbors2<FAST>(a, row, a.nbr_cnt + i, lane, hi_i, lo_i, nl0, nl1);
+        // columns c .. c + 7 (groups g0 and g0 + 1 of one row): a radial row
+        // for lanes 0..13 of q = 0, else angular column x = c - 112 of row
+        // x / 32, staged at kGsRad + 36 (x / 32) + x % 32 = kGsRad + x + 4 (x / 32)
+        static_assert(kGsAngStride == 36 && kRadLen == 112, "staging offsets below");
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c = 8 * lane + 256 * q;
             if (c < kAevLen) {
-                // columns c .. c + 7: groups g0 and g0 + 1 of one row
-                const bool rad = c < kRadLen;
-                const int rowq = rad ? c >> 4 : (c - kRadLen) >> 5;
-                const int g0 = rad ? (c & 15) >> 2 : ((c - kRadLen) & 31) >> 2;
-                *reinterpret_cast<float4*>(gs + (rad ? gs_rad(rowq, g0) : gs_ang(rowq, g0))) =
-                    make_float4(v[q][0], v[q][1], v[q][2], v[q][3]);
-                *reinterpret_cast<float4*>(gs + (rad ? gs_rad(rowq, g0 + 1) : gs_ang(rowq, g0 + 1))) =
-                    make_float4(v[q][4], v[q][5], v[q][6], v[q][7]);
+                int o0, o1;
+                if (q == 0 && c < kRadLen) {
+                    const int rowq = c >> 4, g0 = (c & 15) >> 2;
+                    o0 = gs_rad(rowq, g0);
+                    o1 = gs_rad(rowq, g0 + 1);
+                } else {
+                    const int x = c - kRadLen;
+                    o0 = kGsRad + x + 4 * (x >> 5);
+                    o1 = o0 + 4;
+                }
+                *reinterpret_cast<float4*>(gs + o0) = make_float4(v[q][0], v[q][1], v[q][2], v[q][3]);
+                *reinterpret_cast<float4*>(gs + o1) = make_float4(v[q][4], v[q][5], v[q][6], v[q][7]);
             }
         }
     }
@@ -812,7 +816,7 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
     // angular: one pair (j, k) per lane, all 32 (shift, section) terms in registers.
     // pair_grad: the pair's gradients on j and k (and minus their sum on i).
     auto pair_grad = [&](int j, int kk, float3& gj, float3& gk) {
-        const float4 uj = s.u[j], uk = s.u[kk];
+        const float4 uj = s.u[j], uk = s.u[kk], wj = s.w[j], wk = s.w[kk];
         const float cos0 = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float c = 0.95f * cos0;
         const float sn = M<FAST>::sq(1.f - c * c);
@@ -823,8 +827,8 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         // reciprocal of b (b >= 0.066 for |c| <= 0.95 and the eight theta_z).
         const float B = 0.5f * kZeta * c * M<FAST>::rcp(sn);
         const float rbar = 0.5f * (uj.w + uk.w);
-        const float fj = s.fc[j], fk = s.fc[kk], dfj = s.dfc[j], dfk = s.dfc[kk];
-        const int p = pair_index(s.sp[j], s.sp[kk]);
+        const float fj = wj.y, fk = wk.y, dfj = wj.z, dfk = wk.z;
+        const int p = pair_index(__float_as_int(wj.w), __float_as_int(wk.w));
         float P[kAngZ], D[kAngZ];
 #pragma unroll
         for (int zz = 0; zz < kAngZ / 2; ++zz) {
@@ -875,7 +879,7 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         const float Srj = 0.5f * f * T2 + dfj * fk * T1;
         const float Srk = 0.5f * f * T2 + fj * dfk * T1;
         // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k
-        const float aj = 0.95f * Sc * s.invr[j], ak = 0.95f * Sc * s.invr[kk];
+        const float aj = 0.95f * Sc * wj.x, ak = 0.95f * Sc * wk.x;
         const float gjx = aj * (uk.x - cos0 * uj.x) + Srj * uj.x;
         const float gjy = aj * (uk.y - cos0 * uj.y) + Srj * uj.y;
         const float gjz = aj * (uk.z - cos0 * uj.z) + Srj * uj.z;
