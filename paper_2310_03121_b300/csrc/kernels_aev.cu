@@ -585,8 +585,8 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
             const unsigned ends = __ballot_sync(kFull, last);
             __syncwarp();
             // Lane (a, z) adds the super-chunk's products in pair order, four
-            // pairs per pair of 16-byte loads (a quad with no block end as one
-            // pairwise sum: one dependent add per quad); at a block's last
+            // pairs per pair of 16-byte loads (a quad with no block end as two
+            // fused pair sums: one dependent add per quad); at a block's last
             // pair the sum goes to the block's column and restarts (the last
             // block may continue into the next super-chunk; its sum stays in
             // acc). Factors past n are stale, but no block ends there: what
@@ -596,14 +596,14 @@ __device__ __forceinline__ bool aev_atom(const AevArgs& a, OutT* __restrict__ G,
                 if (q >= n) break;   // warp-uniform
                 const float4 p4 = *reinterpret_cast<const float4*>(pz + q);
                 const float4 r4 = *reinterpret_cast<const float4*>(ra + q);
-                const float xv[4] = {p4.x * r4.x, p4.y * r4.y, p4.z * r4.z, p4.w * r4.w};
                 const unsigned e4 = (ends >> q) & 15u;
                 if (e4 == 0u) {   // warp-uniform
-                    acc += (xv[0] + xv[1]) + (xv[2] + xv[3]);
+                    acc += fmaf(p4.y, r4.y, p4.x * r4.x) + fmaf(p4.w, r4.w, p4.z * r4.z);
                 } else {
+                    const float pv[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        acc += xv[t];
+                        acc = fmaf(pv[t], rv[t], acc);
                         if (e4 & (1u << t)) {   // warp-uniform
                             const int pp = __shfl_sync(kFull, p_b, q + t);
                             put_g(out, out_lo, kRadLen + 32 * pp + lane, acc);
@@ -833,8 +833,8 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
 #pragma unroll
         for (int zz = 0; zz < kAngZ / 2; ++zz) {
             // sections zz and 7 - zz: theta_(7-zz) = pi - theta_zz (cos flips, sin stays)
-            const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f), x = c * c_aev.hcos_z[zz];
-            const float b0 = y + x, b1 = y - x;
+            const float y = fmaf(sn, c_aev.hsin_z[zz], 0.5f);
+            const float b0 = fmaf(c, c_aev.hcos_z[zz], y), b1 = fmaf(-c, c_aev.hcos_z[zz], y);
             float Q0, Q1;
             if (FAST) {
                 Q0 = M<true>::ex2(fmaf(kZeta - 1.f, M<true>::lg2(b0), 1.f));
@@ -878,14 +878,12 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
         Sc *= f;
         const float Srj = 0.5f * f * T2 + dfj * fk * T1;
         const float Srk = 0.5f * f * T2 + fj * dfk * T1;
-        // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j, and j <-> k
+        // dE/d(d_ij) = (0.95 Sc / r_ij)(u_k - cos0 u_j) + Srj u_j
+        //            = aj u_k + (Srj - aj cos0) u_j, and j <-> k
         const float aj = 0.95f * Sc * wj.x, ak = 0.95f * Sc * wk.x;
-        const float gjx = aj * (uk.x - cos0 * uj.x) + Srj * uj.x;
-        const float gjy = aj * (uk.y - cos0 * uj.y) + Srj * uj.y;
-        const float gjz = aj * (uk.z - cos0 * uj.z) + Srj * uj.z;
-        const float gkx = ak * (uj.x - cos0 * uk.x) + Srk * uk.x;
-        const float gky = ak * (uj.y - cos0 * uk.y) + Srk * uk.y;
-        const float gkz = ak * (uj.z - cos0 * uk.z) + Srk * uk.z;
+        const float cj = fmaf(-aj, cos0, Srj), ck = fmaf(-ak, cos0, Srk);
+        const float gjx = fmaf(cj, uj.x, aj * uk.x), gjy = fmaf(cj, uj.y, aj * uk.y), gjz = fmaf(cj, uj.z, aj * uk.z);
+        const float gkx = fmaf(ck, uk.x, ak * uj.x), gky = fmaf(ck, uk.y, ak * uj.y), gkz = fmaf(ck, uk.z, ak * uj.z);
         gj = make_float3(gjx, gjy, gjz);
         gk = make_float3(gkx, gky, gkz);
         fix -= gjx + gkx;
