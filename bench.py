@@ -530,9 +530,9 @@ HBM_BYTES_PER_ATOM = {"stage": 85, "neighbors_allpairs": 124, "neighbors_cell": 
 # the BF16 path (profiles/k_aev_served_bf16.md, profiles/k_forces_served_bf16.md);
 # reported only while kernels_aev.cu is the source that was captured.
 MEASURED_ISSUE = {
-    "file": "kernels_aev.cu", "sha1": "0d3c71ce9793eb7412f4e5154861c3ee4e02aba9",
-    "aev": {"issue_active": 0.751, "xu_pipe": 0.212, "fma_pipe": 0.249},
-    "forces": {"issue_active": 0.778, "xu_pipe": 0.208, "fma_pipe": 0.419},
+    "file": "kernels_aev.cu", "sha1": "aa51c33774ea1a68c6db2d7eef7a58b0d46ca4ec",
+    "aev": {"issue_active": 0.724, "xu_pipe": 0.221, "fma_pipe": 0.229},
+    "forces": {"issue_active": 0.730, "xu_pipe": 0.192, "fma_pipe": 0.377},
 }
 
 
