@@ -8,14 +8,15 @@ ANI-2x-shaped weights). One step evaluates every molecule once: the stream is
 packed, oldest first, into device batches of at most 262,144 atoms / 8,192
 molecules (the serving loop's packing; measured 1.7% faster than 131,072 /
 4,096: fewer launches and kernel tails) and the batches run on two CUDA
-streams, two in flight, as the server's two slots do.
+streams, two in flight.
 
 value  device-resident inputs (all coordinates in HBM before the timed
        region), CUDA-event time per step, L2 flushed between steps.
 e2e    the same stream through the C-ABI server (mlp_server_replay_clients
        with --e2e-clients native client threads: host coordinates in, host
-       energies and forces out, every request due at t = 0), wall time of the
-       median of three runs after a warm-up run; p50/p99 request latency.
+       energies and forces out, every request due at t = 0, the server's
+       default batching), median wall time of at least nine replays after
+       four warm-up replays; p50/p99 request latency.
 Also reported: Langevin dynamics at 2 fs (LF-Middle, graph-replayed steps)
 of the 72-atom ligand and the 672-atom ligand-in-water system in ns/day,
 one net and the 8-net ensemble; velocity-Verlet trajectories at 0.5 fs with
@@ -395,9 +396,11 @@ def run_ours(args):
     # ---------------- e2e through the server (host buffers), saturating arrivals
     if not args.no_e2e:
         # the server's own batching (mlp_server_opts_default: batches of <= 131,072
-        # atoms / 4,096 molecules, two in flight); larger batches lengthen its
-        # pipeline's fill and drain (e2e measured 103.5 M with 262,144)
-        srv = P.Server(W, precision=prec, streams=2)
+        # atoms / 4,096 molecules, three in flight); larger batches lengthen its
+        # pipeline's fill and drain (e2e measured 103.5 M with 262,144), and a
+        # third slot overlaps one more batch's gather and scatter with the
+        # others' kernels (measured +2.3% over two)
+        srv = P.Server(W, precision=prec)
         arr = np.zeros(stream.count, dtype=np.int64)
         walls = []
         lat = None

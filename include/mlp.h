@@ -274,7 +274,7 @@ typedef struct {
     int32_t max_batch_atoms;    /* atoms packed into one device batch (default 131072)   */
     int32_t max_batch_mols;     /* molecules per batch (default 4096)                    */
     int32_t max_atoms_per_mol;  /* largest admissible molecule (default 256)             */
-    int32_t streams;            /* batches in flight on the device (default 2)           */
+    int32_t streams;            /* batches in flight on the device (default 3)           */
     int32_t queue_capacity;     /* requests outstanding (submitted, not yet collected) before MLP_EAGAIN (default 65536) */
     int64_t budget_bytes;       /* device bytes the in-flight batches may hold (40e9)    */
     /* Batching while the device is busy: with another batch in flight, a

@@ -499,7 +499,7 @@ void mlp_server_opts_default(mlp_server_opts* o) {
     o->max_batch_atoms = 131072;
     o->max_batch_mols = 4096;
     o->max_atoms_per_mol = 256;
-    o->streams = 2;
+    o->streams = 3;
     o->queue_capacity = 65536;
     o->budget_bytes = 40LL * 1000 * 1000 * 1000;
     o->min_batch_atoms = 16384;
