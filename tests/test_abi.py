@@ -101,7 +101,7 @@ def test_server_defaults(L):
     o = _lib.ServerOpts()
     L.mlp_server_opts_default(ctypes.byref(o))
     assert o.precision == _lib.MLP_BF16
-    assert o.max_atoms_per_mol == 256 and o.streams == 2
+    assert o.max_atoms_per_mol == 256 and o.streams == 3
     assert o.budget_bytes == 40 * 10**9
 
 
