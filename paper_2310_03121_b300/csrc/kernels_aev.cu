@@ -19,18 +19,19 @@
 //     loaded them by shuffles, a quarter-warp each with two shifts per lane;
 //     each lane owns its accumulator columns per element and quarter -> no
 //     atomics, fixed order;
-//   * angular: pairs are taken 32 at a time: one pair per lane computes its
-//     8 angle factors and 4 distance factors into shared memory, then lane
-//     (a, z) adds the products, pair by pair, to its own column 32 p + 8 a + z
-//     (conflict-free, fixed order -> deterministic).
+//   * angular: pairs are taken 32 at a time, ordered by element pair: one
+//     pair per lane computes its 8 angle factors and 4 distance factors into
+//     shared memory, then lane (a, z) adds the products, pair by pair, into
+//     its own column 32 p + 8 a + z, written when the block's last pair is
+//     in (conflict-free, fixed order -> deterministic).
 // The backward recomputes the terms with their derivatives and contracts
-// them with dE/dG (staged in shared memory as FP32, XOR-swizzled rows):
-// radial one neighbor per lane (16 unrolled exponentials), angular one pair
-// per lane with its 4 distance and 8 angle factors in registers. Gradients
-// on neighbors go to FP64 global sums: radial ones per neighbor; angular
-// ones summed per angular neighbor first (in the registers of the lane that
-// owns the neighbor when an atom has at most 32 of them, else in shared
-// memory) and added once.
+// them with dE/dG (staged in shared memory as FP32: radial rows XOR-swizzled,
+// angular rows padded): radial one neighbor per lane (16 unrolled
+// exponentials), angular one pair per lane with its 4 distance and 8 angle
+// factors in registers. Gradients on neighbors go to FP64 global sums:
+// radial ones per neighbor; angular ones summed per angular neighbor first
+// (in the registers of the lane that owns the neighbor for up to 16 or 21 to
+// 32 of them, else in shared memory) and added once.
 #include <cuda_bf16.h>
 
 #include <type_traits>
