@@ -387,9 +387,16 @@ __host__ __device__ constexpr unsigned long long pair_code_word(int w) {
             if (p / 8 == w) v |= (unsigned long long)(a | (b << 4)) << (8 * (p % 8));
     return v;
 }
-static_assert(kNPairs == 28 && (pair_code_word(0) >> 56 & 0xff) == (1 | (1 << 4)) &&
-                  (pair_code_word(1) >> 8 & 0xff) == (1 | (3 << 4)) && (pair_code_word(3) >> 24 & 0xff) == (6 | (6 << 4)),
-              "element-pair table in pair_index order: pair 7 is (1, 1), pair 9 is (1, 3), pair 27 is (6, 6)");
+// Every entry p of the table decodes to the (s1, s2) whose pair_index
+// (s1 7 - s1 (s1 - 1) / 2 + s2 - s1, the AEV column block) is p.
+__host__ __device__ constexpr bool pair_table_ok() {
+    for (int p = 0; p < kNPairs; ++p) {
+        const int code = (int)((pair_code_word(p / 8) >> (8 * (p % 8))) & 0xffu), a = code & 15, b = code >> 4;
+        if (!(a <= b && b < kNSpecies && a * kNSpecies - (a * (a - 1)) / 2 + (b - a) == p)) return false;
+    }
+    return true;
+}
+static_assert(kNPairs == 28 && pair_table_ok(), "element-pair table in pair_index order");
 
 // Orders the m staged neighbors by element: ord[sorted position] = stage
 // slot (stable within an element); lane e < 7 gets the size (cnt_e) and
