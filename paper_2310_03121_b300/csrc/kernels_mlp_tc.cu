@@ -106,7 +106,8 @@ enum {
     kBarEPart = 22,     // 1: E3 partial sums written; one arrival per epilogue warp
     kBarDrain = 23,     // 1: teardown MMA drain
     kBarG1 = 24,        // 1: ensemble, g1 written to shared memory; one arrival per epilogue warp
-    kNBars = 25
+    kBarOpA = 25,       // 4: 64-column atom a of the next GEMM's A operand written; one arrival per epilogue warp
+    kNBars = 29
 };
 
 struct TcArgs {
@@ -498,8 +499,22 @@ struct MmaState {
     uint32_t f1pos, rpos, geom;
 };
 
+// Operand atoms: the epilogue writes the next GEMM's A operand atom by atom
+// (64 columns) and arrives on barrier kBarOpA + a for each; the GEMM's MMAs
+// for K chunk a start as soon as atom a is in (the rest of the epilogue
+// overlaps them). n: phases waited for, per atom barrier.
+struct AtomWait {
+    uint32_t n[4];
+};
+__device__ __forceinline__ bool wait_atom(AtomWait& W, uint32_t bar0, int a, volatile int* abrt) {
+    if (!mbar_wait(bar0 + 8u * (kBarOpA + a), W.n[a] & 1u, abrt)) return false;
+    ++W.n[a];
+    tc_fence_after();
+    return true;
+}
+
 __device__ __forceinline__ bool mma_job(MmaState& S, const Job& J, uint32_t sbase, uint32_t tmem, uint32_t bar0,
-                                        volatile int* abrt) {
+                                        volatile int* abrt, AtomWait* aw = nullptr) {
     const uint32_t geom = J.geom();
     if (S.geom != geom) {
         S.geom = geom;
@@ -511,10 +526,11 @@ __device__ __forceinline__ bool mma_job(MmaState& S, const Job& J, uint32_t sbas
     for (int q = 0; q < nq; ++q) {
         const int si = (int)S.rpos;
         S.rpos = (S.rpos + 1u == (uint32_t)J.slots) ? 0u : S.rpos + 1u;
+        const int c = J.split ? (q >> 1) : q;
+        if (aw && (!J.split || (q & 1) == 0) && !wait_atom(*aw, bar0, c, abrt)) return false;   // A atom c written
         if (!mbar_wait(full_bar(bar0, 4 + si), (S.fpar >> (4 + si)) & 1u, abrt)) return false;
         S.fpar ^= 1u << (4 + si);
         tc_fence_after();
-        const int c = J.split ? (q >> 1) : q;
         const bool lo_b = J.split && (q & 1);
         const int ks = (c == J.nc - 1) ? J.lastk : 4;
         // one 16-wide K step advances a K-major SW128 descriptor by 32 bytes (2 in the address field)
@@ -557,8 +573,12 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
         tc_fence_after();
         return true;
     };
-    auto job = [&](int k, int s, int half) -> bool {
-        if (!mma_job(S, make_job<SPLIT>(M, k, s), sbase, tmem, bar0, abrt)) return false;
+    AtomWait aw{{0u, 0u, 0u, 0u}};
+    // a GEMM whose A operand an epilogue is still writing waits per K chunk (atoms)
+    auto job = [&](int k, int s, int half, bool atoms) -> bool {
+        Job J = make_job<SPLIT>(M, k, s);
+        J.d_col = 256u * (uint32_t)half;
+        if (!mma_job(S, J, sbase, tmem, bar0, abrt, atoms ? &aw : nullptr)) return false;
         mma_commit(bar0 + 8u * (kBarAcc + half));
         return true;
     };
@@ -605,21 +625,29 @@ __device__ void mma_issuer(const TcMaps& M, const int* counts, uint32_t sbase, u
             MLP_TC_MARK(21);
             // F2 writes half 1: the previous unit's last B1 block must have been read
             if (b1 && tile_no > 0 && !wait_b1(1)) break;
-            if (!wait_op() || !job(kJobF2, es, 1)) break;   // after E1
+            // Each GEMM of the chain starts on the atoms of its A operand as
+            // the previous epilogue writes them (F2 on E1's h1, F3 on E2's h2,
+            // B3 on E3's g3, B2 on EB3's g2, B1's first block on EB2's g1); its
+            // accumulator half was last read by an epilogue that finished
+            // before the previous GEMM completed.
+            if (!job(kJobF2, es, 1, true)) break;
             MLP_TC_MARK(22);
-            if (!wait_op() || !job(kJobF3, es, 0)) break;   // after E2
+            if (!job(kJobF3, es, 0, true)) break;
             MLP_TC_MARK(23);
             if (backward) {
-                if (!wait_op() || !job(kJobB3, es, 1)) break;   // after E3
+                if (!job(kJobB3, es, 1, true)) break;
                 MLP_TC_MARK(24);
-                if (!wait_op() || !job(kJobB2, es, 0)) break;   // after EB3
+                if (!job(kJobB2, es, 0, true)) break;
                 MLP_TC_MARK(25);
             }
             if (b1) {
-                if (!wait_op() || !job(kJobB1 + 0, es, 0)) break;   // after EB2
-                if (!job(kJobB1 + 1, es, 1)) break;
-                if (!wait_b1(0) || !job(kJobB1 + 2, es, 0)) break;
-                if (!wait_b1(1) || !job(kJobB1 + 3, es, 1)) break;
+                // block 0 in half 1 (last read by EB3), block 1 in half 0 once
+                // EB2 has read all of it, then each half after EB1's previous
+                // block in it
+                if (!job(kJobB1 + 0, es, 1, true)) break;
+                if (!wait_op() || !job(kJobB1 + 1, es, 0, false)) break;   // after EB2
+                if (!wait_b1(1) || !job(kJobB1 + 2, es, 1, false)) break;
+                if (!wait_b1(0) || !job(kJobB1 + 3, es, 0, false)) break;
                 MLP_TC_MARK(26);
             }
         }
@@ -707,6 +735,25 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
     const int nets = ENS ? p.nets : 1;
     uint32_t n_epart = 0;
     (void)warp;
+    const bool b1_here = p.backward && !ENS;   // B1 runs in this kernel (one net)
+    // This warp's part of operand atoms [a0, a1) of the next GEMM is written:
+    // one arrival on each atom's barrier (the shared stores made visible to
+    // the tensor core first).
+    auto arrive_atoms = [&](int a0, int a1) {
+        if (a0 >= a1) return;
+        fence_proxy_async();
+        tc_fence_before();
+        __syncwarp();
+        if (X.lane == 0)
+            for (int a = a0; a < a1; ++a) mbar_arrive(bar0 + 8u * (kBarOpA + a));
+    };
+    // after chunk c0 of a phase of N columns: the atoms this warp has no
+    // further chunk in are done (from its previous chunk's atom, or from 0
+    // after its first chunk, up to its next chunk's atom)
+    auto chunk_done = [&](int c0, int N) {
+        const int nxt = c0 + 16 * kParts < N ? (c0 + 16 * kParts) >> 6 : (N + 63) >> 6;
+        arrive_atoms(c0 < 16 * kParts ? 0 : c0 >> 6, nxt);
+    };
     for (int u = blockIdx.x, tile_no = 0;; u += gridDim.x, ++tile_no) {
         const int t = u / nets, net = u - t * nets;
         int s, row0, nvalid;
@@ -731,8 +778,8 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
 #pragma unroll
                 for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b1 + c0 + q));
                 store_act<SPLIT>(sbase, kOffH1, kOffH1lo, r, c0, v);
+                chunk_done(c0, kH1);   // F2 starts on the finished atoms of h1
             }
-            epi_arrive(X, op_bar);
             if (warp == 2) MLP_TC_MARK(2);
 
             // ---- E2: h2 = celu(D + b2)
@@ -747,8 +794,8 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
 #pragma unroll
                 for (int q = 0; q < 16; ++q) v[q] = celu_f(__uint_as_float(d[q]) + __ldg(b2 + c0 + q));
                 store_act<SPLIT>(sbase, kOffH2, kOffH2lo, r, c0, v);
+                chunk_done(c0, kH2);   // F3 starts on the finished atoms of h2
             }
-            epi_arrive(X, op_bar);
             if (warp == 2) MLP_TC_MARK(4);
 
             // ---- E3: energy (column-part partial sums per row, added in
@@ -765,7 +812,7 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
             if (warp == 2) MLP_TC_MARK(5);
             {
                 float es_part = 0.f;
-#pragma unroll 1
+    #pragma unroll 1
                 for (int c0 = 16 * part; c0 < kH3; c0 += 16 * kParts) {
                     uint32_t d[16];
                     tmem_ld16(X.tl + (uint32_t)c0, d);
@@ -786,6 +833,7 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                     if (p.backward) {
                         st_shared_v4(sbase + kOffG3 + op_off(r, c0), pk[0], pk[1], pk[2], pk[3]);
                         st_shared_v4(sbase + kOffG3 + op_off(r, c0 + 8), pk[4], pk[5], pk[6], pk[7]);
+                        chunk_done(c0, kH3);   // B3 starts on the finished atoms of g3
                     }
                 }
                 const uint32_t ep = sbase + kOffEPart + (uint32_t)r * 128u + (uint32_t)((4 ^ (r & 7)) << 4);
@@ -806,13 +854,14 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 }
                 ++n_epart;
             }
-            epi_arrive(X, op_bar);
             if (warp == 2) MLP_TC_MARK(6);
             if (!p.backward) {
+                epi_arrive(X, op_bar);   // the next tile's F1 overwrites the half E3 read
                 __syncwarp();
                 if (X.lane == 0) mbar_arrive(bar0 + 8u * kBarStage);
                 continue;
             }
+            tc_fence_before();   // E3's accumulator reads are done (B3 writes the other half; B2 this one)
 
             // ---- EB3: g2 = D * celu'(z2) over h2
             if (!epi_acc(X, 1)) break;
@@ -823,8 +872,8 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 tmem_ld16(X.tl + 256u + (uint32_t)c0, d);
                 tmem_wait_ld();
                 store_grad(sbase, kOffH2, r, c0, d);
+                chunk_done(c0, kH2);   // B2 starts on the finished atoms of g2
             }
-            epi_arrive(X, op_bar);
             if (warp == 2) MLP_TC_MARK(8);
 
             // ---- EB2: g1 = D * celu'(z1) over h1
@@ -836,8 +885,9 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
                 tmem_ld16(X.tl + (uint32_t)c0, d);
                 tmem_wait_ld();
                 store_grad(sbase, kOffH1, r, c0, d);
+                if (b1_here) chunk_done(c0, kH1);   // B1's first block starts on the finished atoms of g1
             }
-            epi_arrive(X, op_bar);
+            epi_arrive(X, op_bar);   // accumulator half 0 read (B1's second block; an ensemble: the next F1)
             if (warp == 2) MLP_TC_MARK(10);
 
             if (ENS) {
@@ -868,7 +918,7 @@ __device__ void epilogue(const TcMaps& M, const TcArgs& p, const int* counts, Ep
             // writes each with one TMA store.
             bool jok = true;
             for (int j = 0; j < 4; ++j) {
-                const int h = j & 1;
+                const int h = (j & 1) ^ 1;   // block 0 in half 1, block 1 in half 0, ...
                 if (!epi_acc(X, h)) {
                     jok = false;
                     break;
@@ -938,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(const __grid_constant__ 
     if (tid == 0) {
         for (int q = 0; q < kNBars; ++q) {
             const bool epi = q == kBarOp || q == kBarB1Free || q == kBarB1Free + 1 || q == kBarStage ||
-                             q == kBarEPart || q == kBarG1;
+                             q == kBarEPart || q == kBarG1 || (q >= kBarOpA && q < kBarOpA + 4);
             mbar_init(bar0 + 8u * q, epi ? (uint32_t)kEpiWarps : 1u);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
