@@ -44,8 +44,10 @@
 //                column part (w - 2) / 4 of 3: the 16-column chunks
 //                part, part + 3, part + 6, ...
 // Every hand-off is an mbarrier: ring slot full / empty (producer <-> MMA),
-// accumulator half full (MMA -> epilogue), operand ready and B1 half read
-// (epilogue -> MMA), tile done with shared memory (epilogue -> producer). Every
+// accumulator half full (MMA -> epilogue), operand atom ready (each GEMM
+// after F1 starts on the 64-column atoms of its A operand as the previous
+// epilogue writes them), accumulator half read and B1 half read (epilogue ->
+// MMA), tile done with shared memory (epilogue -> producer). Every
 // wait is bounded in time and also gives up when another role has aborted; on
 // abort the CTA records an error, drains its own copies, MMAs and stores,
 // frees its tensor memory and returns. Operands in shared memory use the
