@@ -66,9 +66,10 @@ namespace {
 // Warps (one atom each) per block. Small blocks: a block's shared memory is
 // released only when its slowest atom is done, so with atoms of uneven
 // neighbor counts fewer warps per block keep more warps busy (measured:
-// AEV 1 warp 12% and forces 2 warps 10% faster than 8 warps per block).
+// AEV 1 warp 12% faster than 8 per block; forces 2 warps 10% faster than 8,
+// 1 warp 2.3% faster than 2).
 constexpr int kAevWarps = 1;
-constexpr int kForceWarps = 2;
+constexpr int kForceWarps = 1;
 constexpr unsigned kFull = 0xffffffffu;
 
 template <bool FAST>
@@ -187,8 +188,8 @@ static_assert((sizeof(AngStage<kAngCap>) % 16) == 0 && (kGsRad % 4) == 0 && kGsR
               kGsAngStride % 4 == 0 && (kGsAngStride / 4) % 2 == 1,
               "staged dE/dG rows are read as float4 groups (4 per radial row, 8 per angular row); angular rows "
               "start an odd number of 4-bank groups apart");
-static_assert(2 * force_smem_per_warp<kAngCap>() + 1024 <= 233472 / 16,
-              "16 blocks of two force warps fit an SM (each block also reserves 1 KB)");
+static_assert(kForceWarps * force_smem_per_warp<kAngCap>() + 1024 <= 233472 / (28 / kForceWarps),
+              "28 force warps fit an SM's shared memory (each block also reserves 1 KB)");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -988,10 +989,11 @@ __device__ __forceinline__ bool force_atom(const AevArgs& a, const TG* __restric
 
 // Main force launch: one warp per atom; an atom with more than kAngCap
 // angular neighbors is left to the second launch (the AEV listed it).
-// The BF16 instance (the served path) is held to 64 registers: 16 blocks of
-// two warps per SM; the FP32 instances would spill there (12 blocks: <= 85).
+// The BF16 instance (the served path) is held to 64 registers (shared
+// memory then allows 29 one-warp blocks per SM); the FP32 instances would
+// spill there (24 warps: <= 85 registers).
 template <bool FAST, typename TG>
-__global__ void __launch_bounds__(kForceWarps * 32, std::is_same<TG, __nv_bfloat16>::value ? 16 : 12) k_forces(AevArgs a, const TG* __restrict__ dG,
+__global__ void __launch_bounds__(kForceWarps * 32, std::is_same<TG, __nv_bfloat16>::value ? 32 / kForceWarps : 24 / kForceWarps) k_forces(AevArgs a, const TG* __restrict__ dG,
                                                          double* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5;
